@@ -1,0 +1,82 @@
+"""Workload presets and seeded synthetic inputs.
+
+This module holds numbers and seeded random arrays only -- no step of the
+method's arithmetic -- so that both the CUDA path and the CPU oracle can
+consume the same inputs.  Values that need the method (the synthetic truth
+field and its noisy observations) are produced by ``tests/golden/make_workloads.py``
+with the oracle and stored in ``tests/golden/workload_<name>.json``.
+
+Presets follow the workloads of Sec. 3 of the paper (1D elliptic problem,
+2D Darcy flow with point observations) at the sizes used for parity and for
+the throughput measurement.
+"""
+import json
+import os
+
+import numpy as np
+
+PRESETS = {
+    # 1D elliptic -(e^u w')' = 1 on [0, 1], n = 128 FD intervals, 64 sine modes,
+    # C = (I - 0.01 Lap)^-2, 20 equispaced observations, sigma = 0.01.
+    "elliptic1d_n128": dict(dim=1, n=128, kl_modes=64, alpha=0.01, sigma=0.01,
+                             source_kind=0, src_amp=1.0, src_width=0.0,
+                             n_particles=256, n_components=2, gm_rank=64, mcmc_steps=5,
+                             beta0=0.2, ess_frac=0.5, data_refine=2, seed=2503016028),
+    # 2D Darcy on the unit square, 64 x 64 cells, 32 x 32 cosine modes,
+    # C = (I - 0.02 Lap)^-2, f = 10 exp(-50 |x - c|^2), 16 observations in
+    # mirror pairs (bimodal posterior), sigma = 0.005.
+    "darcy64_bimodal": dict(dim=2, n=64, kl_modes=32, alpha=0.02, sigma=0.005,
+                            source_kind=1, src_amp=10.0, src_width=50.0,
+                            n_particles=1024, n_components=4, gm_rank=64, mcmc_steps=10,
+                            beta0=0.2, ess_frac=0.5, data_refine=2, seed=2503016028),
+    # 2D Darcy at 256 x 256 cells, 128 x 128 modes, 64 observations on a
+    # jittered 8 x 8 lattice, sigma = 0.01, N = 4096, K = 8.
+    "darcy256_precision": dict(dim=2, n=256, kl_modes=128, alpha=0.02, sigma=0.01,
+                               source_kind=1, src_amp=10.0, src_width=50.0,
+                               n_particles=4096, n_components=8, gm_rank=64, mcmc_steps=10,
+                               beta0=0.2, ess_frac=0.5, data_refine=2, seed=2503016028),
+}
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+
+
+def observation_points(name):
+    """Observation locations of a preset (seeded; no method arithmetic)."""
+    p = PRESETS[name]
+    if p["dim"] == 1:
+        return np.arange(1, 21) / 21.0
+    if name == "darcy64_bimodal":
+        left = np.array([(x, y) for x in (0.2, 0.35) for y in (0.2, 0.4, 0.6, 0.8)])
+        right = left.copy()
+        right[:, 0] = 1.0 - right[:, 0]
+        return np.concatenate([left, right])
+    g = (np.arange(8) + 0.5) / 8.0
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    rng = np.random.default_rng(p["seed"])
+    return pts + rng.uniform(-0.03, 0.03, size=pts.shape)
+
+
+def load_workload(name):
+    """Preset merged with the stored observation points and data."""
+    with open(os.path.join(GOLDEN_DIR, "workload_%s.json" % name)) as fh:
+        wl = json.load(fh)
+    out = dict(PRESETS[name])
+    out["name"] = name
+    out["obs"] = np.asarray(wl["obs"], dtype=np.float64)
+    out["data"] = np.asarray(wl["data"], dtype=np.float64)
+    out["truth"] = np.asarray(wl["truth"], dtype=np.float64)
+    return out
+
+
+def random_particles(seed, N, d, scale=None):
+    """Seeded standard-normal particle states (optionally scaled per coordinate)."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, d))
+    if scale is not None:
+        X = X * np.asarray(scale)[None, :]
+    return X
+
+
+def random_potentials(seed, N, low=0.0, high=100.0):
+    return np.random.default_rng(seed).uniform(low, high, size=N)

@@ -1,0 +1,83 @@
+"""Pins for tempering, reweighting, resampling and the beta rule (Alg. 1, App. C)."""
+import math
+from fractions import Fraction
+from itertools import product
+
+import numpy as np
+
+from oracle import smc
+
+
+def test_ess_limits_and_monotonicity():
+    rng = np.random.default_rng(0)
+    phi = rng.uniform(0, 50, 300)
+    assert smc.ess_of_h(phi, 0.0) == 300.0
+    hs = np.linspace(0, 1, 200)
+    e = [smc.ess_of_h(phi, h) for h in hs]
+    assert all(e[i + 1] <= e[i] * (1 + 1e-14) for i in range(len(e) - 1))
+    assert abs(smc.ess_of_h(np.full(50, 3.7), 0.9) - 50.0) < 1e-12
+    # ESS equals (sum w^2)^-1 for the normalised weights (App. C)
+    w = np.exp(-0.3 * phi)
+    w /= w.sum()
+    assert abs(smc.ess_of_h(phi, 0.3) - 1.0 / np.sum(w * w)) < 1e-9
+
+
+def test_bisection_brackets_target():
+    rng = np.random.default_rng(1)
+    phi = rng.exponential(40.0, 500)
+    target = 250.0
+    h = smc.bisect_h(phi, 0.0, target)
+    assert 0 < h < 1
+    assert smc.ess_of_h(phi, h) >= target
+    assert smc.ess_of_h(phi, h * (1 + 1e-9) + 1e-15) < target
+    assert smc.bisect_h(np.full(10, 2.0), 0.25, 5.0) == 0.75
+
+
+def test_log_z_increment_direct_sum():
+    phi = np.random.default_rng(2).uniform(0, 30, 64)
+    h = 0.137
+    ref = math.log(math.fsum(math.exp(-h * p) for p in phi) / 64)
+    assert abs(smc.log_z_increment(phi, h) - ref) < 1e-12
+
+
+def _exact_indices(logw, u48):
+    w = smc.normalised_weights(np.asarray(logw))
+    cdf = smc.fixed_point_cdf(w)
+    N = len(w)
+    T = smc.RESAMPLE_T
+    U = Fraction(2 * u48 + 1, 2 * T)
+    out = []
+    for k in range(N):
+        p = (k + U) / N
+        out.append(min(i for i in range(N) if Fraction(cdf[i], T) > p))
+    return out, cdf
+
+
+def test_systematic_resampling_brute_force():
+    rng = np.random.default_rng(3)
+    for N in range(1, 7):
+        for _ in range(30):
+            logw = rng.normal(0, 2, N)
+            u48 = int(rng.integers(0, smc.RESAMPLE_T))
+            got = smc.systematic_indices(logw, u48)
+            ref, cdf = _exact_indices(logw, u48)
+            assert list(got) == ref
+            q = np.diff([0] + cdf)
+            assert sum(q) == smc.RESAMPLE_T
+            counts = np.bincount(got, minlength=N)
+            for i in range(N):
+                assert math.floor(N * q[i] / smc.RESAMPLE_T) <= counts[i] <= math.ceil(N * q[i] / smc.RESAMPLE_T)
+
+
+def test_equal_weights_identity_and_extremes():
+    for N in (1, 5, 64):
+        assert list(smc.systematic_indices(np.zeros(N), 12345)) == list(range(N))
+        assert list(smc.systematic_indices(np.zeros(N), smc.RESAMPLE_T - 1)) == list(range(N))
+    logw = np.array([0.0, -800.0, -800.0])
+    assert list(smc.systematic_indices(logw, 7)) == [0, 0, 0]
+
+
+def test_beta_rule_table():
+    for (acc, out) in [(0.31, 0.4), (0.3, 0.2), (0.2, 0.2), (0.15, 0.2), (0.149, 0.1), (0.0, 0.1)]:
+        assert smc.beta_rule(0.2, acc) == out
+    assert smc.beta_rule(0.8, 0.9) == 1.0
