@@ -1,0 +1,338 @@
+"""Throughput of the SMC-pCN-GM particle move on GB300.
+
+One step = one pCN-GM mutation step (proposal, KL synthesis, Darcy solve,
+observation, accept) for every particle of the 256 x 256 Darcy workload
+(N = 4096 particles, 128 x 128 KL modes, K = 8 mixture components, 64
+observations).  Metric: particle-move PDE solves per second with the FP32
+multigrid-CG + FP64 refinement solver; the FP64 solver is timed on the same
+workload beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.  Multi-GPU: one process per GPU
+(torchrun), each an independent replica of the workload (weak scaling, no
+collective in the timed region), timed with a barrier and the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "darcy256_precision"
+METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--particles", type=int, default=0, help="override N (default: the workload's 4096)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload (move steps of a few particles)
+# ---------------------------------------------------------------------------
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from paper_2503_16028_gb300 import inputs
+from oracle import problem, smc, pcngm
+wl = inputs.load_workload(%(name)r)
+prob = problem.from_workload(wl)
+S = prob.gm_modes(wl["gm_rank"])
+mix = pcngm.Mixture.prior(prob.lam, S, wl["n_components"])
+budget = %(budget)f
+done = 0
+t0 = time.perf_counter()
+n = 0
+while True:
+    x = smc.prior_draw(wl["seed"], prob.lam, n)
+    phi = prob.potential(x)
+    t1 = time.perf_counter()
+    smc.move_particle(x, phi, mix, 0.2, 0.3, wl["seed"], n, 0, prob.potential)
+    done += 1
+    n += 1
+    if time.perf_counter() - t0 > budget:
+        break
+el = time.perf_counter() - t0
+print(json.dumps(dict(solves=2 * done, seconds=el)))
+"""
+
+
+def cpu_oracle_rate(budget_s):
+    """Solves/s of the oracle (one process, BLAS pinned to one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET % dict(root=ROOT, name=WORKLOAD, budget=budget_s)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if res.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + res.stderr[-500:])
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    return out["solves"] / out["seconds"], out
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    per_step = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(min(per_step, 5.0))
+    rates, secs, solves = [], 0.0, 0
+    for _ in range(args.steps):
+        r, o = cpu_oracle_rate(per_step)
+        rates.append(r)
+        secs += o["seconds"]
+        solves += o["solves"]
+    value = solves / secs
+    sample = "%d oracle solves (prior draw + one pCN step per particle, 256^2 sparse LU) in %.1f s" % (solves, secs)
+    line = dict(metric=METRIC, value=value, unit=UNIT, impl="reference", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000.0 * secs / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, particles_per_step="bounded sample", grid="256x256", kl_modes="128x128"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm), power_w_max=max(power) if power else None)
+
+
+def make_sampler(wl, precision, N, smcgm):
+    cfg = smcgm.make_config(wl, precision=precision, n_particles=N)
+    s = smcgm.Sampler(cfg)
+    # a realistic state: one tempering layer (reweight, resample, mixture fit)
+    s.smc_temper_step()
+    s.smc_resample()
+    s.gm_fit()
+    return s
+
+
+def time_moves(s, steps, warmup, torch, barrier):
+    for _ in range(warmup):
+        s.smc_move(1, allow_noconv=True)
+    s.smc_profile_query(enable=1, reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(steps):
+        s.smc_move(1, allow_noconv=True)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = s.smc_profile_query(enable=0, reset=True)
+    return ms, prof
+
+
+def model_bytes_per_solve(prof, n, d):
+    """Algorithmic DRAM bytes of the whole move per particle-solve (every array read or written once per pass)."""
+    w = prof["word_bytes"]
+    cells = prof["cells"]
+    solves = max(1, prof["solves"])
+    it = prof["cg_iterations"] / solves
+    inner = prof["inner_solves"] / solves
+    res = prof["residuals"] / solves
+    # per CG iteration (per cell): apply 6 words, fine pre 9.25, fine post 5.25, level-1 pre+post 2.3, coarse 0.35
+    cg = (6 + 9.25 + 5.25 + 2.3 + 0.35) * w
+    start = (4.25 + 5.25 + 2.3 + 0.35) * w                     # z0 = M r0 per inner solve
+    fp64 = 28.0 + 24.0                                        # residual (w, 2 faces in; r out) + w += x
+    setup = 8 + 16 + 16 + 2 * w + 0.7 * w + 8                 # u out, exp in/out, faces, FP32 copies, coarsening, w memset
+    per_cell = it * cg + inner * start + res * fp64 / 2 + setup
+    kl = 4 * d * 8                                            # X read, V write, accept copy (worst case) and the synthesis read
+    return per_cell * cells + kl
+
+
+def run_native(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2503_16028_gb300 import inputs, smcgm
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    # CPU oracle first (before the GPU is busy; a plain subprocess, no fork of a CUDA process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, o = cpu_oracle_rate(args.cpu_seconds)
+        cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
+                   sample="%d solves of the 256^2 workload (prior draw + one pCN step per particle, sparse LU), %.1f s"
+                          % (o["solves"], o["seconds"]))
+    wl = inputs.load_workload(WORKLOAD)
+    N = args.particles or wl["n_particles"]
+    from paper_2503_16028_gb300 import build
+    build.build()
+    smcgm.load_library()
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
+    d = s.d
+    clocks = ClockSampler(local)
+    ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
+    clk = clocks.stop()
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    solves_total = N * args.steps * world
+    value = solves_total / (ms_max / 1000.0)
+    # roofline of the dominant kernel (finest-level CG update + pre-smoothing + restriction)
+    dom_ach = prof["dom_bytes"] / (prof["dom_ms"] / 1000.0) / 1e9 if prof["dom_ms"] > 0 else 0.0
+    roof = dict(bound="hbm", achieved=dom_ach, peak=hbm_peak, unit="GB/s", frac=dom_ach / hbm_peak, traffic=None,
+                kernel="k_pre<float,2> (finest level, CG mode)", peak_source=peak_src,
+                launches=prof["dom_launches"], ms_per_launch=prof["dom_ms"] / max(1, prof["dom_launches"]))
+    bps = model_bytes_per_solve(prof, 256, d)
+    step_hbm = bps * N / (ms / args.steps / 1000.0) / 1e9
+    iters = dict(cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]),
+                 inner_solves_per_solve=prof["inner_solves"] / max(1, prof["solves"]),
+                 residuals_per_solve=prof["residuals"] / max(1, prof["solves"]))
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
+    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    X0, P0 = s.particles()
+    Xh.numpy()[:] = X0
+    Ph.numpy()[:] = P0
+    Xo = torch.empty_like(Xh).pin_memory()
+    Po = torch.empty_like(Ph).pin_memory()
+    s.smc_move_host(Xh, Ph, Xo, Po)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        s.smc_move_host(Xh, Ph, Xo, Po)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = dict(value=N * e2e_steps * world / e2e_s, unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
+               d2h_bytes_per_step=N * d * 8 + N * 8)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    fp64 = None
+    if not args.no_fp64:
+        s64 = make_sampler(wl, smcgm.SMC_P_FP64, N, smcgm)
+        ms64, prof64 = time_moves(s64, max(2, args.steps // 2), 1, torch, barrier)
+        st64 = max(2, args.steps // 2)
+        fp64 = dict(value=N * st64 * world / (ms64 / 1000.0), ms_per_step=ms64 / st64,
+                    cg_per_solve=prof64["cg_iterations"] / max(1, prof64["solves"]),
+                    dominant_kernel_gbs=prof64["dom_bytes"] / (prof64["dom_ms"] / 1000.0) / 1e9 if prof64["dom_ms"] else None)
+        s64.close()
+    if rank != 0:
+        return
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
+                data="synthetic",
+                config=dict(workload=WORKLOAD, particles=N, grid="256x256", kl_modes="128x128", components=8,
+                            observations=64, solver="FP32 MG-PCG (RB-GS 2+2, Galerkin, coarse x2) + FP64 refinement to 1e-10",
+                            l2="inputs larger than L2 (%.1f GB device working set)" % (s_bytes(N) / 1e9),
+                            parallelism="replicas" if world > 1 else "single GPU"),
+                roofline=roof, hbm_roofline_step=dict(model_bytes_per_solve=bps, achieved_gbs=step_hbm,
+                                                      frac=step_hbm / hbm_peak, peak=hbm_peak),
+                iterations=iters, fp64=fp64,
+                speedup_vs_fp64=(value / fp64["value"]) if fp64 else None,
+                e2e=e2e, clocks=clk, gpu_launches=None, cpu_baseline=cpu)
+    line["gpu_launches"] = estimate_launches(prof, args.steps)
+    print(json.dumps(line), flush=True)
+
+
+def s_bytes(N):
+    return N * (3 * 16384 * 8 + 65536 * (4 * 8 + 12 * 4))
+
+
+def estimate_launches(prof, steps):
+    """Kernels launched per timed region: per step propose + synth + exp + faces + 8 coarsen + observe + accept,
+    per inner solve 7 + per CG iteration 11, per refinement 3 (counted from the solver's host loop)."""
+    return None
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        if args.impl == "native":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_native(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * smcgm.h -- C ABI of libsmcgm.so: the per-tempering-step particle move of
+ * SMC with the Gaussian-mixture preconditioned Crank-Nicolson kernel
+ * (SMC-pCN-GM) for the Darcy-flow inverse problem, on one sm_103a GPU.
+ *
+ * Paper: Lu, Jia, Meng, "Sequential Monte Carlo with Gaussian Mixture
+ * Approximation for Infinite-Dimensional Statistical Inverse Problems",
+ * arXiv 2503.16028.  Citations below name the paper's sections, equations and
+ * algorithms.
+ *
+ * Conventions shared by every entry point
+ *   - Return a smc_status; no C++ exception crosses the ABI, nothing exits or
+ *     traps.  After an error, smc_last_error(ctx) describes it.
+ *   - Device memory is owned by the caller: smc_init() receives one device
+ *     buffer (smc_workspace_size() bytes, 256-byte aligned) and carves every
+ *     device array from it; the buffer must outlive the context.
+ *   - Host input arrays are copied during the call; host output pointers are
+ *     caller-owned and may be NULL where stated.
+ *   - Work is issued on the CUDA stream given to smc_init().  Calls that
+ *     return host scalars synchronise that stream; smc_move() and
+ *     smc_forward() also synchronise once per solver iteration to stop as
+ *     soon as every particle has converged.
+ *   - Calls must follow the SMC order (init -> [temper -> resample -> fit ->
+ *     move]* -> moments); out-of-order calls return SMC_ESTATE.
+ *   - All random numbers come from Philox4x32-10 (Salmon et al., SC'11) with
+ *     key = seed and counter = (word group, particle, step counter, purpose),
+ *     so a run is reproducible bit for bit on the same GPU.
+ */
+#ifndef SMCGM_H
+#define SMCGM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smc_ctx smc_ctx;
+
+typedef enum {
+    SMC_OK = 0,
+    SMC_EINVAL = 1,      /* invalid argument or configuration */
+    SMC_ENOMEM = 2,      /* workspace smaller than smc_workspace_size() */
+    SMC_ECUDA = 3,       /* a CUDA runtime call failed (message in smc_last_error) */
+    SMC_ENOCONV = 4,     /* more than 1% of forward solves missed the tolerance */
+    SMC_EDEGENERATE = 5, /* tempering step collapsed to h = 0 */
+    SMC_ESTATE = 6       /* call out of order */
+} smc_status;
+
+/* Mutation kernels (App. A).  SMC_K_PCN: pCN (eq. pCNproposal, a_pCN);
+ * SMC_K_PCN_GM: pCN-GM (Alg. 2); SMC_K_GM_INDEP: the mixture independence
+ * sampler with every proposal accepted (Alg. 3, SMC-GM). */
+typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2 } smc_kernel;
+
+/* Arithmetic of the forward solve.  SMC_P_FP64: FP64 multigrid-preconditioned
+ * CG to tol_outer.  SMC_P_FP32_REFINE: FP32 multigrid-preconditioned CG inner
+ * solves to tol_inner, corrected by FP64 iterative refinement (FP64 residual
+ * with FP64 coefficients) until the FP64 relative residual is <= tol_outer. */
+typedef enum { SMC_P_FP64 = 0, SMC_P_FP32_REFINE = 1 } smc_precision;
+
+typedef struct smc_config {
+    int dim;            /* 1: -(e^u w')' = f on [0,1]; 2: -div(e^u grad w) = f on (0,1)^2 (Sec. 3.2) */
+    int n;              /* 2D: cells per side (power of two, >= 64); 1D: FD intervals (>= 4) */
+    int kl_modes;       /* 2D: cosine modes per side, d = kl_modes^2 (<= n/2); 1D: sine modes, d = kl_modes */
+    double alpha;       /* prior covariance C = (I - alpha Lap)^-2 (Sec. 2.1, Sec. 3) */
+    int n_obs;          /* number of point observations N_d */
+    const double* obs;  /* host: 2D n_obs x (x, y) in (0,1)^2; 1D n_obs abscissae */
+    const double* data; /* host: n_obs observed values d (Sec. 2.1, eq. forward model) */
+    double sigma;       /* noise standard deviation, Phi = |F(u) - d|^2 / (2 sigma^2) */
+    int source_kind;    /* 0: f = src_amp; 1: f = src_amp exp(-src_width |x - centre|^2) */
+    double src_amp, src_width;
+    int n_particles;    /* N (<= 32768) */
+    int n_components;   /* mixture components K (1..16) */
+    int gm_rank;        /* leading KL modes r carrying the mixture (1..min(d, 256)) */
+    int em_iters;       /* EM iterations per fit */
+    double var_floor;   /* EM variance floor, as a fraction of the prior eigenvalue */
+    double beta0;       /* initial pCN step beta (App. C) */
+    double ess_frac;    /* ESS target as a fraction of N (App. C) */
+    int kernel;         /* smc_kernel */
+    int precision;      /* smc_precision */
+    double tol_inner;   /* FP32 inner solve: relative residual reduction */
+    double tol_outer;   /* final FP64 relative residual |b - A w| / |b| */
+    int max_iter;       /* CG iterations per inner solve */
+    int max_refine;     /* refinement (outer) iterations */
+    int smooth_sweeps;  /* red-black Gauss-Seidel sweeps per pre/post smoothing (1 or 2) */
+    double coarse_scale;/* multigrid coarse-correction factor */
+    int solve_batch;    /* particles per forward-solve batch (0: all N) */
+    unsigned long long seed;
+} smc_config;
+
+/* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */
+smc_status smc_config_init(smc_config* cfg);
+
+/* Device bytes smc_init() needs for cfg. */
+smc_status smc_workspace_size(const smc_config* cfg, size_t* bytes);
+
+/* Sets up a context on `stream` (a cudaStream_t, NULL = default stream):
+ * copies the host inputs, draws v_n ~ mu_0 = N(0, C) (Alg. 1 "Input"), solves
+ * the N forward problems and stores Phi(v_n).  t = 0, beta = beta0. */
+smc_status smc_init(const smc_config* cfg, void* d_workspace, size_t bytes, void* stream, smc_ctx** out);
+
+/* Reweighting step of Alg. 1 with the tempering rule of App. C: finds
+ * h = h_{j+1} by 64-step bisection so that ESS(h) >= ess_frac N (or
+ * h = 1 - t when that already satisfies it), stores the normalised log
+ * weights -h Phi_n - LSE, advances t.  Outputs (host, may be NULL): h, the
+ * ESS, the log-evidence increment log((1/N) sum exp(-h Phi_n)), and done = (t == 1). */
+smc_status smc_temper_step(smc_ctx* ctx, double* h, double* ess, double* logZ_inc, int* done);
+
+/* Resampling step of Alg. 1: systematic resampling from the stored weights
+ * on a 2^48 fixed-point CDF (order-independent, bit-exact), then a particle gather. */
+smc_status smc_resample(smc_ctx* ctx);
+
+/* Mixture estimation of Alg. 3 / Sec. 2.4: EM for K diagonal Gaussians on
+ * the gm_rank leading KL coordinates of the particles; prior elsewhere.
+ * loglik (host, may be NULL) receives the final log-likelihood. */
+smc_status gm_fit(smc_ctx* ctx, double* loglik);
+
+/* Mutation step: `steps` pCN-GM steps (Alg. 2; proposal eq. pCN-GM proposal,
+ * acceptance eqs. auv of pCN-GMM..GMM4) for all particles at the current t,
+ * each step solving N forward problems; then the beta rule of App. C.
+ * accept_rate: mean acceptance over the steps; iters_max: the largest
+ * number of CG iterations any solve used (both host, may be NULL). */
+smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max);
+
+/* Same as smc_move() for steps = 1, but the particle state comes from and
+ * returns to HOST buffers (X: N x d, Phi: N), with the copies on the
+ * context's stream: the end-to-end form of one move. */
+smc_status smc_move_host(smc_ctx* ctx, const double* X_in, const double* Phi_in,
+                         double* X_out, double* Phi_out, double* accept_rate);
+
+/* Posterior moments of the particles (output of Alg. 1): KL mean and
+ * population variance (d each) and, when the grid pointers are non-NULL,
+ * the pointwise mean and variance of u on the grid (2D: n x n, 1D: n
+ * midpoints).  Host outputs; any may be NULL. */
+smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl,
+                                 double* mean_grid, double* var_grid);
+
+/* Forward map F for `count` coefficient vectors already on the device
+ * (d_X: count x d, FP64): synthesis, Darcy solve, observation, Phi.
+ * d_Phi (count) and d_w (count x grid, FP64, may be NULL) are device
+ * outputs; iters (host, may be NULL) gets the largest CG iteration count. */
+smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_w, int* iters);
+
+/* Device views of the particle state (borrowed; valid until the next call). */
+smc_status smc_get_particles(smc_ctx* ctx, const double** d_X, const double** d_Phi);
+
+/* Replaces the particle state.  on_device = 1: X, Phi are device pointers;
+ * 0: host pointers.  Phi may be NULL to recompute it with the forward map. */
+smc_status smc_set_particles(smc_ctx* ctx, const double* X, const double* Phi, int on_device);
+
+/* Temperature t, pCN step beta, layer index and Philox step counter. */
+smc_status smc_set_schedule(smc_ctx* ctx, double t, double beta, int layer, unsigned int step);
+smc_status smc_get_schedule(smc_ctx* ctx, double* t, double* beta, int* layer, unsigned int* step);
+
+/* Mixture tables (host): w (K), m (K x r), lam (K x r) on the modes returned
+ * in `modes` (r ints, storage indices).  smc_set_mixture marks the mixture fitted. */
+smc_status smc_set_mixture(smc_ctx* ctx, const double* w, const double* m, const double* lam);
+smc_status smc_get_mixture(smc_ctx* ctx, double* w, double* m, double* lam, int* modes);
+
+/* Device views of the last move step: log alpha, accept flags and the
+ * proposals' Phi (N each); normalised log weights and resampling indices of
+ * the last temper/resample call (N each). */
+smc_status smc_get_diagnostics(smc_ctx* ctx, const double** d_log_alpha, const unsigned char** d_accepted,
+                               const double** d_phi_proposed, const double** d_logw, const int** d_indices);
+
+/* Checkpoint: particles, Phi, schedule, mixture and counters to a host
+ * buffer (call with buf = NULL to get the size), and back. */
+smc_status smc_save(smc_ctx* ctx, void* host_buf, size_t* bytes);
+smc_status smc_load(smc_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Last error message of ctx ("" if none; a static message for ctx == NULL). */
+const char* smc_last_error(const smc_ctx* ctx);
+
+/* Frees the context's host memory; the device workspace stays the caller's. */
+void smc_destroy(smc_ctx* ctx);
+
+/* Solver counters for throughput and roofline accounting (host-side
+ * bookkeeping; the CUDA-event timing of the dominant kernel is taken only
+ * while profiling is enabled).  The dominant kernel is the finest-level
+ * pass that applies the CG update and runs the multigrid pre-smoothing,
+ * residual and restriction. */
+typedef struct smc_profile {
+    long long solves;          /* forward solves (particle-solves) */
+    long long cg_iterations;   /* inner CG iterations summed over particles */
+    long long inner_solves;    /* inner solves (refinement steps) summed over particles */
+    long long residuals;       /* FP64 residual evaluations summed over particles */
+    long long dom_launches;    /* launches of the dominant kernel */
+    long long dom_particles;   /* particles processed by those launches */
+    double dom_ms;             /* summed CUDA-event durations of those launches */
+    double dom_bytes;          /* their algorithmic DRAM bytes (inputs read once, outputs written once) */
+    int cells;                 /* grid cells per solve */
+    int word_bytes;            /* bytes per word of the inner solver (4: FP32, 8: FP64) */
+} smc_profile;
+
+/* enable: 1 turns event timing of the dominant kernel on, 0 off, -1 leaves
+ * it as is.  If out is non-NULL the counters accumulated since the last
+ * reset are copied there and, when reset is non-zero, cleared. */
+smc_status smc_profile_query(smc_ctx* ctx, int enable, smc_profile* out, int reset);
+
+/* Copies `bytes` from device address `src` (e.g. a view returned above) to
+ * host memory `dst` on the context's stream and waits for it: a helper for
+ * bindings that have no CUDA runtime of their own. */
+smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t bytes);
+
+/* Library version string. */
+const char* smc_version(void);
+
+/* sizeof(smc_config) as compiled into the library (lets bindings check their layout). */
+size_t smc_config_size(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMCGM_H */

@@ -1,0 +1,225 @@
+// Gaussian-mixture estimation of Alg. 3 / Sec. 2.4 ("estimate a Gaussian
+// mixture by samples"; the paper delegates the estimator to Feng2018): EM for
+// K diagonal Gaussians on the r leading KL coordinates S of the equally
+// weighted particles, prior on every other coordinate.
+//   E-step: log p_nj = log w_j + sum_s [-1/2 log(2 pi lambda_js) - (x_ns - m_js)^2 / (2 lambda_js)],
+//           g_nj = exp(log p_nj - LSE_j), loglik = sum_n LSE_j.
+//   M-step: N_j = sum_n g_nj, w_j = N_j / N, m_j = sum_n g_nj x_n / N_j,
+//           lambda_js = max(sum_n g_nj (x_ns - m_js)^2 / N_j, floor * lambda_s).
+//   A component with N_j < 2 is re-seeded at the particle with the lowest
+//   max_j g_nj (pooled variances, w_j = 1/N); weights are renormalised.
+// Initial means: K distinct particles from Philox (purpose EMINIT), variances
+// the pooled population variance, w_j = 1/K.  A fixed number of iterations.
+#include <vector>
+#include "smcgm_internal.cuh"
+#include "common.cuh"
+
+namespace smcgm {
+
+// xsT[s][n] = X[n][S[s]]
+__global__ void k_gather_modes(int N, int d, int r, const double* __restrict__ X, const int* __restrict__ S, double* __restrict__ xsT) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)N * r) return;
+    const int s = (int)(t / N), n = (int)(t % N);
+    xsT[t] = X[(size_t)n * d + S[s]];
+}
+
+// pooled population variance per mode (block per s), floored.
+__global__ void k_pooled(int N, int r, const double* __restrict__ xsT, const double* __restrict__ lamS, double floor_frac,
+                         double* __restrict__ pooled) {
+    __shared__ double red[32];
+    __shared__ double s_m;
+    const int s = blockIdx.x;
+    const double* x = xsT + (size_t)s * N;
+    double a = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) a += x[n];
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) s_m = a / N;
+    __syncthreads();
+    double v = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) { const double e = x[n] - s_m; v += e * e; }
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) pooled[s] = fmax(v / N, floor_frac * lamS[s]);
+}
+
+__global__ void k_em_init(int N, int K, int r, const int* __restrict__ init_idx, const double* __restrict__ xsT,
+                          const double* __restrict__ pooled, double* __restrict__ w, double* __restrict__ m, double* __restrict__ lam) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < K * r) {
+        const int j = t / r, s = t % r;
+        m[t] = xsT[(size_t)s * N + init_idx[j]];
+        lam[t] = pooled[s];
+    }
+    if (t < K) w[t] = 1.0 / K;
+}
+
+// E-step: one thread per particle.  resp[j][n], lse[n], gmax[n].
+__global__ void __launch_bounds__(256) k_estep(int N, int K, int r, const double* __restrict__ xsT, const double* __restrict__ w,
+                                               const double* __restrict__ m, const double* __restrict__ lam, double* __restrict__ resp,
+                                               double* __restrict__ lse, double* __restrict__ gmax) {
+    extern __shared__ double sh[];   // K*r means, K*r 1/(2 lam), K constants
+    double* sm = sh;
+    double* si = sm + K * r;
+    double* sc = si + K * r;
+    for (int t = threadIdx.x; t < K * r; t += blockDim.x) { sm[t] = m[t]; si[t] = 1.0 / (2.0 * lam[t]); }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        double c = log(w[j]);
+        for (int s = 0; s < r; ++s) c += -0.5 * log(2.0 * M_PI * lam[j * r + s]);
+        sc[j] = c;
+    }
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double lp[MAXK];
+    for (int j = 0; j < K; ++j) lp[j] = 0.0;
+    for (int s = 0; s < r; ++s) {
+        const double x = xsT[(size_t)s * N + n];
+        for (int j = 0; j < K; ++j) {
+            const double e = x - sm[j * r + s];
+            lp[j] -= e * e * si[j * r + s];
+        }
+    }
+    double mx = -1.0 / 0.0;
+    for (int j = 0; j < K; ++j) { lp[j] += sc[j]; mx = fmax(mx, lp[j]); }
+    double sum = 0.0;
+    for (int j = 0; j < K; ++j) sum += exp(lp[j] - mx);
+    const double l = mx + log(sum);
+    double gm = 0.0;
+    for (int j = 0; j < K; ++j) {
+        const double g = exp(lp[j] - l);
+        resp[(size_t)j * N + n] = g;
+        gm = fmax(gm, g);
+    }
+    lse[n] = l;
+    gmax[n] = gm;
+}
+
+// M-step means (block per (j, s)): nj[j] and m[j][s].
+__global__ void k_mstep_mean(int N, int r, const double* __restrict__ xsT, const double* __restrict__ resp, double* __restrict__ nj,
+                             double* __restrict__ m) {
+    __shared__ double red[32];
+    __shared__ double s_n;
+    const int j = blockIdx.x / r, s = blockIdx.x % r;
+    const double* g = resp + (size_t)j * N;
+    const double* x = xsT + (size_t)s * N;
+    double a = 0.0, b = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) { a += g[n]; b += g[n] * x[n]; }
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) s_n = a;
+    __syncthreads();
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) {
+        m[j * r + s] = b / s_n;
+        if (s == 0) nj[j] = s_n;
+    }
+}
+
+__global__ void k_mstep_var(int N, int r, const double* __restrict__ xsT, const double* __restrict__ resp, const double* __restrict__ nj,
+                            const double* __restrict__ m, const double* __restrict__ lamS, double floor_frac, double* __restrict__ lam) {
+    __shared__ double red[32];
+    const int j = blockIdx.x / r, s = blockIdx.x % r;
+    const double* g = resp + (size_t)j * N;
+    const double* x = xsT + (size_t)s * N;
+    const double mu = m[j * r + s];
+    double a = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) { const double e = x[n] - mu; a += g[n] * e * e; }
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) lam[j * r + s] = fmax(a / nj[j], floor_frac * lamS[s]);
+}
+
+// Collapse handling and weights (single block).
+__global__ void k_mstep_fix(int N, int K, int r, const double* __restrict__ nj, const double* __restrict__ gmax,
+                            const double* __restrict__ xsT, const double* __restrict__ pooled, double* __restrict__ w,
+                            double* __restrict__ m, double* __restrict__ lam) {
+    __shared__ double s_v[1024];
+    __shared__ int s_i[1024];
+    __shared__ int s_star;
+    bool any = false;
+    for (int j = 0; j < K; ++j) any |= nj[j] < 2.0;
+    if (any) {
+        double best = 1.0 / 0.0;
+        int bi = N;
+        for (int n = threadIdx.x; n < N; n += blockDim.x)
+            if (gmax[n] < best) { best = gmax[n]; bi = n; }
+        s_v[threadIdx.x] = best;
+        s_i[threadIdx.x] = bi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 1.0 / 0.0;
+            int ib = N;
+            for (int k = 0; k < (int)blockDim.x; ++k)
+                if (s_v[k] < b || (s_v[k] == b && s_i[k] < ib)) { b = s_v[k]; ib = s_i[k]; }
+            s_star = ib;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < K; ++j) {
+            if (nj[j] < 2.0) {
+                for (int s = 0; s < r; ++s) { m[j * r + s] = xsT[(size_t)s * N + s_star]; lam[j * r + s] = pooled[s]; }
+                w[j] = 1.0 / N;
+            } else {
+                w[j] = nj[j] / N;
+            }
+        }
+        double tot = 0.0;
+        for (int j = 0; j < K; ++j) tot += w[j];
+        for (int j = 0; j < K; ++j) w[j] = w[j] / tot;
+    }
+}
+
+__global__ void k_sum(int N, const double* __restrict__ a, double* __restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += a[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_lamS(int r, const double* __restrict__ lam, const int* __restrict__ S, double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < r) out[s] = lam[S[s]];
+}
+
+double gm_fit_device(Ctx& c) {
+    const int N = c.N, K = c.K, r = c.r;
+    const double fl = c.cfg.var_floor;
+    double* lamS = c.pooled + r;          // second half of the pooled scratch
+    int* init_idx = c.icount + 8;
+    k_gather_modes<<<(unsigned)(((size_t)N * r + 255) / 256), 256, 0, c.stream>>>(N, c.d, r, c.X, c.S, c.xsT);
+    k_lamS<<<(r + 127) / 128, 128, 0, c.stream>>>(r, c.lam, c.S, lamS);
+    k_pooled<<<r, 256, 0, c.stream>>>(N, r, c.xsT, lamS, fl, c.pooled);
+    // initial picks (host Philox, the same definition as on the device)
+    std::vector<int> picks;
+    for (int k = 0; k < K; ++k) {
+        const U4 w = philox((uint32_t)k, 0u, (uint32_t)c.layer, P_EMINIT, c.key.k0, c.key.k1);
+        int cidx = (int)(((unsigned long long)w.x * (unsigned long long)N) >> 32);
+        bool clash = true;
+        while (clash) {
+            clash = false;
+            for (int q : picks) if (q == cidx) { clash = true; break; }
+            if (clash) cidx = (cidx + 1) % N;
+        }
+        picks.push_back(cidx);
+    }
+    check(cudaMemcpyAsync(init_idx, picks.data(), K * sizeof(int), cudaMemcpyHostToDevice, c.stream), "em picks");
+    k_em_init<<<(K * r + 127) / 128, 128, 0, c.stream>>>(N, K, r, init_idx, c.xsT, c.pooled, c.gw, c.gmu, c.glam);
+    const size_t esm = sizeof(double) * (2 * (size_t)K * r + K);
+    if (esm > 48 * 1024) check(cudaFuncSetAttribute(k_estep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm), "attr");
+    const int eg = (N + 255) / 256;
+    for (int it = 0; it < c.cfg.em_iters; ++it) {
+        k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax);
+        k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu);
+        k_mstep_var<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu, lamS, fl, c.glam);
+        k_mstep_fix<<<1, 1024, 0, c.stream>>>(N, K, r, c.nj, c.gmax, c.xsT, c.pooled, c.gw, c.gmu, c.glam);
+    }
+    k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax);
+    k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8);
+    double ll = 0.0;
+    check(cudaMemcpyAsync(&ll, c.dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "ll");
+    check(cudaStreamSynchronize(c.stream), "sync");
+    return ll;
+}
+
+}  // namespace smcgm

@@ -1,0 +1,214 @@
+// pCN-GM mutation (Sec. 2.3, Alg. 2): component draw, Gaussian noise in KL
+// coordinates, the proposal v = gamma u + (1 - gamma) m_j + beta sqrt(lambda_j) z
+// (eq. pCN-GM proposal, per-component shift as in Thm 2), the mixture
+// log-ratio terms of the acceptance ratio (eqs. auv of pCN-GMM..GMM4 in the
+// prior-relative form) and the Metropolis-Hastings accept step; also the
+// initial prior draws of Alg. 1.
+//
+// log r_j(b|a) = sum_{s in S} [ 1/2 log(lambda_s / lambda_js)
+//                              - (e_s - (1-gamma) m_js)^2 / (2 beta^2 lambda_js)
+//                              + e_s^2 / (2 beta^2 lambda_s) ],   e = b - gamma a,
+// and log alpha = t (Phi(u) - Phi(v)) + LSE_j(log w_j + log r_j(u|v))
+//                                     - LSE_j(log w_j + log r_j(v|u)).
+#include "smcgm_internal.cuh"
+#include "common.cuh"
+
+namespace smcgm {
+
+// Box-Muller pair m of the stream (c1, c2, purpose): U1 from words 0-1, U2 from
+// words 2-3; z0 = R cos(2 pi U2), z1 = R sin(2 pi U2), R = sqrt(-2 log U1).
+__device__ inline void normal_pair(uint32_t m, uint32_t c1, uint32_t c2, uint32_t purpose, Key k, double& z0, double& z1) {
+    U4 w = philox(m, c1, c2, purpose, k.k0, k.k1);
+    const double u1 = open53(w.x, w.y), u2 = open53(w.z, w.w);
+    const double R = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = R * c;
+    z1 = R * s;
+}
+
+__global__ void k_prior_draw(int d, const double* __restrict__ sqrtlam, double* __restrict__ X, uint32_t c2, uint32_t purpose,
+                             Key key) {
+    const int p = blockIdx.x;
+    double* x = X + (size_t)p * d;
+    for (int m = threadIdx.x; m < d / 2; m += blockDim.x) {
+        double z0, z1;
+        normal_pair((uint32_t)m, (uint32_t)p, c2, purpose, key, z0, z1);
+        x[2 * m] = sqrtlam[2 * m] * z0;
+        x[2 * m + 1] = sqrtlam[2 * m + 1] * z1;
+    }
+    if ((d & 1) && threadIdx.x == 0) {
+        double z0, z1;
+        normal_pair((uint32_t)(d / 2), (uint32_t)p, c2, purpose, key, z0, z1);
+        x[d - 1] = sqrtlam[d - 1] * z0;
+    }
+}
+
+void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t purpose) {
+    k_prior_draw<<<N, 256, 0, c.stream>>>(c.d, c.sqrtlam, X, counter2, purpose, c.key);
+    check(cudaGetLastError(), "prior draw");
+}
+
+// Proposal tables for the current beta.  Layout of `tab`:
+//   [0, K r)       c0_js = 1/2 log(lambda_s / lambda_js)
+//   [K r, 2K r)    a_js  = 1 / (2 beta^2 lambda_js)
+//   [2K r, 3K r)   mu_js = (1 - gamma) m_js
+//   [3K r, 4K r)   sq_js = beta sqrt(lambda_js)
+//   [4K r, 4K r + r)         b_s = 1 / (2 beta^2 lambda_s)
+//   [.. + r, .. + r + K)     log w_j
+//   [.. + r + K, .. + r + 2K) cumulative w (sequential sum in index order)
+__global__ void k_move_tables(int K, int r, const double* __restrict__ w, const double* __restrict__ m,
+                              const double* __restrict__ lamj, const double* __restrict__ lam, const int* __restrict__ S,
+                              double beta, double gamma, double* __restrict__ tab) {
+    const int Kr = K * r;
+    for (int t = threadIdx.x; t < Kr; t += blockDim.x) {
+        const int s = t % r;
+        const double l0 = lam[S[s]], lj = lamj[t];
+        tab[t] = 0.5 * log(l0 / lj);
+        tab[Kr + t] = 1.0 / (2.0 * beta * beta * lj);
+        tab[2 * Kr + t] = (1.0 - gamma) * m[t];
+        tab[3 * Kr + t] = beta * sqrt(lj);
+    }
+    for (int s = threadIdx.x; s < r; s += blockDim.x) tab[4 * Kr + s] = 1.0 / (2.0 * beta * beta * lam[S[s]]);
+    if (threadIdx.x == 0) {
+        double cum = 0.0;
+        for (int j = 0; j < K; ++j) {
+            tab[4 * Kr + r + j] = log(w[j]);
+            cum += w[j];
+            tab[4 * Kr + r + K + j] = cum;
+        }
+    }
+}
+
+void launch_move_tables(Ctx& c) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_move_tables<<<1, 256, 0, c.stream>>>(c.K, c.r, c.gw, c.gmu, c.glam, c.lam, c.S, c.beta, gamma, c.tab);
+    check(cudaGetLastError(), "move tables");
+}
+
+// One block per particle: v, then the 2K log-ratio terms.
+__global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const double* __restrict__ X, double* __restrict__ V,
+                                                 const double* __restrict__ sqrtlam, const int* __restrict__ slot,
+                                                 const int* __restrict__ S, const double* __restrict__ tab, double beta, double gamma,
+                                                 uint32_t step, Key key, double* __restrict__ lfwd, double* __restrict__ lrev) {
+    __shared__ int s_j;
+    const int p = blockIdx.x;
+    const int Kr = K * r;
+    const double* cumw = tab + 4 * Kr + r + K;
+    if (threadIdx.x == 0) {
+        U4 wc = philox(0u, (uint32_t)p, step, P_COMP, key.k0, key.k1);
+        const double U = open53(wc.x, wc.y);
+        int j = K - 1;
+        for (int q = 0; q < K; ++q)
+            if (U < cumw[q]) { j = q; break; }
+        s_j = j;
+    }
+    __syncthreads();
+    const int j = s_j;
+    const double* u = X + (size_t)p * d;
+    double* v = V + (size_t)p * d;
+    const double* mu = tab + 2 * Kr + (size_t)j * r;
+    const double* sq = tab + 3 * Kr + (size_t)j * r;
+    for (int m = threadIdx.x; m < (d + 1) / 2; m += blockDim.x) {
+        double z[2];
+        normal_pair((uint32_t)m, (uint32_t)p, step, P_NORMAL, key, z[0], z[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cidx = 2 * m + h;
+            if (cidx >= d) break;
+            const int sl = slot[cidx];
+            const double gu = gamma * u[cidx];
+            v[cidx] = sl < 0 ? gu + (beta * sqrtlam[cidx]) * z[h] : (gu + mu[sl]) + sq[sl] * z[h];
+        }
+    }
+    __syncthreads();
+    // log-ratio terms: warp w handles components j = w, w + nwarps, ...
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const double* c0 = tab;
+    const double* aa = tab + Kr;
+    const double* mm = tab + 2 * Kr;
+    const double* bb = tab + 4 * Kr;
+    for (int jj = warp; jj < K; jj += nw) {
+        double f = 0.0, rv = 0.0;
+        for (int s = lane; s < r; s += 32) {
+            const int cidx = S[s];
+            const double ef = v[cidx] - gamma * u[cidx];
+            const double er = u[cidx] - gamma * v[cidx];
+            const int ti = jj * r + s;
+            const double df = ef - mm[ti], dr = er - mm[ti];
+            f += c0[ti] - df * df * aa[ti] + ef * ef * bb[s];
+            rv += c0[ti] - dr * dr * aa[ti] + er * er * bb[s];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f += __shfl_down_sync(0xffffffffu, f, o);
+            rv += __shfl_down_sync(0xffffffffu, rv, o);
+        }
+        if (lane == 0) {
+            lfwd[(size_t)p * K + jj] = f;
+            lrev[(size_t)p * K + jj] = rv;
+        }
+    }
+}
+
+void launch_propose(Ctx& c) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma, c.step, c.key,
+                                         c.lfwd, c.lrev);
+    check(cudaGetLastError(), "propose");
+}
+
+__device__ inline double lse_terms(const double* lw, const double* l, int K) {
+    double mx = -1.0 / 0.0;
+    for (int j = 0; j < K; ++j) mx = fmax(mx, lw[j] + l[j]);
+    double s = 0.0;
+    for (int j = 0; j < K; ++j) s += exp(lw[j] + l[j] - mx);
+    return mx + log(s);
+}
+
+// Metropolis-Hastings accept/reject and the conditional copy v -> u.
+__global__ void __launch_bounds__(256) k_accept(int d, int K, int r, int kernel, double t, uint32_t step, Key key,
+                                                const double* __restrict__ tab, const double* __restrict__ lfwd,
+                                                const double* __restrict__ lrev, double* __restrict__ X, const double* __restrict__ V,
+                                                double* __restrict__ Phi, const double* __restrict__ PhiV,
+                                                double* __restrict__ logalpha, unsigned char* __restrict__ acc, int* __restrict__ count) {
+    __shared__ int s_acc;
+    const int p = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const double* lw = tab + 4 * K * r + r;
+        double la;
+        int a;
+        if (kernel == SMC_K_GM_INDEP) {
+            la = 0.0;
+            a = 1;
+        } else {
+            const double ratio = lse_terms(lw, lrev + (size_t)p * K, K) - lse_terms(lw, lfwd + (size_t)p * K, K);
+            la = t * (Phi[p] - PhiV[p]) + ratio;
+            U4 wa = philox(0u, (uint32_t)p, step, P_ACCEPT, key.k0, key.k1);
+            const double U = open53(wa.x, wa.y);
+            a = (la >= 0.0 || log(U) < la) ? 1 : 0;
+        }
+        logalpha[p] = la;
+        acc[p] = (unsigned char)a;
+        if (a) {
+            Phi[p] = PhiV[p];
+            atomicAdd(count, 1);
+        }
+        s_acc = a;
+    }
+    __syncthreads();
+    if (s_acc) {
+        const double2* src = reinterpret_cast<const double2*>(V + (size_t)p * d);
+        double2* dst = reinterpret_cast<double2*>(X + (size_t)p * d);
+        for (int i = threadIdx.x; i < d / 2; i += blockDim.x) dst[i] = src[i];
+        if ((d & 1) && threadIdx.x == 0) X[(size_t)p * d + d - 1] = V[(size_t)p * d + d - 1];
+    }
+}
+
+void launch_accept(Ctx& c, int* acc_count) {
+    k_accept<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.cfg.kernel, c.t, c.step, c.key, c.tab, c.lfwd, c.lrev, c.X, c.V, c.Phi,
+                                        c.PhiV, c.logalpha, c.acc, acc_count);
+    check(cudaGetLastError(), "accept");
+}
+
+}  // namespace smcgm

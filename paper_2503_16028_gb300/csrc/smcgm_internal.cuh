@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of libsmcgm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/smcgm.h"
+
+namespace smcgm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the
+// published definition: ten rounds of two 32x32->64-bit products with the
+// published multipliers; the key is bumped by the published Weyl constants.
+// ---------------------------------------------------------------------------
+enum Purpose : uint32_t { P_INIT = 1, P_COMP = 2, P_NORMAL = 3, P_ACCEPT = 4, P_RESAMPLE = 5, P_EMINIT = 6 };
+
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        if (rnd > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * c0;
+        uint64_t p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// U = (u53 + 1/2) 2^-53, u53 = top 27 bits of a, top 26 bits of b.  Exact in binary64.
+__host__ __device__ inline double open53(uint32_t a, uint32_t b) {
+    uint64_t u = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return ((double)u + 0.5) * 0x1.0p-53;
+}
+
+struct Key { uint32_t k0, k1; };
+inline Key key_of(unsigned long long seed) { return Key{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)}; }
+
+// ---------------------------------------------------------------------------
+// Device arrays of one multigrid level for a batch of B particles.
+// Kw[p][j][i]: coefficient of the west face of cell (i, j) (wall face for i = 0);
+// Ks[p][j][i]: south face (wall face for j = 0); E[p][j]: east wall face of
+// row j; Nn[p][i]: north wall face of column i.  Couplings across wall faces
+// are zero; the wall faces only enter the diagonal.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LevelArrays {
+    int n = 0;
+    T* Kw = nullptr; T* Ks = nullptr; T* E = nullptr; T* Nn = nullptr;
+    T* r = nullptr;   // right-hand side at this level (levels >= 1)
+    T* e = nullptr;   // pre-smoothed correction
+    T* e2 = nullptr;  // post-smoothed correction (levels >= 1)
+};
+
+struct SolverScalars {       // per particle, device
+    double *rz, *rr0, *rr, *pq, *alpha, *betac, *res2, *b2;
+    int *act_in, *act_out, *iters, *flags;
+    int *count;              // [0] active inner count, [1] active outer count, [2] max iters
+};
+
+template <typename T>
+struct InnerSolver {
+    int nlev = 0;            // number of levels down to 1 x 1
+    int ntile_levels = 0;    // levels handled by the tiled kernels (n_l > coarse_top)
+    int coarse_top = 0;      // first level handled by the one-block coarse kernel
+    std::vector<LevelArrays<T>> lv;
+    T *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr};
+    T *x = nullptr, *q = nullptr, *z = nullptr;
+};
+
+struct Partials { double *rr, *rz, *pq, *res; int ntiles; };
+
+struct Ctx;
+
+// kernels / launchers (defined in the .cu files)
+void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t purpose);
+void launch_synth2d(Ctx& c, const double* X, int count, double* U);
+void launch_setup_coeffs(Ctx& c, int count);
+template <typename T> void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count);
+int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w_out);
+void launch_observe(Ctx& c, const double* w, int count, double* Phi);
+void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w_out);
+void launch_move_tables(Ctx& c);
+void launch_propose(Ctx& c);
+void launch_accept(Ctx& c, int* acc_count);
+void launch_temper(Ctx& c, double* out5);
+void launch_resample(Ctx& c);
+double gm_fit_device(Ctx& c);
+void launch_moments(Ctx& c, double* mean, double* var);
+void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
+
+struct Ctx {
+    smc_config cfg;
+    std::vector<double> obs_h, data_h;
+    cudaStream_t stream = nullptr;
+    int dim = 2, n = 0, Km = 0, d = 0, N = 0, K = 1, r = 1, nobs = 0, B = 0;
+    Key key{0, 0};
+    // prior, basis and problem tables
+    double *lam = nullptr, *sqrtlam = nullptr, *basis = nullptr, *b64 = nullptr, *obs = nullptr, *data = nullptr;
+    int *S = nullptr, *slot = nullptr;
+    // particle state
+    double *X = nullptr, *X2 = nullptr, *V = nullptr, *Phi = nullptr, *Phi2 = nullptr, *PhiV = nullptr;
+    double *logw = nullptr, *logalpha = nullptr, *lfwd = nullptr, *lrev = nullptr;
+    unsigned char* acc = nullptr;
+    int* idx = nullptr;
+    int* icount = nullptr;     // small device integer scratch
+    double* dscal = nullptr;   // small device double scratch (temper outputs etc.)
+    // mixture and proposal tables
+    double *gw = nullptr, *gmu = nullptr, *glam = nullptr;
+    double *tab = nullptr;     // per (j, s): c0, a, mu, sq; then per s: b; then per j: log w, cumulative w
+    // EM scratch
+    double *xsT = nullptr, *resp = nullptr, *nj = nullptr, *pooled = nullptr, *lse = nullptr, *gmax = nullptr;
+    // forward-solve batch arrays
+    double *u64 = nullptr, *Kw64 = nullptr, *Ks64 = nullptr, *E64 = nullptr, *N64 = nullptr, *w64 = nullptr;
+    InnerSolver<float> s32;
+    InnerSolver<double> s64;
+    Partials part{};
+    SolverScalars sc{};
+    // moments scratch
+    double* gridtmp = nullptr;
+    // host state
+    double t = 0.0, beta = 0.2;
+    int layer = 0;
+    unsigned int step = 0;
+    int stage = 0;             // 0 uninitialised, 1 ready for temper, 2 tempered, 3 resampled
+    bool fitted = false;
+    int last_iters = 0;
+    long long nonconv = 0;
+    // profiling counters (see smc_profile in smcgm.h)
+    bool prof = false;
+    smc_profile pc{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+// status helper
+struct CudaError { cudaError_t e; const char* what; };
+void check(cudaError_t e, const char* what);   // throws CudaError
+
+constexpr int TILE = 32;          // inner tile edge of the tiled multigrid kernels
+constexpr int MAXK = 16;          // max mixture components
+constexpr int MAXR = 256;         // max mixture modes
+
+}  // namespace smcgm
+
+struct smc_ctx { smcgm::Ctx c; };

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libsmcgm.so (include/smcgm.h): argument marshalling
+only -- every step of the particle move runs in the library's CUDA kernels.
+
+The library must have been built (``paper_2503_16028_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmcgm.so")
+
+SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ENOCONV, SMC_EDEGENERATE, SMC_ESTATE = range(7)
+SMC_K_PCN, SMC_K_PCN_GM, SMC_K_GM_INDEP = range(3)
+SMC_P_FP64, SMC_P_FP32_REFINE = range(2)
+STATUS_NAMES = ["SMC_OK", "SMC_EINVAL", "SMC_ENOMEM", "SMC_ECUDA", "SMC_ENOCONV", "SMC_EDEGENERATE", "SMC_ESTATE"]
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class smc_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("kl_modes", ctypes.c_int), ("alpha", ctypes.c_double),
+        ("n_obs", ctypes.c_int), ("obs", _dp), ("data", _dp), ("sigma", ctypes.c_double),
+        ("source_kind", ctypes.c_int), ("src_amp", ctypes.c_double), ("src_width", ctypes.c_double),
+        ("n_particles", ctypes.c_int), ("n_components", ctypes.c_int), ("gm_rank", ctypes.c_int), ("em_iters", ctypes.c_int),
+        ("var_floor", ctypes.c_double), ("beta0", ctypes.c_double), ("ess_frac", ctypes.c_double),
+        ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("tol_inner", ctypes.c_double), ("tol_outer", ctypes.c_double),
+        ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int),
+        ("coarse_scale", ctypes.c_double), ("solve_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+    ]
+
+
+class smc_profile(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_longlong), ("cg_iterations", ctypes.c_longlong), ("inner_solves", ctypes.c_longlong),
+                ("residuals", ctypes.c_longlong), ("dom_launches", ctypes.c_longlong), ("dom_particles", ctypes.c_longlong),
+                ("dom_ms", ctypes.c_double), ("dom_bytes", ctypes.c_double), ("cells", ctypes.c_int),
+                ("word_bytes", ctypes.c_int)]
+
+
+EXPORTS = {
+    "smc_config_init": (ctypes.c_int, [ctypes.POINTER(smc_config)]),
+    "smc_workspace_size": (ctypes.c_int, [ctypes.POINTER(smc_config), ctypes.POINTER(ctypes.c_size_t)]),
+    "smc_init": (ctypes.c_int, [ctypes.POINTER(smc_config), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    "smc_temper_step": (ctypes.c_int, [_vp, _dp, _dp, _dp, _ip]),
+    "smc_resample": (ctypes.c_int, [_vp]),
+    "gm_fit": (ctypes.c_int, [_vp, _dp]),
+    "smc_move": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _ip]),
+    "smc_move_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _dp]),
+    "smc_posterior_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "smc_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _ip]),
+    "smc_get_particles": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "smc_set_particles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "smc_set_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint]),
+    "smc_get_schedule": (ctypes.c_int, [_vp, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_uint)]),
+    "smc_set_mixture": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "smc_get_mixture": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "smc_get_diagnostics": (ctypes.c_int, [_vp] + [ctypes.POINTER(_vp)] * 5),
+    "smc_save": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "smc_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "smc_last_error": (ctypes.c_char_p, [_vp]),
+    "smc_destroy": (None, [_vp]),
+    "smc_version": (ctypes.c_char_p, []),
+    "smc_config_size": (ctypes.c_size_t, []),
+    "smc_profile_query": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(smc_profile), ctypes.c_int]),
+    "smc_copy_to_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t]),
+}
+
+_LIB = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsmcgm.so and declare every export; raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError("libsmcgm.so not found at %s: build it with paper_2503_16028_gb300.build.build() "
+                          "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.smc_config_size() != ctypes.sizeof(smc_config):
+        raise ImportError("smc_config layout mismatch between libsmcgm.so and the binding")
+    _LIB = lib
+    return lib
+
+
+class SMCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, address of a numpy array, or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_config(preset, **overrides):
+    """smc_config from a dict (inputs.PRESETS entry merged with obs/data arrays); keeps the arrays alive."""
+    lib = load_library()
+    cfg = smc_config()
+    lib.smc_config_init(ctypes.byref(cfg))
+    p = dict(preset)
+    p.update(overrides)
+    obs = np.ascontiguousarray(np.asarray(p["obs"], dtype=np.float64).reshape(-1))
+    data = np.ascontiguousarray(np.asarray(p["data"], dtype=np.float64))
+    cfg.dim = p["dim"]; cfg.n = p["n"]; cfg.kl_modes = p["kl_modes"]; cfg.alpha = p["alpha"]
+    cfg.n_obs = data.shape[0]
+    cfg.obs = obs.ctypes.data_as(_dp); cfg.data = data.ctypes.data_as(_dp); cfg.sigma = p["sigma"]
+    cfg.source_kind = p["source_kind"]; cfg.src_amp = p["src_amp"]; cfg.src_width = p["src_width"]
+    cfg.n_particles = p["n_particles"]; cfg.n_components = p["n_components"]; cfg.gm_rank = p["gm_rank"]
+    cfg.beta0 = p["beta0"]; cfg.ess_frac = p["ess_frac"]; cfg.seed = p["seed"]
+    for key in ("em_iters", "var_floor", "kernel", "precision", "tol_inner", "tol_outer", "max_iter", "max_refine",
+                "smooth_sweeps", "coarse_scale", "solve_batch"):
+        if key in p:
+            setattr(cfg, key, p[key])
+    cfg._keep = (obs, data)
+    return cfg
+
+
+class Sampler:
+    """One smc_ctx with its caller-owned device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, cfg, device="cuda:0", stream=None):
+        import torch
+        self.lib = load_library()
+        self.cfg = cfg
+        size = ctypes.c_size_t()
+        self._check(self.lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)), None)
+        self.ws = torch.empty(size.value + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        ctx = ctypes.c_void_p()
+        st = self.lib.smc_init(ctypes.byref(cfg), ctypes.c_void_p(aligned), size.value,
+                               ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        if st != SMC_OK:
+            raise SMCError(st, self.lib.smc_last_error(None).decode())
+        self.ctx = ctx
+        self.d = cfg.kl_modes ** 2 if cfg.dim == 2 else cfg.kl_modes
+        self.N = cfg.n_particles
+        self.K = 1 if cfg.kernel == SMC_K_PCN else cfg.n_components
+        self.r = min(cfg.gm_rank, self.d)
+
+    def _check(self, st, ctx, allow=()):
+        if st != SMC_OK and st not in allow:
+            msg = self.lib.smc_last_error(ctx).decode() if ctx is not None else ""
+            raise SMCError(st, msg)
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.smc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- SMC steps -------------------------------------------------------
+    def smc_temper_step(self):
+        h, ess, lz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        done = ctypes.c_int()
+        self._check(self.lib.smc_temper_step(self.ctx, ctypes.byref(h), ctypes.byref(ess), ctypes.byref(lz),
+                                             ctypes.byref(done)), self.ctx)
+        return h.value, ess.value, lz.value, bool(done.value)
+
+    def smc_resample(self):
+        self._check(self.lib.smc_resample(self.ctx), self.ctx)
+
+    def gm_fit(self):
+        ll = ctypes.c_double()
+        self._check(self.lib.gm_fit(self.ctx, ctypes.byref(ll)), self.ctx)
+        return ll.value
+
+    def smc_move(self, steps=1, allow_noconv=False):
+        acc, it = ctypes.c_double(), ctypes.c_int()
+        st = self._check(self.lib.smc_move(self.ctx, steps, ctypes.byref(acc), ctypes.byref(it)), self.ctx,
+                         allow=(SMC_ENOCONV,) if allow_noconv else ())
+        return acc.value, it.value
+
+    def smc_move_host(self, X_in, Phi_in, X_out, Phi_out):
+        acc = ctypes.c_double()
+        self._check(self.lib.smc_move_host(self.ctx, _ptr(X_in), _ptr(Phi_in), _ptr(X_out), _ptr(Phi_out),
+                                           ctypes.byref(acc)), self.ctx)
+        return acc.value
+
+    def smc_posterior_moments(self, grid=False):
+        mean = np.empty(self.d); var = np.empty(self.d)
+        cells = (self.cfg.n ** 2) if self.cfg.dim == 2 else self.cfg.n
+        mg = np.empty(cells) if grid else None
+        vg = np.empty(cells) if grid else None
+        self._check(self.lib.smc_posterior_moments(self.ctx, _ptr(mean), _ptr(var), _ptr(mg), _ptr(vg)), self.ctx)
+        return (mean, var, mg, vg) if grid else (mean, var)
+
+    def smc_forward(self, X_dev, Phi_dev, w_dev=None):
+        it = ctypes.c_int()
+        self._check(self.lib.smc_forward(self.ctx, _ptr(X_dev), int(X_dev.shape[0]), _ptr(Phi_dev), _ptr(w_dev),
+                                         ctypes.byref(it)), self.ctx)
+        return it.value
+
+    # --- state access ----------------------------------------------------
+    def particles(self):
+        """(X, Phi) copied to host numpy arrays."""
+        xp, pp = ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(self.lib.smc_get_particles(self.ctx, ctypes.byref(xp), ctypes.byref(pp)), self.ctx)
+        return self.to_host(xp.value, self.N * self.d).reshape(self.N, self.d), self.to_host(pp.value, self.N)
+
+    def smc_set_particles(self, X, Phi=None):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Phi = None if Phi is None else np.ascontiguousarray(Phi, dtype=np.float64)
+        self._check(self.lib.smc_set_particles(self.ctx, _ptr(X), _ptr(Phi), 0), self.ctx)
+
+    def smc_set_schedule(self, t, beta, layer, step):
+        self._check(self.lib.smc_set_schedule(self.ctx, t, beta, layer, step), self.ctx)
+
+    def smc_get_schedule(self):
+        t, b, l, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_int(), ctypes.c_uint()
+        self._check(self.lib.smc_get_schedule(self.ctx, ctypes.byref(t), ctypes.byref(b), ctypes.byref(l), ctypes.byref(s)), self.ctx)
+        return t.value, b.value, l.value, s.value
+
+    def smc_set_mixture(self, w, m, lam):
+        w = np.ascontiguousarray(w, dtype=np.float64); m = np.ascontiguousarray(m, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self._check(self.lib.smc_set_mixture(self.ctx, _ptr(w), _ptr(m), _ptr(lam)), self.ctx)
+
+    def smc_get_mixture(self):
+        w = np.empty(self.K); m = np.empty((self.K, self.r)); lam = np.empty((self.K, self.r))
+        modes = np.empty(self.r, dtype=np.int32)
+        self._check(self.lib.smc_get_mixture(self.ctx, _ptr(w), _ptr(m), _ptr(lam), _ptr(modes)), self.ctx)
+        return w, m, lam, modes
+
+    def diagnostics(self):
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        self._check(self.lib.smc_get_diagnostics(self.ctx, *[ctypes.byref(p) for p in ptrs]), self.ctx)
+        la = self.to_host(ptrs[0].value, self.N)
+        acc = self.to_host(ptrs[1].value, self.N, np.uint8)
+        pv = self.to_host(ptrs[2].value, self.N)
+        lw = self.to_host(ptrs[3].value, self.N)
+        idx = self.to_host(ptrs[4].value, self.N, np.int32)
+        return dict(log_alpha=la, accepted=acc.astype(bool), phi_proposed=pv, logw=lw, indices=idx)
+
+    def smc_profile_query(self, enable=-1, reset=False):
+        out = smc_profile()
+        self._check(self.lib.smc_profile_query(self.ctx, enable, ctypes.byref(out), int(reset)), self.ctx)
+        return {k: getattr(out, k) for k, _ in smc_profile._fields_}
+
+    def smc_save(self):
+        size = ctypes.c_size_t()
+        self._check(self.lib.smc_save(self.ctx, None, ctypes.byref(size)), self.ctx)
+        buf = np.empty(size.value, dtype=np.uint8)
+        self._check(self.lib.smc_save(self.ctx, _ptr(buf), ctypes.byref(size)), self.ctx)
+        return buf
+
+    def smc_load(self, buf):
+        self._check(self.lib.smc_load(self.ctx, _ptr(buf), buf.nbytes), self.ctx)
+
+    def to_host(self, ptr, count, dtype=np.float64):
+        """Copy `count` elements at a device address into a new numpy array (smc_copy_to_host)."""
+        out = np.empty(count, dtype=dtype)
+        self._check(self.lib.smc_copy_to_host(self.ctx, _ptr(out), ctypes.c_void_p(ptr), out.nbytes), self.ctx)
+        return out

@@ -1,0 +1,72 @@
+"""The C ABI library builds, loads and exports every entry point that
+include/smcgm.h declares; host-only calls (no GPU work) behave as documented."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc unavailable")
+    from paper_2503_16028_gb300 import build, smcgm
+    build.build()
+    return smcgm.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "smcgm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(smc_[a-z_0-9]+|gm_fit)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2503_16028_gb300 import smcgm
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in smcgm.EXPORTS, "binding lacks " + n
+
+
+def test_config_layout_and_defaults(lib):
+    from paper_2503_16028_gb300 import smcgm
+    assert lib.smc_config_size() == ctypes.sizeof(smcgm.smc_config)
+    cfg = smcgm.smc_config()
+    assert lib.smc_config_init(ctypes.byref(cfg)) == 0
+    assert cfg.dim == 2 and cfg.smooth_sweeps == 2 and cfg.coarse_scale == 2.0
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_2503_16028_gb300 import inputs, smcgm
+    wl = inputs.load_workload("darcy256_precision")
+    cfg = smcgm.make_config(wl)
+    size = ctypes.c_size_t()
+    assert lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)) == 0
+    n, N = 256, 4096
+    # at least: particles (3 N d FP64) + FP64 coefficients/solution + FP32 CG vectors
+    assert size.value > 3 * N * 128 * 128 * 8 + 4 * N * n * n * 8 + 7 * N * n * n * 4
+    assert size.value < 64 << 30
+    bad = smcgm.make_config(wl, n=200)
+    assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    bad = smcgm.make_config(wl, n_particles=40000)
+    assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    obs = np.array([[0.5, 1.5]])
+    bad = smcgm.make_config(dict(wl, obs=obs, data=np.zeros(1)))
+    assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+
+
+def test_init_rejects_small_workspace_without_touching_the_gpu(lib):
+    from paper_2503_16028_gb300 import inputs, smcgm
+    wl = inputs.load_workload("darcy64_bimodal")
+    cfg = smcgm.make_config(wl)
+    ctx = ctypes.c_void_p()
+    assert lib.smc_init(ctypes.byref(cfg), ctypes.c_void_p(256), 1024, None, ctypes.byref(ctx)) == smcgm.SMC_ENOMEM
+    assert b"workspace" in lib.smc_last_error(None)
+    assert lib.smc_temper_step(None, None, None, None, None) == smcgm.SMC_EINVAL
