@@ -82,7 +82,8 @@ typedef struct smc_config {
     double tol_outer;   /* final FP64 relative residual |b - A w| / |b| */
     int max_iter;       /* CG iterations per inner solve */
     int max_refine;     /* refinement (outer) iterations */
-    int smooth_sweeps;  /* red-black Gauss-Seidel sweeps per pre/post smoothing (1 or 2) */
+    int smooth_sweeps;  /* red-black Gauss-Seidel sweeps per pre/post smoothing on coarse levels (1 or 2) */
+    int fine_sweeps;    /* the same on the finest level (1 or 2; used when smooth_sweeps = 2) */
     double coarse_scale;/* multigrid coarse-correction factor */
     int solve_batch;    /* particles per forward-solve batch (0: all N) */
     unsigned long long seed;

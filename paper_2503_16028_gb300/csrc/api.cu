@@ -57,6 +57,7 @@ static const char* validate(const smc_config& c) {
     if (!(c.tol_inner > 0 && c.tol_inner < 1) || !(c.tol_outer > 0 && c.tol_outer < 1)) return "tolerances must be in (0, 1)";
     if (c.max_iter < 1 || c.max_refine < 1) return "max_iter and max_refine must be >= 1";
     if (c.smooth_sweeps != 1 && c.smooth_sweeps != 2) return "smooth_sweeps must be 1 or 2";
+    if (c.fine_sweeps != 1 && c.fine_sweeps != 2) return "fine_sweeps must be 1 or 2";
     if (!(c.coarse_scale > 0 && c.coarse_scale <= 2.5)) return "coarse_scale must be in (0, 2.5]";
     if (c.solve_batch < 0) return "solve_batch must be >= 0";
     for (int i = 0; i < c.n_obs * c.dim; ++i)
@@ -88,6 +89,7 @@ static void plan_inner(Planner& P, InnerSolver<T>& s, int n, int B, int coarse_t
         L.e = P.take<T>(cells);
         if (l > 0) { L.r = P.take<T>(cells); L.e2 = P.take<T>(cells); }
     }
+    s.list = P.take<int>(B); s.nact = P.take<int>(4);
     s.r[0] = P.take<T>(nn); s.r[1] = P.take<T>(nn);
     s.p[0] = P.take<T>(nn); s.p[1] = P.take<T>(nn);
     s.x = P.take<T>(nn); s.q = P.take<T>(nn); s.z = P.take<T>(nn);
@@ -116,7 +118,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     C.logw = P.take<double>(N); C.logalpha = P.take<double>(N);
     C.lfwd = P.take<double>((size_t)N * K); C.lrev = P.take<double>((size_t)N * K);
     C.acc = P.take<unsigned char>(N); C.idx = P.take<int>(N);
-    C.icount = P.take<int>(64); C.dscal = P.take<double>(64);
+    C.icount = P.take<int>(64); C.dscal = P.take<double>(64); C.dev_err = P.take<int>(4);
     C.gw = P.take<double>(K); C.gmu = P.take<double>((size_t)K * r); C.glam = P.take<double>((size_t)K * r);
     C.tab = P.take<double>(4 * (size_t)K * r + r + 2 * K);
     C.xsT = P.take<double>((size_t)r * N); C.resp = P.take<double>((size_t)K * N); C.nj = P.take<double>(K);
@@ -128,7 +130,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
         C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
         C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
         C.w64 = P.take<double>(bn);
-        const int ntiles = (n / TILE) * (n / TILE);
+        const int ntiles = (n / 16) * (n / 16);   // the finest tiled level's tiles (16 x 16 warp tiles or fewer)
         C.part.ntiles = ntiles;
         C.part.rr = P.take<double>((size_t)B * ntiles); C.part.rz = P.take<double>((size_t)B * ntiles);
         C.part.pq = P.take<double>((size_t)B * ntiles); C.part.res = P.take<double>((size_t)B * ntiles);
@@ -275,7 +277,7 @@ smc_status smc_config_init(smc_config* cfg) {
     cfg->n_particles = 1024; cfg->n_components = 4; cfg->gm_rank = 64; cfg->em_iters = 50; cfg->var_floor = 1e-3;
     cfg->beta0 = 0.2; cfg->ess_frac = 0.5; cfg->kernel = SMC_K_PCN_GM; cfg->precision = SMC_P_FP32_REFINE;
     cfg->tol_inner = 1e-5; cfg->tol_outer = 1e-10; cfg->max_iter = 60; cfg->max_refine = 6;
-    cfg->smooth_sweeps = 2; cfg->coarse_scale = 2.0; cfg->solve_batch = 0; cfg->seed = 2503016028ull;
+    cfg->smooth_sweeps = 2; cfg->fine_sweeps = 1; cfg->coarse_scale = 2.0; cfg->solve_batch = 0; cfg->seed = 2503016028ull;
     return SMC_OK;
 }
 
@@ -321,7 +323,17 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     check(cudaMemcpyAsync(c.data, c.data_h.data(), c.data_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.S, S.data(), S.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+    check(cudaMemsetAsync(c.dev_err, 0, 4 * sizeof(int), c.stream), "memset err");
     check(cudaStreamSynchronize(c.stream), "sync");
+    {
+        int dev = 0;
+        check(cudaGetDevice(&dev), "device");
+        check(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    }
+    if (c.dim == 2) {
+        if (c.cfg.precision == SMC_P_FP32_REFINE) build_tma_maps<float>(c, c.s32);
+        else build_tma_maps<double>(c, c.s64);
+    }
     set_prior_mixture(c);
     c.fitted = (c.cfg.kernel == SMC_K_PCN);
     c.t = 0.0;
@@ -351,6 +363,8 @@ void smc_destroy(smc_ctx* ctx) {
     if (!ctx) return;
     if (ctx->c.ev0) cudaEventDestroy(ctx->c.ev0);
     if (ctx->c.ev1) cudaEventDestroy(ctx->c.ev1);
+    delete ctx->c.s32.maps;
+    delete ctx->c.s64.maps;
     delete ctx;
 }
 

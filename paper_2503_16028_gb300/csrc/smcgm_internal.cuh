@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libsmcgm.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -65,8 +66,18 @@ struct SolverScalars {       // per particle, device
     int *count;              // [0] active inner count, [1] active outer count, [2] max iters
 };
 
+// TMA descriptors of the tiled levels (boxes described in tiles.cuh).
+struct TmaMaps {
+    CUtensorMap kw[12], ks[12], r[12], e[12], ec[12];   // per tiled level
+    CUtensorMap r0[2], q, x, p[2];                       // finest level, CG vectors
+    CUtensorMap kwa, ksa, za, pa[2];                      // finest level, operator application
+};
+
 template <typename T>
 struct InnerSolver {
+    TmaMaps* maps = nullptr;
+    int* list = nullptr;     // active particle indices (device)
+    int* nact = nullptr;     // their count (device)
     int nlev = 0;            // number of levels down to 1 x 1
     int ntile_levels = 0;    // levels handled by the tiled kernels (n_l > coarse_top)
     int coarse_top = 0;      // first level handled by the one-block coarse kernel
@@ -84,6 +95,7 @@ void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t pur
 void launch_synth2d(Ctx& c, const double* X, int count, double* U);
 void launch_setup_coeffs(Ctx& c, int count);
 template <typename T> void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count);
+template <typename T> void build_tma_maps(Ctx& c, InnerSolver<T>& s);
 int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w_out);
 void launch_observe(Ctx& c, const double* w, int count, double* Phi);
 void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w_out);
@@ -137,6 +149,8 @@ struct Ctx {
     bool prof = false;
     smc_profile pc{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int* dev_err = nullptr;    // device flag set by kernels whose bounded waits time out
+    int sm_count = 0;
     std::string err;
 };
 

@@ -21,8 +21,10 @@
 // particle entirely in shared memory.
 #include <cstdio>
 #include <algorithm>
+#include <cudaTypedefs.h>
 #include "smcgm_internal.cuh"
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace smcgm {
 
@@ -91,296 +93,290 @@ __global__ void k_coarsen(int m, int count, const T* __restrict__ Kw, const T* _
 }
 
 // ------------------------------------------------------------------------
-// Tiled smoothing kernels.  Shared layout for a region of R x R cells
-// (R = TILE + 2H): r, e, D (R*R each), Kw (R rows of R+1), Ks (R+1 rows of R).
+// Tiled smoothing kernels.  A block covers a TILE x TILE tile of one particle
+// plus a halo of H cells, a region of R x R cells (R = TILE + 2H).  Thread t
+// (t < R*G) owns the region cells in column lx = t % R and rows
+// ly = t / R + G k; G is odd, so a thread's cells alternate in colour and every
+// half-sweep keeps all threads busy.  The owned cells' right-hand side, face
+// coefficients and 1/D live in registers; only the correction e is shared.
+// A half-sweep over [lo, hi)^2 is exact there as long as lo >= s for the s-th
+// half-sweep (the halo shrinks by one cell per half-sweep).
 // ------------------------------------------------------------------------
-template <typename T>
-struct TileSmem {
-    T *r, *e, *d, *kw, *ks;
-    __device__ TileSmem(T* base, int R) {
-        r = base; e = r + R * R; d = e + R * R; kw = d + R * R; ks = kw + R * (R + 1);
-    }
+constexpr int OWN_G = 7;
+
+template <int R>
+struct Own {
+    static constexpr int G = OWN_G;
+    static constexpr int ROWS = (R + G - 1) / G;
+    static constexpr int NT = R * G;
+    static constexpr int THREADS = ((NT + 31) / 32) * 32;
 };
 
-template <typename T>
-__host__ __device__ inline size_t tile_smem_bytes(int R) { return sizeof(T) * (size_t)(3 * R * R + 2 * R * (R + 1)); }
+template <typename T> __device__ inline T rcp_pos(T d);
+template <> __device__ inline float rcp_pos<float>(float d) { return __frcp_rn(d); }
+template <> __device__ inline double rcp_pos<double>(double d) { return recip_nr(d); }
 
-// Load the face coefficients of a region whose origin is (gx0, gy0).
-// skw(ly, lx) is the west face of region cell (lx, ly), lx = 0..R (lx = R: the
-// east face of the last column); global column n maps to the east wall E.
+// Face coefficients of global cell (gx, gy): west, east, south, north (walls at the domain edge).
 template <typename T>
-__device__ inline void load_faces(TileSmem<T>& sm, int R, int n, int gx0, int gy0, const T* __restrict__ Kw,
-                                  const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn) {
-    for (int idx = threadIdx.x; idx < R * (R + 1); idx += blockDim.x) {
-        int ly = idx / (R + 1), lx = idx - ly * (R + 1);
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T v = T(0);
-        if (gy >= 0 && gy < n) {
-            if (gx >= 0 && gx < n) v = Kw[gy * n + gx];
-            else if (gx == n) v = E[gy];
-        }
-        sm.kw[ly * (R + 1) + lx] = v;
-    }
-    for (int idx = threadIdx.x; idx < (R + 1) * R; idx += blockDim.x) {
-        int ly = idx / R, lx = idx - ly * R;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T v = T(0);
-        if (gx >= 0 && gx < n) {
-            if (gy >= 0 && gy < n) v = Ks[gy * n + gx];
-            else if (gy == n) v = Nn[gx];
-        }
-        sm.ks[ly * R + lx] = v;
-    }
+__device__ inline void load_cell_faces(const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E,
+                                       const T* __restrict__ Nn, int n, int gx, int gy, T& w, T& e, T& s, T& nn) {
+    const int c = gy * n + gx;
+    w = Kw[c];
+    e = gx + 1 < n ? Kw[c + 1] : E[gy];
+    s = Ks[c];
+    nn = gy + 1 < n ? Ks[c + n] : Nn[gx];
 }
 
-template <typename T>
-__device__ inline T nbr_sum(const TileSmem<T>& sm, int R, int lx, int ly) {
-    const int c = ly * R + lx;
-    return sm.kw[ly * (R + 1) + lx] * sm.e[c - 1] + sm.kw[ly * (R + 1) + lx + 1] * sm.e[c + 1] +
-           sm.ks[ly * R + lx] * sm.e[c - R] + sm.ks[(ly + 1) * R + lx] * sm.e[c + R];
-}
-
-// One red-black half-sweep of colour `col` over region cells [lo, hi)^2 that lie
-// in the domain; zero start allows a pointwise update when `pointwise`.
-template <typename T>
-__device__ inline void half_sweep(TileSmem<T>& sm, int R, int n, int gx0, int gy0, int lo, int hi, int col, bool pointwise) {
-    const int w = hi - lo;
-    if (w <= 0) return;
-    const int half = (w + 1) / 2;
-    for (int idx = threadIdx.x; idx < w * half; idx += blockDim.x) {
-        int ly = lo + idx / half;
-        int k = idx - (idx / half) * half;
-        // first lx in [lo, hi) with (gx0 + lx + gy0 + ly) % 2 == col
-        int lx = lo + ((((gx0 + lo + gy0 + ly) & 1) == col) ? 0 : 1) + 2 * k;
-        if (lx >= hi) continue;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        if (gx < 0 || gx >= n || gy < 0 || gy >= n) continue;
-        const int c = ly * R + lx;
-        T num = sm.r[c];
-        if (!pointwise) num += nbr_sum(sm, R, lx, ly);
-        sm.e[c] = num / sm.d[c];
-    }
-}
-
-template <typename T>
-__device__ inline void compute_diag(TileSmem<T>& sm, int R, int n, int gx0, int gy0) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-        int ly = idx / R, lx = idx - ly * R;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T dv = T(1);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n)
-            dv = sm.kw[ly * (R + 1) + lx] + sm.kw[ly * (R + 1) + lx + 1] + sm.ks[ly * R + lx] + sm.ks[(ly + 1) * R + lx];
-        sm.d[idx] = dv;
-    }
-}
-
-// Pre-smoothing + residual + restriction.  cg = 1 (finest level): first applies
-// the CG update r' = r - alpha q (whole region), x += alpha p and stores r'
-// (tile interior), accumulating |r'|^2 per tile.
 template <typename T, int NU>
-__global__ void __launch_bounds__(256) k_pre(int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E,
-                                             const T* __restrict__ Nn, const T* __restrict__ rin, T* __restrict__ rout,
-                                             T* __restrict__ e_out, T* __restrict__ rc, const T* __restrict__ q, T* __restrict__ x,
-                                             const T* __restrict__ p, const double* __restrict__ alpha, double* __restrict__ part_rr,
-                                             const int* __restrict__ active, int cg, int want_rr) {
+__global__ void __launch_bounds__(Own<TILE + 4 * NU>::THREADS) k_pre(
+        int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn,
+        const T* __restrict__ rin, T* __restrict__ rout, T* __restrict__ e_out, T* __restrict__ rc, const T* __restrict__ q,
+        T* __restrict__ x, const T* __restrict__ p, const double* __restrict__ alpha, double* __restrict__ part_rr,
+        const int* __restrict__ active, int cg, int want_rr) {
     constexpr int H = 2 * NU;
     constexpr int R = TILE + 2 * H;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    using O = Own<R>;
+    constexpr int ROWS = O::ROWS, G = O::G;
+    __shared__ T se[R * R];
     __shared__ double red[32];
-    const int pb = blockIdx.y;
-    if (!active[pb]) return;
+    const int pb = active[blockIdx.y];   // active-particle list
     const int tpr = n / TILE;
     const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
     const int gx0 = tx * TILE - H, gy0 = ty * TILE - H;
-    const size_t nn = (size_t)n * n;
-    const size_t base = (size_t)pb * nn;
-    TileSmem<T> sm(reinterpret_cast<T*>(smraw), R);
-    load_faces(sm, R, n, gx0, gy0, Kw + base, Ks + base, E + (size_t)pb * n, Nn + (size_t)pb * n);
+    const size_t base = (size_t)pb * n * n;
+    const T* kw = Kw + base;
+    const T* ks = Ks + base;
+    const T* Ep = E + (size_t)pb * n;
+    const T* Np = Nn + (size_t)pb * n;
+    const int t = threadIdx.x;
+    const bool own = t < O::NT;
+    const int lx = own ? t % R : 0, g = own ? t / R : 0;
+    const int gx = gx0 + lx;
+    const int col0 = (gx + gy0 + g) & 1;
     const T a = cg ? (T)alpha[pb] : T(0);
+    T rr[ROWS], inv[ROWS], cw[ROWS], ce[ROWS], cs[ROWS], cn[ROWS];
     double rr_loc = 0.0;
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-        int ly = idx / R, lx = idx - ly * R;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T rv = T(0);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        const int gy = gy0 + ly;
+        const bool inreg = own && ly < R;
+        const bool in = inreg && gx >= 0 && gx < n && gy >= 0 && gy < n;
+        T rv = T(0), w = T(0), e = T(0), s = T(0), nn = T(0);
+        if (in) {
             const size_t gi = base + (size_t)gy * n + gx;
             rv = rin[gi];
+            load_cell_faces(kw, ks, Ep, Np, n, gx, gy, w, e, s, nn);
+            const bool inner = lx >= H && lx < H + TILE && ly >= H && ly < H + TILE;
             if (cg) {
                 rv -= a * q[gi];
-                if (lx >= H && lx < H + TILE && ly >= H && ly < H + TILE) {
+                if (inner) {
                     rout[gi] = rv;
                     x[gi] += a * p[gi];
-                    rr_loc += (double)rv * (double)rv;
                 }
-            } else if (want_rr && lx >= H && lx < H + TILE && ly >= H && ly < H + TILE) {
-                rr_loc += (double)rv * (double)rv;
+            }
+            if (inner && (cg || want_rr)) rr_loc += (double)rv * (double)rv;
+        }
+        rr[k] = rv; cw[k] = w; ce[k] = e; cs[k] = s; cn[k] = nn;
+        inv[k] = in ? rcp_pos(w + e + s + nn) : T(0);
+        if (inreg) se[ly * R + lx] = T(0);
+    }
+    __syncthreads();
+    // NU sweeps of (red, black); the first red half-sweep starts from e = 0 and is pointwise.
+#pragma unroll
+    for (int hs = 0; hs < 2 * NU; ++hs) {
+        const int colr = hs & 1;
+        const int lo = hs, hi = R - hs;
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k) {
+            const int ly = g + G * k;
+            if (inv[k] != T(0) && ((col0 ^ (k & 1)) == colr) && lx >= lo && lx < hi && ly >= lo && ly < hi) {
+                const int c = ly * R + lx;
+                T num = rr[k];
+                if (hs > 0) num += cw[k] * se[c - 1] + ce[k] * se[c + 1] + cs[k] * se[c - R] + cn[k] * se[c + R];
+                se[c] = num * inv[k];
             }
         }
-        sm.r[idx] = rv;
-        sm.e[idx] = T(0);
+        __syncthreads();
     }
-    __syncthreads();
-    compute_diag(sm, R, n, gx0, gy0);
-    __syncthreads();
-    // NU sweeps of (red, black); the first red half-sweep starts from e = 0.
-    int s = 0;
+    // residual on the tile interior, then restriction (sum of 2 x 2)
+    T res[ROWS], ev[ROWS];
 #pragma unroll
-    for (int sw = 0; sw < NU; ++sw) {
-        half_sweep(sm, R, n, gx0, gy0, s == 0 ? 0 : s, s == 0 ? R : R - s, 0, s == 0);
-        __syncthreads();
-        ++s;
-        half_sweep(sm, R, n, gx0, gy0, s, R - s, 1, false);
-        __syncthreads();
-        ++s;
-    }
-    // residual on the interior (after 2NU half-sweeps the valid region is [2NU-1, R-2NU+1)).
-    T res[4];
-    int cnt = 0;
-    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-        int ly = H + idx / TILE, lx = H + idx % TILE;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T rv = T(0);
-        if (gx < n && gy < n) {
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        res[k] = T(0);
+        ev[k] = T(0);
+        if (own && ly >= H && ly < H + TILE && lx >= H && lx < H + TILE) {
             const int c = ly * R + lx;
-            rv = sm.r[c] - (sm.d[c] * sm.e[c] - nbr_sum(sm, R, lx, ly));
+            const T ec = se[c];
+            ev[k] = ec;
+            res[k] = rr[k] - ((cw[k] + ce[k] + cs[k] + cn[k]) * ec -
+                              (cw[k] * se[c - 1] + ce[k] * se[c + 1] + cs[k] * se[c - R] + cn[k] * se[c + R]));
         }
-        res[cnt++] = rv;
     }
     __syncthreads();
-    cnt = 0;
-    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-        int ly = H + idx / TILE, lx = H + idx % TILE;
-        sm.r[ly * R + lx] = res[cnt++];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        if (own && ly >= H && ly < H + TILE && lx >= H && lx < H + TILE) {
+            se[ly * R + lx] = res[k];
+            e_out[base + (size_t)(gy0 + ly) * n + gx] = ev[k];
+        }
     }
     __syncthreads();
-    // write e (interior) and the restricted residual (TILE/2)^2
-    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-        int ly = H + idx / TILE, lx = H + idx % TILE;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        e_out[base + (size_t)gy * n + gx] = sm.e[ly * R + lx];
-    }
+    constexpr int hT = TILE / 2;
     const int m = n / 2;
-    const int hT = TILE / 2;
-    for (int idx = threadIdx.x; idx < hT * hT; idx += blockDim.x) {
-        int J = idx / hT, I = idx % hT;
-        int lx = H + 2 * I, ly = H + 2 * J;
-        T v = sm.r[ly * R + lx] + sm.r[ly * R + lx + 1] + sm.r[(ly + 1) * R + lx] + sm.r[(ly + 1) * R + lx + 1];
-        int GX = tx * hT + I, GY = ty * hT + J;
-        rc[(size_t)pb * m * m + (size_t)GY * m + GX] = v;
+    for (int idx = t; idx < hT * hT; idx += blockDim.x) {
+        const int J = idx / hT, I = idx % hT;
+        const int c = (H + 2 * J) * R + H + 2 * I;
+        rc[(size_t)pb * m * m + (size_t)(ty * hT + J) * m + tx * hT + I] = se[c] + se[c + 1] + se[c + R] + se[c + R + 1];
     }
     if (cg || want_rr) {
-        double tot = block_sum(rr_loc, red);
-        if (threadIdx.x == 0) part_rr[(size_t)pb * gridDim.x + blockIdx.x] = tot;
+        const double tot = block_sum(rr_loc, red);
+        if (t == 0) part_rr[(size_t)pb * gridDim.x + blockIdx.x] = tot;
     }
 }
 
-// Prolongation of the coarse correction, post-smoothing (black, red) and,
-// on the finest level, the partial r.z of the CG step.
+// Prolongation of the coarse correction (scaled by cc), post-smoothing
+// (black, red) and, on the finest level, the partial r.z of the CG step.
 template <typename T, int NU>
-__global__ void __launch_bounds__(256) k_post(int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E,
-                                              const T* __restrict__ Nn, const T* __restrict__ r, const T* __restrict__ e_in,
-                                              const T* __restrict__ ec, T cc, T* __restrict__ e_out, double* __restrict__ part_rz,
-                                              const int* __restrict__ active, int cg) {
+__global__ void __launch_bounds__(Own<TILE + 4 * NU>::THREADS) k_post(
+        int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn,
+        const T* __restrict__ r, const T* __restrict__ e_in, const T* __restrict__ ec, T cc, T* __restrict__ e_out,
+        double* __restrict__ part_rz, const int* __restrict__ active, int cg) {
     constexpr int H = 2 * NU;
     constexpr int R = TILE + 2 * H;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    using O = Own<R>;
+    constexpr int ROWS = O::ROWS, G = O::G;
+    __shared__ T se[R * R];
     __shared__ double red[32];
-    const int pb = blockIdx.y;
-    if (!active[pb]) return;
+    const int pb = active[blockIdx.y];   // active-particle list
     const int tpr = n / TILE;
     const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
     const int gx0 = tx * TILE - H, gy0 = ty * TILE - H;
     const int m = n / 2;
-    const size_t nn = (size_t)n * n, base = (size_t)pb * nn, cbase = (size_t)pb * m * m;
-    TileSmem<T> sm(reinterpret_cast<T*>(smraw), R);
-    load_faces(sm, R, n, gx0, gy0, Kw + base, Ks + base, E + (size_t)pb * n, Nn + (size_t)pb * n);
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-        int ly = idx / R, lx = idx - ly * R;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T rv = T(0), ev = T(0);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+    const size_t base = (size_t)pb * n * n, cbase = (size_t)pb * m * m;
+    const T* kw = Kw + base;
+    const T* ks = Ks + base;
+    const T* Ep = E + (size_t)pb * n;
+    const T* Np = Nn + (size_t)pb * n;
+    const int t = threadIdx.x;
+    const bool own = t < O::NT;
+    const int lx = own ? t % R : 0, g = own ? t / R : 0;
+    const int gx = gx0 + lx;
+    const int col0 = (gx + gy0 + g) & 1;
+    T rr[ROWS], inv[ROWS], cw[ROWS], ce[ROWS], cs[ROWS], cn[ROWS];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        const int gy = gy0 + ly;
+        const bool inreg = own && ly < R;
+        const bool in = inreg && gx >= 0 && gx < n && gy >= 0 && gy < n;
+        T rv = T(0), w = T(0), e = T(0), s = T(0), nn = T(0), ev = T(0);
+        if (in) {
             const size_t gi = base + (size_t)gy * n + gx;
             rv = r[gi];
             ev = e_in[gi] + cc * ec[cbase + (size_t)(gy >> 1) * m + (gx >> 1)];
+            load_cell_faces(kw, ks, Ep, Np, n, gx, gy, w, e, s, nn);
         }
-        sm.r[idx] = rv;
-        sm.e[idx] = ev;
+        rr[k] = rv; cw[k] = w; ce[k] = e; cs[k] = s; cn[k] = nn;
+        inv[k] = in ? rcp_pos(w + e + s + nn) : T(0);
+        if (inreg) se[ly * R + lx] = ev;
     }
     __syncthreads();
-    compute_diag(sm, R, n, gx0, gy0);
-    __syncthreads();
-    int s = 1;
 #pragma unroll
-    for (int sw = 0; sw < NU; ++sw) {
-        half_sweep(sm, R, n, gx0, gy0, s, R - s, 1, false);
+    for (int hs = 0; hs < 2 * NU; ++hs) {
+        const int colr = 1 - (hs & 1);
+        const int lo = hs + 1, hi = R - hs - 1;
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k) {
+            const int ly = g + G * k;
+            if (inv[k] != T(0) && ((col0 ^ (k & 1)) == colr) && lx >= lo && lx < hi && ly >= lo && ly < hi) {
+                const int c = ly * R + lx;
+                se[c] = (rr[k] + cw[k] * se[c - 1] + ce[k] * se[c + 1] + cs[k] * se[c - R] + cn[k] * se[c + R]) * inv[k];
+            }
+        }
         __syncthreads();
-        ++s;
-        half_sweep(sm, R, n, gx0, gy0, s, R - s, 0, false);
-        __syncthreads();
-        ++s;
     }
     double rz = 0.0;
-    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-        int ly = H + idx / TILE, lx = H + idx % TILE;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        const int c = ly * R + lx;
-        T ev = sm.e[c];
-        e_out[base + (size_t)gy * n + gx] = ev;
-        if (cg) rz += (double)sm.r[c] * (double)ev;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        if (own && ly >= H && ly < H + TILE && lx >= H && lx < H + TILE) {
+            const T ev = se[ly * R + lx];
+            e_out[base + (size_t)(gy0 + ly) * n + gx] = ev;
+            if (cg) rz += (double)rr[k] * (double)ev;
+        }
     }
     if (cg) {
-        double tot = block_sum(rz, red);
-        if (threadIdx.x == 0) part_rz[(size_t)pb * gridDim.x + blockIdx.x] = tot;
+        const double tot = block_sum(rz, red);
+        if (t == 0) part_rz[(size_t)pb * gridDim.x + blockIdx.x] = tot;
     }
 }
 
 // CG direction update and operator application: p <- z + beta p, q = A p, partial p.q.
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E,
-                                               const T* __restrict__ Nn, const T* __restrict__ z, const T* __restrict__ pin,
-                                               T* __restrict__ pout, T* __restrict__ q, const double* __restrict__ betac,
-                                               double* __restrict__ part_pq, const int* __restrict__ active, int first) {
+__global__ void __launch_bounds__(Own<TILE + 2>::THREADS) k_apply(
+        int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn,
+        const T* __restrict__ z, const T* __restrict__ pin, T* __restrict__ pout, T* __restrict__ q,
+        const double* __restrict__ betac, double* __restrict__ part_pq, const int* __restrict__ active, int first) {
     constexpr int H = 1;
     constexpr int R = TILE + 2 * H;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    using O = Own<R>;
+    constexpr int ROWS = O::ROWS, G = O::G;
+    __shared__ T se[R * R];
     __shared__ double red[32];
-    const int pb = blockIdx.y;
-    if (!active[pb]) return;
+    const int pb = active[blockIdx.y];   // active-particle list
     const int tpr = n / TILE;
     const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
     const int gx0 = tx * TILE - H, gy0 = ty * TILE - H;
-    const size_t nn = (size_t)n * n, base = (size_t)pb * nn;
-    TileSmem<T> sm(reinterpret_cast<T*>(smraw), R);
-    load_faces(sm, R, n, gx0, gy0, Kw + base, Ks + base, E + (size_t)pb * n, Nn + (size_t)pb * n);
+    const size_t base = (size_t)pb * n * n;
+    const int t = threadIdx.x;
+    const bool own = t < O::NT;
+    const int lx = own ? t % R : 0, g = own ? t / R : 0;
+    const int gx = gx0 + lx;
     const T b = first ? T(0) : (T)betac[pb];
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-        int ly = idx / R, lx = idx - ly * R;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        T pv = T(0);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-            const size_t gi = base + (size_t)gy * n + gx;
-            pv = z[gi];
-            if (!first) pv += b * pin[gi];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        const int gy = gy0 + ly;
+        if (own && ly < R) {
+            T pv = T(0);
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                const size_t gi = base + (size_t)gy * n + gx;
+                pv = z[gi];
+                if (!first) pv += b * pin[gi];
+            }
+            se[ly * R + lx] = pv;
         }
-        sm.e[idx] = pv;
     }
     __syncthreads();
     double pq = 0.0;
-    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-        int ly = H + idx / TILE, lx = H + idx % TILE;
-        int gx = gx0 + lx, gy = gy0 + ly;
-        const int c = ly * R + lx;
-        T dv = sm.kw[ly * (R + 1) + lx] + sm.kw[ly * (R + 1) + lx + 1] + sm.ks[ly * R + lx] + sm.ks[(ly + 1) * R + lx];
-        T pv = sm.e[c];
-        T qv = dv * pv - nbr_sum(sm, R, lx, ly);
-        const size_t gi = base + (size_t)gy * n + gx;
-        pout[gi] = pv;
-        q[gi] = qv;
-        pq += (double)pv * (double)qv;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int ly = g + G * k;
+        if (own && ly >= H && ly < H + TILE && lx >= H && lx < H + TILE) {
+            const int gy = gy0 + ly;
+            T w, e, s, nn;
+            load_cell_faces(Kw + base, Ks + base, E + (size_t)pb * n, Nn + (size_t)pb * n, n, gx, gy, w, e, s, nn);
+            const int c = ly * R + lx;
+            const T pv = se[c];
+            const T qv = (w + e + s + nn) * pv - (w * se[c - 1] + e * se[c + 1] + s * se[c - R] + nn * se[c + R]);
+            const size_t gi = base + (size_t)gy * n + gx;
+            pout[gi] = pv;
+            q[gi] = qv;
+            pq += (double)pv * (double)qv;
+        }
     }
-    double tot = block_sum(pq, red);
-    if (threadIdx.x == 0) part_pq[(size_t)pb * gridDim.x + blockIdx.x] = tot;
+    const double tot = block_sum(pq, red);
+    if (t == 0) part_pq[(size_t)pb * gridDim.x + blockIdx.x] = tot;
 }
+
+}  // namespace smcgm
+#include "tiles.cuh"
+#include "quads.cuh"
+#include "wtiles.cuh"
+namespace smcgm {
 
 // ------------------------------------------------------------------------
 // Coarse V-cycle: levels with n_l <= coarse_top, one block per particle, all
@@ -428,8 +424,7 @@ __device__ inline void chalf(const T* kw, const T* ks, const T* E, const T* Nn, 
 template <typename T, int NU>
 __global__ void __launch_bounds__(256) k_coarse(CoarseLevelPtrs<T> P, T cc, const int* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int pb = blockIdx.x;
-    if (!active[pb]) return;
+    const int pb = active[blockIdx.x];   // active-particle list
     T* kw[12]; T* ks[12]; T* E[12]; T* Nn[12]; T* r[12]; T* e[12];
     T* cur = reinterpret_cast<T*>(smraw);
     int nl = P.ntop;
@@ -638,17 +633,187 @@ static inline int grid_for(size_t total, int block = 256) {
     return (int)std::min<size_t>(g, 152 * 64);
 }
 
+// Deterministic compaction of the active flags into a list (one block).
+__global__ void __launch_bounds__(1024) k_compact(int count, const int* __restrict__ act, int* __restrict__ list,
+                                                  int* __restrict__ nact) {
+    __shared__ int sums[1024];
+    const int chunk = (count + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * chunk, b1 = min(count, b0 + chunk);
+    int loc = 0;
+    for (int i = b0; i < b1; ++i) loc += act[i] ? 1 : 0;
+    sums[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) { const int v = sums[k]; sums[k] = run; run += v; }
+        *nact = run;
+    }
+    __syncthreads();
+    int pos = sums[threadIdx.x];
+    for (int i = b0; i < b1; ++i)
+        if (act[i]) list[pos++] = i;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        check(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q), "entry point");
+        if (q != cudaDriverEntryPointSuccess || !p) throw CudaError{cudaErrorNotSupported, "cuTensorMapEncodeTiled unavailable"};
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D map over a particle-major [B][n][n] array, box bx x by x 1 (x innermost).
+template <typename T>
+static CUtensorMap make_map(const T* base, int n, int B, int bx, int by) {
+    CUtensorMap m;
+    cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B};
+    cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(T), (cuuint64_t)n * n * sizeof(T)};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const CUresult r = tensor_map_encoder()(&m, dt, 3, const_cast<T*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
+    return m;
+}
+
+// Halo (2 nu) of the tiled level l: the finest level uses fine_sweeps, the others smooth_sweeps.
+static inline int level_halo(const Ctx& c, int l) { return 2 * (l == 0 ? c.cfg.fine_sweeps : c.cfg.smooth_sweeps); }
+
+template <typename T>
+void build_tma_maps(Ctx& c, InnerSolver<T>& s) {
+    if (!s.maps) s.maps = new TmaMaps();
+    TmaMaps& M = *s.maps;
+    const int B = c.B;
+    for (int l = 0; l < s.ntile_levels; ++l) {
+        LevelArrays<T>& L = s.lv[l];
+        const int H = level_halo(c, l);
+        const int RY = TT + 2 * H;
+        M.kw[l] = make_map(L.Kw, L.n, B, 44, RY);
+        M.ks[l] = make_map(L.Ks, L.n, B, 40, RY + 1);
+        M.e[l] = make_map(L.e, L.n, B, 40, RY);
+        if (l > 0) M.r[l] = make_map(L.r, L.n, B, 40, RY);
+        M.ec[l] = make_map(s.lv[l + 1].e2, s.lv[l + 1].n, B, 24, RY / 2);
+    }
+    LevelArrays<T>& L0 = s.lv[0];
+    const int n = L0.n;
+    const int RY0 = TT + 2 * level_halo(c, 0);
+    for (int k = 0; k < 2; ++k) {
+        M.r0[k] = make_map(s.r[k], n, B, 40, RY0);
+        M.p[k] = make_map(s.p[k], n, B, TT, TT);
+        M.pa[k] = make_map(s.p[k], n, B, ApplyStage<T>::AC, ApplyStage<T>::AR);
+    }
+    M.q = make_map(s.q, n, B, 40, RY0);
+    M.x = make_map(s.x, n, B, TT, TT);
+    M.za = make_map(s.z, n, B, ApplyStage<T>::AC, ApplyStage<T>::AR);
+    M.kwa = make_map(L0.Kw, n, B, ApplyStage<T>::FKW, TT);
+    M.ksa = make_map(L0.Ks, n, B, TT, TT + 1);
+}
+template void build_tma_maps<float>(Ctx&, InnerSolver<float>&);
+template void build_tma_maps<double>(Ctx&, InnerSolver<double>&);
+
+constexpr int PIPE_STAGES = 2;
+
+// Resident blocks per SM of a pipelined kernel (queried once, with its shared-memory opt-in).
+template <typename K>
+static int pipe_occupancy(K kernel, int threads, size_t smem) {
+    check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
+    int b = 0;
+    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem), "occupancy");
+    return std::max(1, b);
+}
+
+template <typename T, int H>
+static int qpre_blocks() {
+    static int b = pipe_occupancy(k_qpre<T, H, PIPE_STAGES>, QGeo<T, H>::THREADS, qpre_smem<T, H, PIPE_STAGES>());
+    return b;
+}
+template <typename T, int H>
+static int qpost_blocks() {
+    static int b = pipe_occupancy(k_qpost<T, H, PIPE_STAGES>, QGeo<T, H>::THREADS, qpost_smem<T, H, PIPE_STAGES>());
+    return b;
+}
+template <typename T>
+static int apply_blocks() {
+    static int b = pipe_occupancy(k_apply_tma<T, PIPE_STAGES>, 256, apply_tma_smem<T, PIPE_STAGES>());
+    return b;
+}
+
+static inline int persistent_grid(int total, int per_sm, int sms) { return std::max(1, std::min(total, per_sm * sms)); }
+
+// Pre-smoothing pass on tiled level `level` (halo H); cg = 1 only on the finest level.
+template <typename T, int H>
+static void launch_qpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const CUtensorMap& mr, T* rout, int cg, int want_rr,
+                        const CUtensorMap* mp) {
+    LevelArrays<T>& L = s.lv[level];
+    TmaMaps& M = *s.maps;
+    QPreArgs<T> a{};
+    a.pc.n = L.n; a.pc.ntiles = (L.n / TT) * (L.n / TT); a.pc.total = nact * a.pc.ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
+    a.E = L.E; a.Nn = L.Nn; a.rout = rout; a.e_out = L.e; a.rc = s.lv[level + 1].r; a.x = s.x; a.alpha = c.sc.alpha;
+    a.part_rr = c.part.rr; a.cg = cg; a.want_rr = want_rr;
+    const int grid = persistent_grid(a.pc.total, qpre_blocks<T, H>(), c.sm_count);
+    k_qpre<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpre_smem<T, H, PIPE_STAGES>(), c.stream>>>(
+        a, mr, M.kw[level], M.ks[level], M.q, M.x, mp ? *mp : M.x);
+}
+
+template <typename T, int H>
+static void launch_qpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const CUtensorMap& mr, T* eout, int cg) {
+    LevelArrays<T>& L = s.lv[level];
+    TmaMaps& M = *s.maps;
+    QPostArgs<T> a{};
+    a.pc.n = L.n; a.pc.ntiles = (L.n / TT) * (L.n / TT); a.pc.total = nact * a.pc.ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
+    a.E = L.E; a.Nn = L.Nn; a.cc = (T)c.cfg.coarse_scale; a.e_out = eout; a.part_rz = c.part.rz; a.cg = cg;
+    const int grid = persistent_grid(a.pc.total, qpost_blocks<T, H>(), c.sm_count);
+    k_qpost<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpost_smem<T, H, PIPE_STAGES>(), c.stream>>>(
+        a, M.e[level], M.ec[level], mr, M.kw[level], M.ks[level]);
+}
+
+// Finest-level passes dispatch on its halo (fine_sweeps 1 -> H = 2, 2 -> H = 4).
+template <typename T>
+static void fine_pre(Ctx& c, InnerSolver<T>& s, int nact, const CUtensorMap& mr, T* rout, int cg, const CUtensorMap* mp) {
+    if (c.cfg.fine_sweeps == 1) launch_qpre<T, 2>(c, s, 0, nact, mr, rout, cg, 1, mp);
+    else launch_qpre<T, 4>(c, s, 0, nact, mr, rout, cg, 1, mp);
+}
+template <typename T>
+static void fine_post(Ctx& c, InnerSolver<T>& s, int nact, const CUtensorMap& mr, T* eout) {
+    if (c.cfg.fine_sweeps == 1) launch_qpost<T, 2>(c, s, 0, nact, mr, eout, 1);
+    else launch_qpost<T, 4>(c, s, 0, nact, mr, eout, 1);
+}
+
+template <typename T>
+static void run_vcycle_lower_tma(Ctx& c, InnerSolver<T>& s, int nact) {
+    TmaMaps& M = *s.maps;
+    for (int l = 1; l < s.ntile_levels; ++l) launch_qpre<T, 4>(c, s, l, nact, M.r[l], nullptr, 0, 0, nullptr);
+    {
+        CoarseLevelPtrs<T> P{};
+        const int top = s.ntile_levels;
+        P.ntop = s.lv[top].n;
+        P.nlev = s.nlev - top;
+        for (int l = 0; l < P.nlev; ++l) {
+            P.Kw[l] = s.lv[top + l].Kw; P.Ks[l] = s.lv[top + l].Ks; P.E[l] = s.lv[top + l].E; P.Nn[l] = s.lv[top + l].Nn;
+        }
+        P.rtop = s.lv[top].r;
+        P.etop = s.lv[top].e2;
+        const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
+        k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
+    }
+    for (int l = s.ntile_levels - 1; l >= 1; --l) launch_qpost<T, 4>(c, s, l, nact, M.r[l], s.lv[l].e2, 0);
+}
+
 template <typename T, int NU>
-static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int count, const int* act) {
-    // levels 1 .. ntile_levels-1 (pre), coarse, then post back up to level 1
+static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int nact) {
     const T cc = (T)c.cfg.coarse_scale;
-    constexpr int R = TILE + 4 * NU;
-    const size_t smem = tile_smem_bytes<T>(R);
+    constexpr int TPB = Own<TILE + 4 * NU>::THREADS;
     for (int l = 1; l < s.ntile_levels; ++l) {
         LevelArrays<T>& L = s.lv[l];
-        dim3 grid((L.n / TILE) * (L.n / TILE), count);
-        k_pre<T, NU><<<grid, 256, smem, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, nullptr, L.e, s.lv[l + 1].r, nullptr,
-                                                    nullptr, nullptr, nullptr, nullptr, act, 0, 0);
+        dim3 grid((L.n / TILE) * (L.n / TILE), nact);
+        k_pre<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, nullptr, L.e, s.lv[l + 1].r, nullptr, nullptr,
+                                                 nullptr, nullptr, nullptr, s.list, 0, 0);
     }
     {
         CoarseLevelPtrs<T> P{};
@@ -661,97 +826,221 @@ static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int count, const int* ac
         P.rtop = s.lv[top].r;
         P.etop = s.lv[top].e2;
         const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
-        k_coarse<T, NU><<<count, 256, cs, c.stream>>>(P, cc, act);
+        k_coarse<T, NU><<<nact, 256, cs, c.stream>>>(P, cc, s.list);
     }
     for (int l = s.ntile_levels - 1; l >= 1; --l) {
         LevelArrays<T>& L = s.lv[l];
-        dim3 grid((L.n / TILE) * (L.n / TILE), count);
-        k_post<T, NU><<<grid, 256, smem, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr,
-                                                     act, 0);
+        dim3 grid((L.n / TILE) * (L.n / TILE), nact);
+        k_post<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr, s.list, 0);
     }
 }
 
-template <typename T, int NU>
+// Compacts act_in into the active list and returns its length (synchronises the stream).
+template <typename T>
+static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
+    k_compact<<<1, 1024, 0, c.stream>>>(count, c.sc.act_in, s.list, s.nact);
+    int h[4];
+    check(cudaMemcpyAsync(h, s.nact, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "nact d2h");
+    check(cudaMemcpyAsync(hcount, c.sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
+    check(cudaStreamSynchronize(c.stream), "sync");
+    int err = 0;
+    check(cudaMemcpy(&err, c.dev_err, sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
+    if (err) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
+    return h[0];
+}
+
+// ---------------------------------------------------------------------------
+// Warp-tile path: launchers
+// ---------------------------------------------------------------------------
+static inline int wtiles(int n) { return (n / WT) * (n / WT); }
+
+template <typename T, int H>
+static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T* rin, T* rout, int cg, int want_rr, const T* p) {
+    LevelArrays<T>& L = s.lv[level];
+    WPreArgs<T> A{};
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
+    A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
+    A.cg = cg; A.want_rr = want_rr;
+    k_wpre<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+}
+
+template <typename T, int H>
+static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T* r, T* eout, int cg) {
+    LevelArrays<T>& L = s.lv[level];
+    WPostArgs<T> A{};
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
+    A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg;
+    k_wpost<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+}
+
+template <typename T>
+static void launch_coarse(Ctx& c, InnerSolver<T>& s, int nact) {
+    CoarseLevelPtrs<T> P{};
+    const int top = s.ntile_levels;
+    P.ntop = s.lv[top].n;
+    P.nlev = s.nlev - top;
+    for (int l = 0; l < P.nlev; ++l) {
+        P.Kw[l] = s.lv[top + l].Kw; P.Ks[l] = s.lv[top + l].Ks; P.E[l] = s.lv[top + l].E; P.Nn[l] = s.lv[top + l].Nn;
+    }
+    P.rtop = s.lv[top].r;
+    P.etop = s.lv[top].e2;
+    const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
+    if (c.cfg.smooth_sweeps == 1) k_coarse<T, 1><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
+    else k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
+}
+
+// Solver kernel family for the tiled levels: 0 = one block per 32 x 32 tile,
+// 1 = persistent TMA-pipelined blocks, 2 = one warp per 16 x 16 tile (default).
+static int tile_path(const Ctx& c) {
+    if (c.cfg.smooth_sweeps == 1) return 0;
+    static int path = -1;
+    if (path < 0) {
+        const char* e = getenv("SMCGM_TILE_PATH");
+        path = e ? atoi(e) : 2;
+        if (path < 0 || path > 2) path = 2;
+    }
+    return path;
+}
+
+// The passes of one CG iteration on the finest level and the V-cycle below it.
+template <typename T>
+struct Passes {
+    Ctx& c;
+    InnerSolver<T>& s;
+    int path, n, ntiles;
+    Passes(Ctx& cc, InnerSolver<T>& ss) : c(cc), s(ss) {
+        path = tile_path(cc);
+        n = ss.lv[0].n;
+        ntiles = path == 2 ? wtiles(n) : (n / TILE) * (n / TILE);
+    }
+    // finest-level pre-smoothing (cg: with the CG update from r[cur] into r[1-cur])
+    void pre(int nact, int cur, int pc, int cg) {
+        TmaMaps* M = s.maps;
+        LevelArrays<T>& L0 = s.lv[0];
+        T* rout = cg ? s.r[1 - cur] : nullptr;
+        if (path == 2) {
+            if (c.cfg.fine_sweeps == 1) launch_wpre<T, 2>(c, s, 0, nact, s.r[cur], rout, cg, 1, s.p[pc]);
+            else launch_wpre<T, 4>(c, s, 0, nact, s.r[cur], rout, cg, 1, s.p[pc]);
+        } else if (path == 1) {
+            fine_pre<T>(c, s, nact, M->r0[cur], rout, cg, cg ? &M->p[pc] : nullptr);
+        } else {
+            constexpr int NU = 1;
+            k_pre<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
+                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], rout, L0.e, s.lv[1].r, s.q, s.x, s.p[pc], c.sc.alpha, c.part.rr, s.list, cg, 1);
+        }
+    }
+    void lower(int nact) {
+        if (path == 2) {
+            for (int l = 1; l < s.ntile_levels; ++l) launch_wpre<T, 4>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+            launch_coarse<T>(c, s, nact);
+            for (int l = s.ntile_levels - 1; l >= 1; --l) launch_wpost<T, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+        } else if (path == 1) {
+            run_vcycle_lower_tma<T>(c, s, nact);
+        } else {
+            run_vcycle_lower<T, 1>(c, s, nact);
+        }
+    }
+    void post(int nact, int cur) {
+        TmaMaps* M = s.maps;
+        LevelArrays<T>& L0 = s.lv[0];
+        if (path == 2) {
+            if (c.cfg.fine_sweeps == 1) launch_wpost<T, 2>(c, s, 0, nact, s.r[cur], s.z, 1);
+            else launch_wpost<T, 4>(c, s, 0, nact, s.r[cur], s.z, 1);
+        } else if (path == 1) {
+            fine_post<T>(c, s, nact, M->r0[cur], s.z);
+        } else {
+            constexpr int NU = 1;
+            k_post<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
+                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], L0.e, s.lv[1].e2, (T)c.cfg.coarse_scale, s.z, c.part.rz, s.list, 1);
+        }
+    }
+    void apply(int nact, int pc, int first) {
+        LevelArrays<T>& L0 = s.lv[0];
+        if (path == 2) {
+            WApplyArgs<T> A{};
+            A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list;
+            A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
+            A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;
+            k_wapply<T><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+        } else if (path == 1) {
+            TmaMaps* M = s.maps;
+            ApplyArgs<T> a{};
+            a.pc.n = n; a.pc.ntiles = ntiles; a.pc.total = nact * ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
+            a.E = L0.E; a.Nn = L0.Nn; a.pout = s.p[1 - pc]; a.q = s.q; a.betac = c.sc.betac; a.part_pq = c.part.pq; a.first = first;
+            k_apply_tma<T, PIPE_STAGES><<<persistent_grid(a.pc.total, apply_blocks<T>(), c.sm_count), 256,
+                                          apply_tma_smem<T, PIPE_STAGES>(), c.stream>>>(a, M->za, M->pa[pc], M->kwa, M->ksa);
+        } else {
+            k_apply<T><<<dim3(ntiles, nact), Own<TILE + 2>::THREADS, 0, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.z, s.p[pc],
+                                                                                   s.p[1 - pc], s.q, c.sc.betac, c.part.pq, s.list,
+                                                                                   first);
+        }
+    }
+};
+
+// One preconditioned-CG solve A x = r[0] (x = 0 on entry) for the particles whose
+// refinement is still active; every launch covers only the particles still iterating.
+template <typename T>
 static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
     SolverScalars& sc = c.sc;
-    LevelArrays<T>& L0 = s.lv[0];
-    const int n = L0.n;
-    const int ntiles = (n / TILE) * (n / TILE);
-    dim3 tgrid(ntiles, count);
-    constexpr int R = TILE + 4 * NU;
-    const size_t smem = tile_smem_bytes<T>(R);
-    const size_t smem_apply = tile_smem_bytes<T>(TILE + 2);
-    const T cc = (T)c.cfg.coarse_scale;
+    Passes<T> P(c, s);
+    const int n = P.n, ntiles = P.ntiles;
     const int sgrid = (count + 127) / 128;
     const double tol2 = tol * tol;
     const int maxit = c.cfg.max_iter;
     int cur = 0, pc = 0;
+    int hcount[3] = {0, 0, 0};
     k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit);
     check(cudaMemsetAsync(sc.count, 0, 3 * sizeof(int), c.stream), "memset count");
-    // z0 = M r0
-    k_pre<T, NU><<<tgrid, 256, smem, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], nullptr, L0.e, s.lv[1].r, nullptr,
-                                                 nullptr, nullptr, nullptr, c.part.rr, sc.act_in, 0, 1);
+    int nact = compact_active(c, s, count, hcount);
+    if (nact == 0) return 0;
+    P.pre(nact, cur, pc, 0);                      // z0 = M r0
     k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit);
-    int hcount[3] = {0, 0, 0};
-    check(cudaMemcpyAsync(hcount, sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
-    check(cudaStreamSynchronize(c.stream), "sync");
-    int active = hcount[0];
-    c.pc.inner_solves += active;
-    if (active == 0) return 0;
-    run_vcycle_lower<T, NU>(c, s, count, sc.act_in);
-    k_post<T, NU><<<tgrid, 256, smem, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], L0.e, s.lv[1].e2, cc, s.z, c.part.rz,
-                                                  sc.act_in, 1);
+    nact = compact_active(c, s, count, hcount);
+    c.pc.inner_solves += nact;
+    if (nact == 0) return 0;
+    P.lower(nact);
+    P.post(nact, cur);
     k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit);
     const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T);   // per cell: r,q,x,p,Kw,Ks in; r,x,e,rc out
     for (int it = 0; it < maxit; ++it) {
-        k_apply<T><<<tgrid, 256, smem_apply, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.z, s.p[pc], s.p[1 - pc], s.q, sc.betac,
-                                                        c.part.pq, sc.act_in, it == 0);
+        P.apply(nact, pc, it == 0);
         pc ^= 1;
         k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit);
         if (c.prof) check(cudaEventRecord(c.ev0, c.stream), "event");
-        k_pre<T, NU><<<tgrid, 256, smem, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], s.r[1 - cur], L0.e, s.lv[1].r, s.q,
-                                                     s.x, s.p[pc], sc.alpha, c.part.rr, sc.act_in, 1, 1);
+        P.pre(nact, cur, pc, 1);
         if (c.prof) check(cudaEventRecord(c.ev1, c.stream), "event");
         cur ^= 1;
-        c.pc.cg_iterations += active;
+        c.pc.cg_iterations += nact;
+        const int launched = nact;
         check(cudaMemsetAsync(sc.count, 0, sizeof(int), c.stream), "memset count");
         k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit);
-        check(cudaMemcpyAsync(hcount, sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
-        check(cudaStreamSynchronize(c.stream), "sync");
+        nact = compact_active(c, s, count, hcount);
         if (c.prof) {
             float ms = 0.f;
             check(cudaEventElapsedTime(&ms, c.ev0, c.ev1), "event time");
             c.pc.dom_ms += ms;
             c.pc.dom_launches += 1;
-            c.pc.dom_particles += active;
-            c.pc.dom_bytes += dom_bpc * (double)n * n * active;
+            c.pc.dom_particles += launched;
+            c.pc.dom_bytes += dom_bpc * (double)n * n * launched;
         }
-        active = hcount[0];
-        if (active == 0) break;
-        run_vcycle_lower<T, NU>(c, s, count, sc.act_in);
-        k_post<T, NU><<<tgrid, 256, smem, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], L0.e, s.lv[1].e2, cc, s.z, c.part.rz,
-                                                      sc.act_in, 1);
+        if (nact == 0) break;
+        P.lower(nact);
+        P.post(nact, cur);
         k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit);
     }
     check(cudaGetLastError(), "inner solve launch");
     return hcount[2];
 }
 
-// Dynamic shared-memory opt-in; the coarse kernel's need depends on the grid, so
-// the largest size requested so far is remembered per precision.
+// Dynamic shared-memory opt-in of the coarse kernel; its need depends on the
+// grid, so the largest size requested so far is remembered per precision.
 template <typename T>
 static void set_smem_attrs(Ctx& c, InnerSolver<T>& s) {
-    static size_t tile_set[2] = {0, 0}, coarse_set[2] = {0, 0};
+    (void)c;
+    static size_t coarse_set[2] = {0, 0};
     const int k = sizeof(T) == 4 ? 0 : 1;
-    const size_t t2 = tile_smem_bytes<T>(TILE + 8);
-    if (tile_set[k] < t2) {
-        const size_t t1 = tile_smem_bytes<T>(TILE + 4);
-        check(cudaFuncSetAttribute(k_pre<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1), "attr");
-        check(cudaFuncSetAttribute(k_post<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t1), "attr");
-        check(cudaFuncSetAttribute(k_pre<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2), "attr");
-        check(cudaFuncSetAttribute(k_post<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t2), "attr");
-        tile_set[k] = t2;
-    }
     const int top = s.ntile_levels;
     const size_t cs = coarse_smem_bytes<T>(s.lv[top].n, s.nlev - top);
     if (coarse_set[k] < cs) {
@@ -817,11 +1106,10 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
     const int sgrid = (count + 127) / 128;
     k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2);
     int itmax = 0;
-    const int nu = c.cfg.smooth_sweeps;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
     for (int o = 0; o < max_outer; ++o) {
-        int it = nu == 1 ? inner_solve<T, 1>(c, s, count, tol_in) : inner_solve<T, 2>(c, s, count, tol_in);
+        int it = inner_solve<T>(c, s, count, tol_in);
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
         k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out);

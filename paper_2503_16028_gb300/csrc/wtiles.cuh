@@ -1,0 +1,472 @@
+// Warp-per-tile kernels of the tiled multigrid/CG levels.
+//
+// A work item is one 16 x 16 tile of one active particle and is processed by
+// one warp on its own: the warp's lanes own the 2 x 2 quads of the smoothing
+// region (tile plus a halo of H = 2 nu cells), hold each quad's right-hand
+// side, face coefficients and 1/D in registers, and keep only the correction
+// in a per-warp shared array with a zero border.  Warps never wait for one
+// another (__syncwarp only), so an SM keeps ~16 tiles in flight and their
+// global loads -- all issued up front -- overlap the smoothing of other tiles.
+//
+// Quad cells (0,0), (1,1) are red and (1,0), (0,1) black (tile origins are
+// even), so each half-sweep updates two cells per quad with no colour test;
+// the quad's residuals sum to its restricted value and it shares one parent
+// for the prolongation.  Tile origins are even and n is even, so a quad lies
+// wholly inside or wholly outside the grid; outside quads keep e = 0.  Every
+// half-sweep updates the whole region: an error can enter only at the region
+// edge and moves one cell per half-sweep, which the halo H = 2 nu keeps out of
+// the tile interior (the first pre-smoothing half-sweep is pointwise from zero).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace smcgm {
+
+constexpr int WT = 16;            // tile edge of the warp kernels
+constexpr int WPB = 4;            // warps per block
+
+template <typename T, int H>
+struct WGeo {
+    static constexpr int RW = WT + 2 * H;              // region edge
+    static constexpr int QW = RW / 2;                  // quads per region edge
+    static constexpr int NQ = QW * QW;
+    static constexpr int SLOTS = (NQ + 31) / 32;       // quads per lane
+    static constexpr int EW = RW + 2;                  // correction array edge (zero border)
+    static constexpr int EN = EW * EW;
+};
+
+struct WArgs {
+    int n, ntiles, total;   // total = active particles x tiles
+    const int* list;
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T>
+__device__ inline void ld2(const T* p, T& a, T& b) {
+    const typename Vec2<T>::type v = *reinterpret_cast<const typename Vec2<T>::type*>(p);
+    a = v.x;
+    b = v.y;
+}
+template <typename T>
+__device__ inline void st2(T* p, T a, T b) {
+    typename Vec2<T>::type v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
+}
+
+template <typename T>
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Quad data: cells k = 0..3 are (0,0), (1,0), (0,1), (1,1).
+template <typename T>
+struct WQuad {
+    T r[4], w[4], e[4], s[4], n[4], inv[4];
+};
+
+// Raw loads of a quad at global (gx, gy) (inside the grid): west faces of its
+// two columns and of the column to the east (wall E at the grid edge), south
+// faces of its two rows and of the row to the north (wall Nn at the edge).
+template <typename T>
+struct WRaw {
+    T a0, a1, ea, b0, b1, eb;      // west faces rows gy, gy+1; east face of column gx+1
+    T s0, s1, m0, m1, t0, t1;      // south faces rows gy, gy+1, gy+2 (north of gy+1)
+};
+
+template <typename T>
+__device__ inline void load_faces_raw(WRaw<T>& R, const T* kw, const T* ks, const T* E, const T* Nn, int n, int gx, int gy) {
+    ld2(kw + (size_t)gy * n + gx, R.a0, R.a1);
+    ld2(kw + (size_t)(gy + 1) * n + gx, R.b0, R.b1);
+    R.ea = gx + 2 < n ? kw[(size_t)gy * n + gx + 2] : E[gy];
+    R.eb = gx + 2 < n ? kw[(size_t)(gy + 1) * n + gx + 2] : E[gy + 1];
+    ld2(ks + (size_t)gy * n + gx, R.s0, R.s1);
+    ld2(ks + (size_t)(gy + 1) * n + gx, R.m0, R.m1);
+    if (gy + 2 < n) ld2(ks + (size_t)(gy + 2) * n + gx, R.t0, R.t1);
+    else { R.t0 = Nn[gx]; R.t1 = Nn[gx + 1]; }
+}
+
+// 1/D of the smoother.  The smoother only has to be a fixed symmetric
+// preconditioner, so FP32 uses the one-instruction approximate reciprocal.
+template <typename T> __device__ inline T smoother_rcp(T d);
+template <> __device__ inline float smoother_rcp<float>(float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
+}
+template <> __device__ inline double smoother_rcp<double>(double d) { return recip_nr(d); }
+
+template <typename T>
+__device__ inline void faces_from_raw(WQuad<T>& Q, const WRaw<T>& R) {
+    Q.w[0] = R.a0; Q.e[0] = R.a1; Q.w[1] = R.a1; Q.e[1] = R.ea;
+    Q.w[2] = R.b0; Q.e[2] = R.b1; Q.w[3] = R.b1; Q.e[3] = R.eb;
+    Q.s[0] = R.s0; Q.n[0] = R.m0; Q.s[1] = R.s1; Q.n[1] = R.m1;
+    Q.s[2] = R.m0; Q.n[2] = R.t0; Q.s[3] = R.m1; Q.n[3] = R.t1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Q.inv[k] = smoother_rcp(Q.w[k] + Q.e[k] + Q.s[k] + Q.n[k]);
+}
+
+// Zeroes the border ring of a warp's correction array (interior cells are
+// always written before they are read, or belong to quads outside the grid,
+// which their owners zero).
+template <int EW>
+__device__ inline void zero_border(float* se, int lane) {
+    for (int i = lane; i < 4 * (EW - 1); i += 32) {
+        const int side = i / (EW - 1), j = i % (EW - 1);
+        const int c = side == 0 ? j : side == 1 ? (EW - 1) * EW + j + 1 : side == 2 ? (j + 1) * EW : j * EW + EW - 1;
+        se[c] = 0.f;
+    }
+}
+template <int EW>
+__device__ inline void zero_border(double* se, int lane) {
+    for (int i = lane; i < 4 * (EW - 1); i += 32) {
+        const int side = i / (EW - 1), j = i % (EW - 1);
+        const int c = side == 0 ? j : side == 1 ? (EW - 1) * EW + j + 1 : side == 2 ? (j + 1) * EW : j * EW + EW - 1;
+        se[c] = 0.0;
+    }
+}
+
+template <typename T, int EW>
+__device__ inline void wgs(T* se, int c0, const WQuad<T>& Q, int k, bool pointwise) {
+    const int c = c0 + (k >> 1) * EW + (k & 1);
+    T num = Q.r[k];
+    if (!pointwise) num += Q.w[k] * se[c - 1] + Q.e[k] * se[c + 1] + Q.s[k] * se[c - EW] + Q.n[k] * se[c + EW];
+    se[c] = num * Q.inv[k];
+}
+
+template <typename T>
+struct WPreArgs {
+    WArgs a;
+    const T *Kw, *Ks, *E, *Nn, *rin, *q, *p;
+    T *rout, *e_out, *rc, *x;
+    const double* alpha;
+    double* part_rr;
+    int cg, want_rr;
+};
+
+// Pre-smoothing (nu = H/2 sweeps red, black from zero), residual, restriction;
+// with cg (finest level) first r' = r - alpha q, x += alpha p, and |r'|^2.
+template <typename T, int H>
+__global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
+    using G = WGeo<T, H>;
+    constexpr int NU = H / 2;
+    __shared__ T sme[WPB][G::EN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= A.a.total) return;
+    const int n = A.a.n;
+    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    const int p = A.a.list[pi];
+    const int tpr = n / WT;
+    const int tx = tile % tpr, ty = tile / tpr;
+    const size_t base = (size_t)p * n * n;
+    const T* kw = A.Kw + base;
+    const T* ks = A.Ks + base;
+    const T* Ep = A.E + (size_t)p * n;
+    const T* Np = A.Nn + (size_t)p * n;
+    T* se = sme[warp];
+    zero_border<G::EW>(se, lane);
+    const T al = A.cg ? (T)A.alpha[p] : T(0);
+    const T* rin = A.rin + base;
+    const T* qg = A.q + base;
+    T* xg = A.x + base;
+    const T* pg = A.p + base;
+    T* routg = A.rout + base;
+    WQuad<T> Q[G::SLOTS];
+    int c0[G::SLOTS];
+    bool live[G::SLOTS], inner[G::SLOTS];
+    T rr = T(0);
+    // phase 1: every global load of every owned quad is issued before any is used
+    WRaw<T> Rw[G::SLOTS];
+    T rq[G::SLOTS][8];            // r (4) and q (4)
+    T xp[G::SLOTS][8];            // x (4) and p (4) of inner quads (CG update)
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        const int qi = lane + 32 * sl;
+        const int qx = qi % G::QW, qy = qi / G::QW;
+        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+        live[sl] = qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n;
+        inner[sl] = qi < G::NQ && qx >= H / 2 && qx < H / 2 + WT / 2 && qy >= H / 2 && qy < H / 2 + WT / 2;
+        c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        if (live[sl]) {
+            load_faces_raw(Rw[sl], kw, ks, Ep, Np, n, gx, gy);
+            const int gi = gy * n + gx;
+            ld2(rin + gi, rq[sl][0], rq[sl][1]);
+            ld2(rin + gi + n, rq[sl][2], rq[sl][3]);
+            if (A.cg) {
+                ld2(qg + gi, rq[sl][4], rq[sl][5]);
+                ld2(qg + gi + n, rq[sl][6], rq[sl][7]);
+                if (inner[sl]) {
+                    ld2(xg + gi, xp[sl][0], xp[sl][1]);
+                    ld2(xg + gi + n, xp[sl][2], xp[sl][3]);
+                    ld2(pg + gi, xp[sl][4], xp[sl][5]);
+                    ld2(pg + gi + n, xp[sl][6], xp[sl][7]);
+                }
+            }
+        } else if (qi < G::NQ) {
+            const int c = c0[sl];
+            se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
+        }
+    }
+    // phase 2: derived quantities and the CG update
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        if (!live[sl]) continue;
+        faces_from_raw(Q[sl], Rw[sl]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Q[sl].r[k] = A.cg ? rq[sl][k] - al * rq[sl][4 + k] : rq[sl][k];
+        if (inner[sl]) {
+            if (A.cg) {
+                const int qi = lane + 32 * sl;
+                const int qx = qi % G::QW, qy = qi / G::QW;
+                const int gi = (ty * WT - H + 2 * qy) * n + tx * WT - H + 2 * qx;
+                st2(xg + gi, xp[sl][0] + al * xp[sl][4], xp[sl][1] + al * xp[sl][5]);
+                st2(xg + gi + n, xp[sl][2] + al * xp[sl][6], xp[sl][3] + al * xp[sl][7]);
+                st2(routg + gi, Q[sl].r[0], Q[sl].r[1]);
+                st2(routg + gi + n, Q[sl].r[2], Q[sl].r[3]);
+            }
+            if (A.cg || A.want_rr) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rr += Q[sl].r[k] * Q[sl].r[k];
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int sw = 0; sw < NU; ++sw) {
+#pragma unroll
+        for (int sl = 0; sl < G::SLOTS; ++sl)
+            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G::EW>(se, c0[sl], Q[sl], 3, sw == 0); }
+        __syncwarp();
+#pragma unroll
+        for (int sl = 0; sl < G::SLOTS; ++sl)
+            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 1, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 2, false); }
+        __syncwarp();
+    }
+    const int m = n / 2;
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        if (!inner[sl]) continue;   // inner quads are always inside the grid
+        const int qi = lane + 32 * sl;
+        const int qx = qi % G::QW, qy = qi / G::QW;
+        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+        T rsum = T(0), ev[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0[sl] + (k >> 1) * G::EW + (k & 1);
+            const WQuad<T>& q = Q[sl];
+            ev[k] = se[c];
+            rsum += q.r[k] - ((q.w[k] + q.e[k] + q.s[k] + q.n[k]) * ev[k] -
+                              (q.w[k] * se[c - 1] + q.e[k] * se[c + 1] + q.s[k] * se[c - G::EW] + q.n[k] * se[c + G::EW]));
+        }
+        const int gi = gy * n + gx;
+        st2(A.e_out + base + gi, ev[0], ev[1]);
+        st2(A.e_out + base + gi + n, ev[2], ev[3]);
+        A.rc[(size_t)p * m * m + (gy >> 1) * m + (gx >> 1)] = rsum;
+    }
+    if (A.cg || A.want_rr) {
+        const double tot = warp_sum<T>((double)rr);
+        if (lane == 0) A.part_rr[(size_t)p * A.a.ntiles + tile] = tot;
+    }
+}
+
+template <typename T>
+struct WPostArgs {
+    WArgs a;
+    const T *Kw, *Ks, *E, *Nn, *r, *e_in, *ec;
+    T cc;
+    T* e_out;
+    double* part_rz;
+    int cg;
+};
+
+// Prolongation e + cc P ec, nu = H/2 sweeps (black, red), and on the finest level r.z.
+template <typename T, int H>
+__global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
+    using G = WGeo<T, H>;
+    constexpr int NU = H / 2;
+    __shared__ T sme[WPB][G::EN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= A.a.total) return;
+    const int n = A.a.n, m = n / 2;
+    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    const int p = A.a.list[pi];
+    const int tpr = n / WT;
+    const int tx = tile % tpr, ty = tile / tpr;
+    const size_t base = (size_t)p * n * n;
+    const T* kw = A.Kw + base;
+    const T* ks = A.Ks + base;
+    const T* Ep = A.E + (size_t)p * n;
+    const T* Np = A.Nn + (size_t)p * n;
+    const T* ecp = A.ec + (size_t)p * m * m;
+    T* se = sme[warp];
+    zero_border<G::EW>(se, lane);
+    const T* rg = A.r + base;
+    const T* eg = A.e_in + base;
+    WQuad<T> Q[G::SLOTS];
+    int c0[G::SLOTS];
+    bool live[G::SLOTS], inner[G::SLOTS];
+    WRaw<T> Rw[G::SLOTS];
+    T ev[G::SLOTS][5];            // e_in (4) and the parent correction
+    // phase 1: all global loads first
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        const int qi = lane + 32 * sl;
+        const int qx = qi % G::QW, qy = qi / G::QW;
+        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+        live[sl] = qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n;
+        inner[sl] = qi < G::NQ && qx >= H / 2 && qx < H / 2 + WT / 2 && qy >= H / 2 && qy < H / 2 + WT / 2;
+        c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        if (live[sl]) {
+            load_faces_raw(Rw[sl], kw, ks, Ep, Np, n, gx, gy);
+            const int gi = gy * n + gx;
+            ld2(rg + gi, Q[sl].r[0], Q[sl].r[1]);
+            ld2(rg + gi + n, Q[sl].r[2], Q[sl].r[3]);
+            ld2(eg + gi, ev[sl][0], ev[sl][1]);
+            ld2(eg + gi + n, ev[sl][2], ev[sl][3]);
+            ev[sl][4] = ecp[(gy >> 1) * m + (gx >> 1)];
+        } else if (qi < G::NQ) {
+            const int c = c0[sl];
+            se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
+        }
+    }
+    // phase 2: prolongation into the correction array, faces and 1/D
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        if (!live[sl]) continue;
+        faces_from_raw(Q[sl], Rw[sl]);
+        const T up = A.cc * ev[sl][4];
+        const int c = c0[sl];
+        se[c] = ev[sl][0] + up;
+        se[c + 1] = ev[sl][1] + up;
+        se[c + G::EW] = ev[sl][2] + up;
+        se[c + G::EW + 1] = ev[sl][3] + up;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int sw = 0; sw < NU; ++sw) {
+#pragma unroll
+        for (int sl = 0; sl < G::SLOTS; ++sl)
+            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 1, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 2, false); }
+        __syncwarp();
+#pragma unroll
+        for (int sl = 0; sl < G::SLOTS; ++sl)
+            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 0, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 3, false); }
+        __syncwarp();
+    }
+    T rz = T(0);
+#pragma unroll
+    for (int sl = 0; sl < G::SLOTS; ++sl) {
+        if (!inner[sl]) continue;
+        const int qi = lane + 32 * sl;
+        const int qx = qi % G::QW, qy = qi / G::QW;
+        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+        const int c = c0[sl];
+        const T e0 = se[c], e1 = se[c + 1], e2 = se[c + G::EW], e3 = se[c + G::EW + 1];
+        const int gi = gy * n + gx;
+        st2(A.e_out + base + gi, e0, e1);
+        st2(A.e_out + base + gi + n, e2, e3);
+        if (A.cg) rz += Q[sl].r[0] * e0 + Q[sl].r[1] * e1 + Q[sl].r[2] * e2 + Q[sl].r[3] * e3;
+    }
+    if (A.cg) {
+        const double tot = warp_sum<T>((double)rz);
+        if (lane == 0) A.part_rz[(size_t)p * A.a.ntiles + tile] = tot;
+    }
+}
+
+template <typename T>
+struct WApplyArgs {
+    WArgs a;
+    const T *Kw, *Ks, *E, *Nn, *z, *pin;
+    T *pout, *q;
+    const double* betac;
+    double* part_pq;
+    int first;
+};
+
+// p <- z + beta p on the tile plus a one-cell ring, then q = A p and p.q on the tile.
+template <typename T>
+__global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
+    constexpr int PW = WT + 2;                // staged p edge (tile + ring)
+    __shared__ T smp[WPB][PW * PW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= A.a.total) return;
+    const int n = A.a.n;
+    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    const int p = A.a.list[pi];
+    const int tpr = n / WT;
+    const int tx = tile % tpr, ty = tile / tpr;
+    const size_t base = (size_t)p * n * n;
+    const T b = A.first ? T(0) : (T)A.betac[p];
+    T* sp = smp[warp];
+    // tile: lane handles columns 2*(lane%8) .. +1 of rows lane/8 + 4 k (k = 0..3): 8 lanes x float2 per row
+    const int cx = 2 * (lane & 7), ry = lane >> 3;
+    T pv[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int yy = ry + 4 * k;
+        const size_t gi = base + (size_t)(ty * WT + yy) * n + tx * WT + cx;
+        T z0, z1;
+        ld2(A.z + gi, z0, z1);
+        if (!A.first) {
+            T q0, q1;
+            ld2(A.pin + gi, q0, q1);
+            z0 += b * q0;
+            z1 += b * q1;
+        }
+        pv[2 * k] = z0;
+        pv[2 * k + 1] = z1;
+        sp[(yy + 1) * PW + cx + 1] = z0;
+        sp[(yy + 1) * PW + cx + 2] = z1;
+    }
+    // ring: 16 cells on each side (zero outside the grid)
+    for (int i = lane; i < 4 * WT; i += 32) {
+        const int side = i / WT, j = i % WT;
+        int gx, gy, lx, ly;
+        if (side == 0) { gx = tx * WT - 1; gy = ty * WT + j; lx = 0; ly = j + 1; }
+        else if (side == 1) { gx = tx * WT + WT; gy = ty * WT + j; lx = PW - 1; ly = j + 1; }
+        else if (side == 2) { gx = tx * WT + j; gy = ty * WT - 1; lx = j + 1; ly = 0; }
+        else { gx = tx * WT + j; gy = ty * WT + WT; lx = j + 1; ly = PW - 1; }
+        T v = T(0);
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+            const size_t gi = base + (size_t)gy * n + gx;
+            v = A.z[gi];
+            if (!A.first) v += b * A.pin[gi];
+        }
+        sp[ly * PW + lx] = v;
+    }
+    __syncwarp();
+    double pq = 0.0;
+    const T* kw = A.Kw + base;
+    const T* ks = A.Ks + base;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int yy = ry + 4 * k;
+        const int gy = ty * WT + yy, gx = tx * WT + cx;
+        T w0, w1, s0, s1, t0, t1;
+        ld2(kw + (size_t)gy * n + gx, w0, w1);
+        const T e1 = gx + 2 < n ? kw[(size_t)gy * n + gx + 2] : A.E[(size_t)p * n + gy];
+        ld2(ks + (size_t)gy * n + gx, s0, s1);
+        if (gy + 1 < n) ld2(ks + (size_t)(gy + 1) * n + gx, t0, t1);
+        else { t0 = A.Nn[(size_t)p * n + gx]; t1 = A.Nn[(size_t)p * n + gx + 1]; }
+        const int c = (yy + 1) * PW + cx + 1;
+        const T p0 = pv[2 * k], p1 = pv[2 * k + 1];
+        const T q0 = (w0 + w1 + s0 + t0) * p0 - (w0 * sp[c - 1] + w1 * sp[c + 1] + s0 * sp[c - PW] + t0 * sp[c + PW]);
+        const T q1 = (w1 + e1 + s1 + t1) * p1 - (w1 * sp[c] + e1 * sp[c + 2] + s1 * sp[c + 1 - PW] + t1 * sp[c + 1 + PW]);
+        const size_t gi = base + (size_t)gy * n + gx;
+        st2(A.pout + gi, p0, p1);
+        st2(A.q + gi, q0, q1);
+        pq += (double)p0 * q0 + (double)p1 * q1;
+    }
+    pq = warp_sum<T>(pq);
+    if (lane == 0) A.part_pq[(size_t)p * A.a.ntiles + tile] = pq;
+}
+
+}  // namespace smcgm

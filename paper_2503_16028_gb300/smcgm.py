@@ -30,7 +30,7 @@ class smc_config(ctypes.Structure):
         ("n_particles", ctypes.c_int), ("n_components", ctypes.c_int), ("gm_rank", ctypes.c_int), ("em_iters", ctypes.c_int),
         ("var_floor", ctypes.c_double), ("beta0", ctypes.c_double), ("ess_frac", ctypes.c_double),
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("tol_inner", ctypes.c_double), ("tol_outer", ctypes.c_double),
-        ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int), ("fine_sweeps", ctypes.c_int),
         ("coarse_scale", ctypes.c_double), ("solve_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong),
     ]
 
@@ -123,7 +123,7 @@ def make_config(preset, **overrides):
     cfg.n_particles = p["n_particles"]; cfg.n_components = p["n_components"]; cfg.gm_rank = p["gm_rank"]
     cfg.beta0 = p["beta0"]; cfg.ess_frac = p["ess_frac"]; cfg.seed = p["seed"]
     for key in ("em_iters", "var_floor", "kernel", "precision", "tol_inner", "tol_outer", "max_iter", "max_refine",
-                "smooth_sweeps", "coarse_scale", "solve_batch"):
+                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch"):
         if key in p:
             setattr(cfg, key, p[key])
     cfg._keep = (obs, data)
