@@ -127,6 +127,8 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     if (dim == 2) {
         const size_t bn = (size_t)B * n * n;
         C.u64 = P.take<double>(bn);
+        C.fct_tw = P.take<double>(n);
+        C.fct_tmp = P.take<double>((size_t)B * n * Km);
         C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
         C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
         C.w64 = P.take<double>(bn);
@@ -276,7 +278,7 @@ smc_status smc_config_init(smc_config* cfg) {
     cfg->sigma = 0.01; cfg->source_kind = 1; cfg->src_amp = 10.0; cfg->src_width = 50.0;
     cfg->n_particles = 1024; cfg->n_components = 4; cfg->gm_rank = 64; cfg->em_iters = 50; cfg->var_floor = 1e-3;
     cfg->beta0 = 0.2; cfg->ess_frac = 0.5; cfg->kernel = SMC_K_PCN_GM; cfg->precision = SMC_P_FP32_REFINE;
-    cfg->tol_inner = 1e-5; cfg->tol_outer = 1e-10; cfg->max_iter = 60; cfg->max_refine = 6;
+    cfg->tol_inner = 1e-4; cfg->tol_outer = 1e-10; cfg->max_iter = 60; cfg->max_refine = 6;
     cfg->smooth_sweeps = 2; cfg->fine_sweeps = 1; cfg->coarse_scale = 2.0; cfg->solve_batch = 0; cfg->seed = 2503016028ull;
     return SMC_OK;
 }
@@ -313,6 +315,8 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     std::vector<double> lam, basis, b;
     std::vector<int> S, slot;
     host_tables(c, lam, basis, b, S, slot);
+    c.b2 = 0.0;
+    for (double v : b) c.b2 += v * v;
     std::vector<double> sq(lam.size());
     for (size_t i = 0; i < lam.size(); ++i) sq[i] = std::sqrt(lam[i]);
     check(cudaMemcpyAsync(c.lam, lam.data(), lam.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
@@ -322,6 +326,14 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     check(cudaMemcpyAsync(c.obs, c.obs_h.data(), c.obs_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.data, c.data_h.data(), c.data_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.S, S.data(), S.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+    std::vector<double> tw;
+    if (c.dim == 2) {
+        // twiddles of the fast cosine synthesis, block M/2 - 1 .. M - 2 for M = 2, 4, ..., n
+        tw.assign(c.n, 0.0);
+        for (int M = 2; M <= c.n; M *= 2)
+            for (int i = 0; i < M / 2; ++i) tw[M / 2 - 1 + i] = 1.0 / (2.0 * std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * M)));
+        check(cudaMemcpyAsync(c.fct_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
+    }
     check(cudaMemcpyAsync(c.slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemsetAsync(c.dev_err, 0, 4 * sizeof(int), c.stream), "memset err");
     check(cudaStreamSynchronize(c.stream), "sync");

@@ -137,6 +137,9 @@ struct Ctx {
     SolverScalars sc{};
     // moments scratch
     double* gridtmp = nullptr;
+    // fast cosine synthesis: twiddles 1/(2 cos(pi (2i+1) / (2M))) for M = 2, 4, .., n and the stage-1 output
+    double *fct_tw = nullptr, *fct_tmp = nullptr;
+    double b2 = 0.0;           // |h^2 f|^2 on the grid (the initial FP64 residual of w = 0)
     // host state
     double t = 0.0, beta = 0.2;
     int layer = 0;

@@ -516,17 +516,23 @@ size_t coarse_smem_bytes(int ntop, int nlev) {
 // ------------------------------------------------------------------------
 enum ScalarMode { SM_START = 0, SM_INIT_RR = 1, SM_RZ_FIRST = 2, SM_RZ = 3, SM_PQ = 4, SM_RR = 5 };
 
+// One warp per particle: the tile partial sums are reduced in a fixed order
+// (lane-strided, then a shuffle tree), so results do not depend on scheduling.
 __global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, int maxit) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= count) return;
     if (mode == SM_START) {
-        sc.act_in[p] = sc.act_out[p];
+        if (lane == 0) sc.act_in[p] = sc.act_out[p];
         return;
     }
     if (!sc.act_in[p]) return;
     const double* src = mode == SM_PQ ? part.pq : (mode == SM_RZ || mode == SM_RZ_FIRST) ? part.rz : part.rr;
     double s = 0.0;
-    for (int t = 0; t < ntiles; ++t) s += src[(size_t)p * ntiles + t];
+    for (int t = lane; t < ntiles; t += 32) s += src[(size_t)p * ntiles + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0) return;
     if (mode == SM_INIT_RR) {
         sc.rr0[p] = s;
         sc.rr[p] = s;
@@ -604,12 +610,20 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* __restric
     if (threadIdx.x == 0) part_res[(size_t)pb * gridDim.x + blockIdx.x] = tot;
 }
 
-__global__ void k_outer(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2) {
+// r = b for every particle (the residual of w = 0), in the inner precision.
+template <typename T>
+__global__ void k_fill_rhs(size_t nn, int count, const double* __restrict__ b, T* __restrict__ r) {
+    const size_t total = nn * count;
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (; t < total; t += stride) r[t] = (T)b[t % nn];
+}
+
+__global__ void k_outer(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, double b2const) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= count) return;
-    if (mode == 0) {  // initial residual = b
-        double s = 0.0;
-        for (int t = 0; t < ntiles; ++t) s += part.res[(size_t)p * ntiles + t];
+    if (mode == 0) {  // initial residual = b, |b|^2 known
+        const double s = b2const;
         sc.b2[p] = s;
         sc.res2[p] = s;
         sc.act_out[p] = s > 0.0 ? 1 : 0;
@@ -986,28 +1000,28 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
     SolverScalars& sc = c.sc;
     Passes<T> P(c, s);
     const int n = P.n, ntiles = P.ntiles;
-    const int sgrid = (count + 127) / 128;
+    const int wgrid = (count * 32 + 127) / 128;   // k_scalar: one warp per particle
     const double tol2 = tol * tol;
     const int maxit = c.cfg.max_iter;
     int cur = 0, pc = 0;
     int hcount[3] = {0, 0, 0};
-    k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit);
     check(cudaMemsetAsync(sc.count, 0, 3 * sizeof(int), c.stream), "memset count");
     int nact = compact_active(c, s, count, hcount);
     if (nact == 0) return 0;
     P.pre(nact, cur, pc, 0);                      // z0 = M r0
-    k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit);
     nact = compact_active(c, s, count, hcount);
     c.pc.inner_solves += nact;
     if (nact == 0) return 0;
     P.lower(nact);
     P.post(nact, cur);
-    k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit);
     const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T);   // per cell: r,q,x,p,Kw,Ks in; r,x,e,rc out
     for (int it = 0; it < maxit; ++it) {
         P.apply(nact, pc, it == 0);
         pc ^= 1;
-        k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit);
         if (c.prof) check(cudaEventRecord(c.ev0, c.stream), "event");
         P.pre(nact, cur, pc, 1);
         if (c.prof) check(cudaEventRecord(c.ev1, c.stream), "event");
@@ -1015,7 +1029,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         c.pc.cg_iterations += nact;
         const int launched = nact;
         check(cudaMemsetAsync(sc.count, 0, sizeof(int), c.stream), "memset count");
-        k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit);
         nact = compact_active(c, s, count, hcount);
         if (c.prof) {
             float ms = 0.f;
@@ -1028,7 +1042,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         if (nact == 0) break;
         P.lower(nact);
         P.post(nact, cur);
-        k_scalar<<<sgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit);
     }
     check(cudaGetLastError(), "inner solve launch");
     return hcount[2];
@@ -1097,14 +1111,13 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         check(cudaMemcpyAsync(sc.act_out, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, c.stream), "act init");
         check(cudaStreamSynchronize(c.stream), "sync");
     }
-    k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out);
-    c.pc.residuals += count;
+    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, c.b64, s.r[0]);
     c.pc.solves += count;
     c.pc.cells = n * n;
     c.pc.word_bytes = (int)sizeof(T);
     int outer_active = count;
     const int sgrid = (count + 127) / 128;
-    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2);
+    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, c.b2);
     int itmax = 0;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
@@ -1115,7 +1128,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out);
         k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out);
         check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
-        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2);
+        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, c.b2);
         int h = 0;
         check(cudaMemcpyAsync(&h, sc.count + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
         check(cudaStreamSynchronize(c.stream), "sync");

@@ -1,72 +1,120 @@
 // Field synthesis u = sum_{k,l} v_kl c_k cos(k pi x) c_l cos(l pi y) at the
 // cell centres (the KL expansion of the prior, Sec. 2.1 / Sec. 3.2, eq. Fourier
 // series), in FP64, and the whole 1D forward map of the elliptic problem.
-//
-// 2D synthesis is separable: T = V^T B^T (stage 1, along x), U = B T (stage 2,
-// along y), with B[i][k] = c_k cos(k pi (i + 1/2)/n).  Both stages use the
-// mirror symmetry of the cell-centre cosines, B[n-1-i][k] = (-1)^k B[i][k]:
-// even and odd modes are summed separately for i < n/2 and combined as
-// E + O (row i) and E - O (row n-1-i), halving the multiply-adds.
+// At cell centres x_i = (i + 1/2)/n the synthesis along one axis is a DCT-III
+// of length n, so the separable 2D synthesis is two passes of fast cosine
+// transforms (stage 1 along x, stage 2 along y).
 #include "smcgm_internal.cuh"
 #include "common.cuh"
 
 namespace smcgm {
 
-constexpr int SY_CI = 16;        // output columns i per block (plus their mirrors)
+// ------------------------------------------------------------------------
+// Fast cosine synthesis.  Both stages are DCT-III transforms of length n,
+// X[i] = sum_k x_k cos(pi k (2i + 1) / (2n)), with x_k = c_k v_k for k < Km and
+// 0 above, evaluated by Lee's recursive factorisation (B. G. Lee, "A new
+// algorithm to compute the discrete cosine transform", IEEE Trans. ASSP 32,
+// 1984): with x_e[m] = x_{2m} and y[m] = x_{2m+1} + x_{2m-1},
+//   X[i] = G[i] + H[i],  X[n-1-i] = G[i] - H[i],  i < n/2,
+//   G = DCT-III_{n/2}(x_e),  H[i] = DCT-III_{n/2}(y)[i] / (2 cos(pi (2i + 1) / (2n))).
+// The recursion is unrolled into log2 n top-down splitting levels and log2 n
+// bottom-up butterfly levels, O(n log n) FP64 operations per transform
+// instead of O(n Km).  One warp per transform (warp-synchronous); a block
+// handles 32 transforms so that its input and output rows are contiguous.
+// Stage 1 (along x, one transform per y-mode l) writes T^T[i][l]; stage 2
+// (along y, one transform per column i) writes U[j][i].
+// ------------------------------------------------------------------------
+constexpr int FCT_T = 32;            // transforms per block
+constexpr int FCT_WARPS = 8;
 
-// grid: (n/2/SY_CI, count); block 256.  Shared: T[Km][2*SY_CI] doubles.
-__global__ void __launch_bounds__(256) k_synth2d(int n, int Km, const double* __restrict__ X, const double* __restrict__ B,
-                                                 double* __restrict__ U) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    double* Ts = reinterpret_cast<double*>(smraw);   // [Km][2*SY_CI]: columns i0+c (c < CI) then mirrors
-    const int p = blockIdx.y;
-    const int i0 = blockIdx.x * SY_CI;
-    const double* V = X + (size_t)p * Km * Km;       // V[k][l]
-    const int tid = threadIdx.x;
-    const int Kh = (Km + 1) / 2;
-    // stage 1: for each (l, c): Te = sum_{k even} V[k][l] B[i0+c][k], To = sum_{k odd}
-    for (int task = tid; task < Km * SY_CI; task += blockDim.x) {
-        const int l = task / SY_CI, cc = task % SY_CI;
-        const int i = i0 + cc;
-        const double* Bi = B + (size_t)i * Km;
-        double te = 0.0, to = 0.0;
-        for (int h = 0; h < Kh; ++h) {
-            const int k = 2 * h;
-            te = fma(V[(size_t)k * Km + l], Bi[k], te);
-            if (k + 1 < Km) to = fma(V[(size_t)(k + 1) * Km + l], Bi[k + 1], to);
+__device__ inline void fct_warp(double* b0, double* b1, int N, int lgN, const double* __restrict__ tw, int lane) {
+    double* src = b0;
+    double* dst = b1;
+    const int half = N >> 1;
+    // top-down splitting: segment size M -> [even | odd sums]
+    for (int lm = lgN; lm >= 1; --lm) {
+        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+        for (int idx = lane; idx < half; idx += 32) {
+            const int o = (idx >> lh) << lm, m = idx & (h - 1);
+            dst[o + m] = src[o + 2 * m];
+            dst[o + h + m] = m > 0 ? src[o + 2 * m + 1] + src[o + 2 * m - 1] : src[o + 2 * m + 1];
         }
-        Ts[l * (2 * SY_CI) + cc] = te + to;
-        Ts[l * (2 * SY_CI) + SY_CI + cc] = te - to;
+        __syncwarp();
+        double* t = src; src = dst; dst = t;
+    }
+    // bottom-up butterflies
+    for (int lm = 1; lm <= lgN; ++lm) {
+        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+        const double* twm = tw + (h - 1);
+        for (int idx = lane; idx < half; idx += 32) {
+            const int o = (idx >> lh) << lm, i = idx & (h - 1);
+            const double g = src[o + i];
+            const double hp = src[o + h + i] * twm[i];
+            dst[o + i] = g + hp;
+            dst[o + M - 1 - i] = g - hp;
+        }
+        __syncwarp();
+        double* t = src; src = dst; dst = t;
+    }
+    // after 2 lgN swaps the result is back in b0
+}
+
+// stage: 0 = along x (input V[k][l], one transform per l, output T^T[i][l]),
+//        1 = along y (input T^T[i][l], one transform per i, output U[j][i]).
+__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lgn, int Km, const double* __restrict__ in,
+                                                      double* __restrict__ out, const double* __restrict__ tw) {
+    extern __shared__ __align__(16) double fsm[];
+    const int SP = n + 1;                               // padded staging row
+    double* stg = fsm;                                  // FCT_T x SP
+    double* work = fsm + FCT_T * SP;                    // FCT_WARPS x 2n
+    const int p = blockIdx.y;
+    const int t0 = blockIdx.x * FCT_T;                  // first transform of the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t inb = stage == 0 ? (size_t)p * Km * Km : (size_t)p * n * Km;
+    const size_t outb = stage == 0 ? (size_t)p * n * Km : (size_t)p * n * n;
+    // load inputs: stage 0 rows V[k][t0 .. t0+31]; stage 1 rows T^T[t0 + t][0 .. Km)
+    for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
+        if (stage == 0) {
+            const int k = idx / FCT_T, t = idx % FCT_T;
+            stg[t * SP + k] = t0 + t < Km ? in[inb + (size_t)k * Km + t0 + t] * (k == 0 ? 1.0 : M_SQRT2) : 0.0;
+        } else {
+            const int t = idx / Km, l = idx % Km;
+            stg[t * SP + l] = in[inb + (size_t)(t0 + t) * Km + l] * (l == 0 ? 1.0 : M_SQRT2);
+        }
     }
     __syncthreads();
-    // stage 2: U[j][col] = sum_l B[j][l] T[l][col], j < n/2 with mirrors.
-    const int nh = n / 2;
-    for (int task = tid; task < nh * 2 * SY_CI; task += blockDim.x) {
-        const int j = task / (2 * SY_CI), col = task % (2 * SY_CI);
-        const double* Bj = B + (size_t)j * Km;
-        double e = 0.0, o = 0.0;
-        for (int h = 0; h < Kh; ++h) {
-            const int l = 2 * h;
-            e = fma(Bj[l], Ts[l * (2 * SY_CI) + col], e);
-            if (l + 1 < Km) o = fma(Bj[l + 1], Ts[(l + 1) * (2 * SY_CI) + col], o);
-        }
-        const int i = col < SY_CI ? i0 + col : n - 1 - (i0 + col - SY_CI);
-        double* Up = U + (size_t)p * n * n;
-        Up[(size_t)j * n + i] = e + o;
-        Up[(size_t)(n - 1 - j) * n + i] = e - o;
+    double* b0 = work + warp * 2 * n;
+    double* b1 = b0 + n;
+    for (int t = warp; t < FCT_T; t += FCT_WARPS) {
+        for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : 0.0;
+        __syncwarp();
+        fct_warp(b0, b1, n, lgn, tw, lane);
+        for (int k = lane; k < n; k += 32) stg[t * SP + k] = b0[k];
+        __syncwarp();
+    }
+    __syncthreads();
+    // write: stage 0 -> T^T[i][t0 + t]; stage 1 -> U[j][t0 + t]
+    const int rowlen = stage == 0 ? Km : n;
+    for (int idx = threadIdx.x; idx < FCT_T * n; idx += blockDim.x) {
+        const int i = idx / FCT_T, t = idx % FCT_T;
+        if (t0 + t < rowlen) out[outb + (size_t)i * rowlen + t0 + t] = stg[t * SP + i];
     }
 }
 
 void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
     const int n = c.n, Km = c.Km;
-    const size_t smem = sizeof(double) * (size_t)Km * 2 * SY_CI;
-    static bool attr = false;
-    if (!attr) {
-        check(cudaFuncSetAttribute(k_synth2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * 256 * 2 * SY_CI)), "attr");
-        attr = true;
+    int lgn = 0;
+    while ((1 << lgn) < n) ++lgn;
+    const size_t smem = sizeof(double) * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
+    static size_t attr = 0;
+    if (attr < smem) {
+        check(cudaFuncSetAttribute(k_fct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
+        attr = smem;
     }
-    dim3 grid(n / 2 / SY_CI, count);
-    k_synth2d<<<grid, 256, smem, c.stream>>>(n, Km, X, c.basis, U);
+    // stage 1: ceil(Km / 32) blocks per particle (transforms past Km are masked); stage 2: n / 32
+    const int b1 = (Km + FCT_T - 1) / FCT_T, b2 = n / FCT_T;
+    k_fct<<<dim3(b1, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, X, c.fct_tmp, c.fct_tw);
+    k_fct<<<dim3(b2, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, c.fct_tmp, U, c.fct_tw);
     check(cudaGetLastError(), "synth2d");
 }
 
