@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <algorithm>
 #include <numeric>
 #include <new>
@@ -141,8 +142,10 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
         s.alpha = P.take<double>(B); s.betac = P.take<double>(B); s.res2 = P.take<double>(B); s.b2 = P.take<double>(B);
         s.act_in = P.take<int>(B); s.act_out = P.take<int>(B); s.iters = P.take<int>(B); s.flags = P.take<int>(B);
         s.count = P.take<int>(4);
+        // levels with n_l <= coarse_top run in the one-block-per-particle coarse kernel
+        const int ctop = 32;
         if (cfg.precision == SMC_P_FP32_REFINE)
-            plan_inner<float>(P, C.s32, n, B, 64, false, nullptr, nullptr, nullptr, nullptr);
+            plan_inner<float>(P, C.s32, n, B, ctop, false, nullptr, nullptr, nullptr, nullptr);
         else
             plan_inner<double>(P, C.s64, n, B, 32, true, C.Kw64, C.Ks64, C.E64, C.N64);
     } else {

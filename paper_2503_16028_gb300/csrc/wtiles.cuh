@@ -391,6 +391,8 @@ struct WApplyArgs {
 };
 
 // p <- z + beta p on the tile plus a one-cell ring, then q = A p and p.q on the tile.
+// Lane l covers columns 2 (l % 8), +1 of rows l / 8 + 4 k; all global loads
+// (z, p, ring, faces) are issued before any is used.
 template <typename T>
 __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     constexpr int PW = WT + 2;                // staged p edge (tile + ring)
@@ -404,69 +406,81 @@ __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     const int tpr = n / WT;
     const int tx = tile % tpr, ty = tile / tpr;
     const size_t base = (size_t)p * n * n;
-    const T b = A.first ? T(0) : (T)A.betac[p];
-    T* sp = smp[warp];
-    // tile: lane handles columns 2*(lane%8) .. +1 of rows lane/8 + 4 k (k = 0..3): 8 lanes x float2 per row
-    const int cx = 2 * (lane & 7), ry = lane >> 3;
-    T pv[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int yy = ry + 4 * k;
-        const size_t gi = base + (size_t)(ty * WT + yy) * n + tx * WT + cx;
-        T z0, z1;
-        ld2(A.z + gi, z0, z1);
-        if (!A.first) {
-            T q0, q1;
-            ld2(A.pin + gi, q0, q1);
-            z0 += b * q0;
-            z1 += b * q1;
-        }
-        pv[2 * k] = z0;
-        pv[2 * k + 1] = z1;
-        sp[(yy + 1) * PW + cx + 1] = z0;
-        sp[(yy + 1) * PW + cx + 2] = z1;
-    }
-    // ring: 16 cells on each side (zero outside the grid)
-    for (int i = lane; i < 4 * WT; i += 32) {
-        const int side = i / WT, j = i % WT;
-        int gx, gy, lx, ly;
-        if (side == 0) { gx = tx * WT - 1; gy = ty * WT + j; lx = 0; ly = j + 1; }
-        else if (side == 1) { gx = tx * WT + WT; gy = ty * WT + j; lx = PW - 1; ly = j + 1; }
-        else if (side == 2) { gx = tx * WT + j; gy = ty * WT - 1; lx = j + 1; ly = 0; }
-        else { gx = tx * WT + j; gy = ty * WT + WT; lx = j + 1; ly = PW - 1; }
-        T v = T(0);
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-            const size_t gi = base + (size_t)gy * n + gx;
-            v = A.z[gi];
-            if (!A.first) v += b * A.pin[gi];
-        }
-        sp[ly * PW + lx] = v;
-    }
-    __syncwarp();
-    double pq = 0.0;
+    const T* zg = A.z + base;
+    const T* pg = A.pin + base;
     const T* kw = A.Kw + base;
     const T* ks = A.Ks + base;
+    const bool first = A.first != 0;
+    const T b = first ? T(0) : (T)A.betac[p];
+    T* sp = smp[warp];
+    const int cx = 2 * (lane & 7), ry = lane >> 3;
+    const int gx = tx * WT + cx;
+    // phase 1: loads
+    T zv[8], pv0[8], rz[2], rp[2];
+    T w0[4], w1[4], e1[4], s0[4], s1[4], t0[4], t1[4];
+    int rgi[2];
+    bool rin[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int gy = ty * WT + ry + 4 * k;
+        const int gi = gy * n + gx;
+        ld2(zg + gi, zv[2 * k], zv[2 * k + 1]);
+        if (!first) ld2(pg + gi, pv0[2 * k], pv0[2 * k + 1]);
+        ld2(kw + gi, w0[k], w1[k]);
+        e1[k] = gx + 2 < n ? kw[gi + 2] : A.E[(size_t)p * n + gy];
+        ld2(ks + gi, s0[k], s1[k]);
+        if (gy + 1 < n) ld2(ks + gi + n, t0[k], t1[k]);
+        else { t0[k] = A.Nn[(size_t)p * n + gx]; t1[k] = A.Nn[(size_t)p * n + gx + 1]; }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const int side = i / WT, j = i % WT;
+        int gxx, gyy;
+        if (side == 0) { gxx = tx * WT - 1; gyy = ty * WT + j; }
+        else if (side == 1) { gxx = tx * WT + WT; gyy = ty * WT + j; }
+        else if (side == 2) { gxx = tx * WT + j; gyy = ty * WT - 1; }
+        else { gxx = tx * WT + j; gyy = ty * WT + WT; }
+        rin[h] = gxx >= 0 && gxx < n && gyy >= 0 && gyy < n;
+        rgi[h] = gyy * n + gxx;
+        rz[h] = rin[h] ? zg[rgi[h]] : T(0);
+        rp[h] = (rin[h] && !first) ? pg[rgi[h]] : T(0);
+    }
+    // phase 2: p_new into shared memory
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int yy = ry + 4 * k;
-        const int gy = ty * WT + yy, gx = tx * WT + cx;
-        T w0, w1, s0, s1, t0, t1;
-        ld2(kw + (size_t)gy * n + gx, w0, w1);
-        const T e1 = gx + 2 < n ? kw[(size_t)gy * n + gx + 2] : A.E[(size_t)p * n + gy];
-        ld2(ks + (size_t)gy * n + gx, s0, s1);
-        if (gy + 1 < n) ld2(ks + (size_t)(gy + 1) * n + gx, t0, t1);
-        else { t0 = A.Nn[(size_t)p * n + gx]; t1 = A.Nn[(size_t)p * n + gx + 1]; }
+        if (!first) { zv[2 * k] += b * pv0[2 * k]; zv[2 * k + 1] += b * pv0[2 * k + 1]; }
+        sp[(yy + 1) * PW + cx + 1] = zv[2 * k];
+        sp[(yy + 1) * PW + cx + 2] = zv[2 * k + 1];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const int side = i / WT, j = i % WT;
+        const int lx = side == 0 ? 0 : side == 1 ? PW - 1 : j + 1;
+        const int ly = side == 2 ? 0 : side == 3 ? PW - 1 : j + 1;
+        sp[ly * PW + lx] = rz[h] + b * rp[h];
+    }
+    __syncwarp();
+    T pq = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int yy = ry + 4 * k;
+        const int gy = ty * WT + yy;
         const int c = (yy + 1) * PW + cx + 1;
-        const T p0 = pv[2 * k], p1 = pv[2 * k + 1];
-        const T q0 = (w0 + w1 + s0 + t0) * p0 - (w0 * sp[c - 1] + w1 * sp[c + 1] + s0 * sp[c - PW] + t0 * sp[c + PW]);
-        const T q1 = (w1 + e1 + s1 + t1) * p1 - (w1 * sp[c] + e1 * sp[c + 2] + s1 * sp[c + 1 - PW] + t1 * sp[c + 1 + PW]);
+        const T p0 = zv[2 * k], p1 = zv[2 * k + 1];
+        const T q0 = (w0[k] + w1[k] + s0[k] + t0[k]) * p0 -
+                     (w0[k] * sp[c - 1] + w1[k] * sp[c + 1] + s0[k] * sp[c - PW] + t0[k] * sp[c + PW]);
+        const T q1 = (w1[k] + e1[k] + s1[k] + t1[k]) * p1 -
+                     (w1[k] * sp[c] + e1[k] * sp[c + 2] + s1[k] * sp[c + 1 - PW] + t1[k] * sp[c + 1 + PW]);
         const size_t gi = base + (size_t)gy * n + gx;
         st2(A.pout + gi, p0, p1);
         st2(A.q + gi, q0, q1);
-        pq += (double)p0 * q0 + (double)p1 * q1;
+        pq += p0 * q0 + p1 * q1;
     }
-    pq = warp_sum<T>(pq);
-    if (lane == 0) A.part_pq[(size_t)p * A.a.ntiles + tile] = pq;
+    const double tot = warp_sum<T>((double)pq);
+    if (lane == 0) A.part_pq[(size_t)p * A.a.ntiles + tile] = tot;
 }
 
 }  // namespace smcgm
