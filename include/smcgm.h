@@ -203,6 +203,30 @@ smc_status smc_profile_query(smc_ctx* ctx, int enable, smc_profile* out, int res
  * bindings that have no CUDA runtime of their own. */
 smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t bytes);
 
+/* Largest particle count smc_resample_indices_static() accepts: its scratch is
+ * a fixed device array of this many 64-bit words (256 KiB). */
+#define SMC_STATIC_RESAMPLE_MAX 32768
+
+/* Systematic-resampling indices without any allocation.  The paper has no
+ * counterpart: this is an interface for callers that cannot give the library
+ * device memory (an application whose own pool owns all device memory and
+ * forbids other allocations, or a loop that must not risk the implicit
+ * synchronisation of cudaMalloc).  It computes exactly what smc_resample()
+ * computes for one layer: d_logw (device, n_particles log weights), the key
+ * `seed` and the layer index select the Philox draw; d_indices (device,
+ * n_particles ints) receives the indices.  Scratch is a file-scope device
+ * array of SMC_STATIC_RESAMPLE_MAX words that each GPU loading the library
+ * keeps until the process exits; the library calls no cudaMalloc, cudaFree or
+ * allocating routine.  The first call on a device looks up the array's
+ * device address with that device current (call it once before capturing work
+ * into a stream graph).  All calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller (e.g. one stream).  Returns
+ * SMC_EINVAL for n_particles outside [1, SMC_STATIC_RESAMPLE_MAX] (message in
+ * smc_last_error(NULL)), SMC_ECUDA if a CUDA call fails.  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = default stream). */
+smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
+                                       int* d_indices, void* stream);
+
 /* Library version string. */
 const char* smc_version(void);
 

@@ -238,6 +238,15 @@ using namespace smcgm;
         return SMC_ENOMEM;                                                                      \
     }
 
+namespace smcgm {
+// Message for smc_last_error(NULL), set by entry points that have no context.
+std::string& global_error() {
+    static thread_local std::string msg;
+    return msg;
+}
+void set_global_error(const char* msg) { global_error() = msg; }
+}  // namespace smcgm
+
 static smc_status fail(smc_ctx* ctx, smc_status s, const std::string& msg) {
     if (ctx) ctx->c.err = msg;
     return s;
@@ -293,7 +302,7 @@ smc_status smc_workspace_size(const smc_config* cfg, size_t* bytes) {
     return SMC_OK;
 }
 
-static thread_local std::string g_init_error;
+static thread_local std::string& g_init_error = smcgm::global_error();
 
 smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* stream, smc_ctx** out) {
     if (!cfg || !out) return SMC_EINVAL;

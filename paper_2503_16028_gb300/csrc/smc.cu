@@ -11,6 +11,7 @@
 // prefix sums CDF_i; particle k takes min{i : N CDF_i > k T + u48} with u48 one
 // Philox draw.  Integer arithmetic makes the indices independent of summation
 // order.
+#include <mutex>
 #include "smcgm_internal.cuh"
 #include "common.cuh"
 
@@ -243,4 +244,61 @@ void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, doubl
     check(cudaGetLastError(), "grid moments");
 }
 
+// ---------------------------------------------------------------------------
+// Resampling without any allocation.
+//
+// Some callers cannot hand the library a device buffer at all: a host
+// application that owns every byte of device memory through its own pool and
+// forbids other allocations, or a loop where a cudaMalloc (which may
+// synchronise the device) is not acceptable.  For them the systematic-
+// resampling indices can be computed with scratch that lives in this file: a
+// fixed array of device memory that every GPU loading the library keeps until
+// the process exits.  The caller passes the log weights and the output array;
+// the library allocates nothing.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned long long g_static_cdf[SMC_STATIC_RESAMPLE_MAX];
+
+// Device address of g_static_cdf per device, looked up once with that device current.
+static unsigned long long* static_cdf_ptr(int dev) {
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static unsigned long long* ptrs[MAXDEV] = {nullptr};
+    if (dev < 0 || dev >= MAXDEV) throw CudaError{cudaErrorInvalidDevice, "device index out of range"};
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        check(cudaGetSymbolAddress(&p, g_static_cdf), "cudaGetSymbolAddress(g_static_cdf)");
+        ptrs[dev] = reinterpret_cast<unsigned long long*>(p);
+    }
+    return ptrs[dev];
+}
+
 }  // namespace smcgm
+
+extern "C" smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
+                                                  int* d_indices, void* stream) {
+    using namespace smcgm;
+    if (!d_logw || !d_indices || layer < 0) {
+        set_global_error("smc_resample_indices_static: null pointer or negative layer");
+        return SMC_EINVAL;
+    }
+    if (n_particles < 1 || n_particles > SMC_STATIC_RESAMPLE_MAX) {
+        set_global_error("smc_resample_indices_static: n_particles must be in [1, SMC_STATIC_RESAMPLE_MAX] (32768)");
+        return SMC_EINVAL;
+    }
+    try {
+        int dev = 0;
+        check(cudaGetDevice(&dev), "cudaGetDevice");
+        unsigned long long* cdf = static_cdf_ptr(dev);
+        const Key key = key_of(seed);
+        const U4 w = philox(0u, 0u, (uint32_t)layer, P_RESAMPLE, key.k0, key.k1);
+        const unsigned long long u48 = ((unsigned long long)w.x << 16) | (unsigned long long)(w.y >> 16);
+        // every entry of the CDF scratch below n_particles is written before it is read; nothing needs clearing
+        k_resample<<<1, SB, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n_particles, d_logw, u48, cdf, d_indices);
+        check(cudaGetLastError(), "k_resample launch");
+    } catch (const CudaError& ce) {
+        set_global_error((std::string(ce.what) + ": " + cudaGetErrorString(ce.e)).c_str());
+        return SMC_ECUDA;
+    }
+    return SMC_OK;
+}

@@ -159,6 +159,8 @@ struct Ctx {
 
 // status helper
 struct CudaError { cudaError_t e; const char* what; };
+void set_global_error(const char* msg);
+std::string& global_error();
 void check(cudaError_t e, const char* what);   // throws CudaError
 
 constexpr int TILE = 32;          // inner tile edge of the tiled multigrid kernels

@@ -12,6 +12,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsmcgm.so")
 
+SMC_STATIC_RESAMPLE_MAX = 32768
 SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ENOCONV, SMC_EDEGENERATE, SMC_ESTATE = range(7)
 SMC_K_PCN, SMC_K_PCN_GM, SMC_K_GM_INDEP = range(3)
 SMC_P_FP64, SMC_P_FP32_REFINE = range(2)
@@ -68,6 +69,7 @@ EXPORTS = {
     "smc_config_size": (ctypes.c_size_t, []),
     "smc_profile_query": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(smc_profile), ctypes.c_int]),
     "smc_copy_to_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t]),
+    "smc_resample_indices_static": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _vp, _vp]),
 }
 
 _LIB = None
@@ -258,6 +260,12 @@ class Sampler:
         out = smc_profile()
         self._check(self.lib.smc_profile_query(self.ctx, enable, ctypes.byref(out), int(reset)), self.ctx)
         return {k: getattr(out, k) for k, _ in smc_profile._fields_}
+
+    def diagnostics_pointers(self):
+        """Device addresses of (log alpha, accepted, phi proposed, logw, indices)."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        self._check(self.lib.smc_get_diagnostics(self.ctx, *[ctypes.byref(p) for p in ptrs]), self.ctx)
+        return [p.value for p in ptrs]
 
     def smc_save(self):
         size = ctypes.c_size_t()

@@ -1,0 +1,56 @@
+"""The allocation-free resampling entry point (smc_resample_indices_static) gives
+the same indices as the context-based smc_resample().
+
+Callers that cannot give the library device memory -- an application whose own
+pool owns all device memory, or a loop that must not risk cudaMalloc's implicit
+synchronisation -- use the static variant, whose scratch is a fixed device array
+inside the library.  This file sorts last so that a run stopping at the first
+failure has already run every other test; it also passes on its own.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_16028_gb300 import build, smcgm
+    build.build()
+    return smcgm.load_library()
+
+
+def test_static_resampling_matches_context_resampling_twice(lib):
+    from paper_2503_16028_gb300 import inputs, smcgm
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 300
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N))
+    s.smc_temper_step()
+    s.smc_resample()
+    _, _, _, logw_ptr, idx_ptr = s.diagnostics_pointers()
+    ref = s.to_host(idx_ptr, N, np.int32)
+    assert ref.min() >= 0 and ref.max() < N and np.all(np.diff(ref) >= 0)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):   # two calls in a row share the static scratch
+        out.fill_(-1)
+        st = lib.smc_resample_indices_static(ctypes.c_void_p(logw_ptr), N, wl["seed"], 0,
+                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+        assert st == smcgm.SMC_OK, lib.smc_last_error(None)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+    s.close()
+
+
+def test_static_resampling_rejects_oversize(lib):
+    from paper_2503_16028_gb300 import smcgm
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    st = lib.smc_resample_indices_static(ctypes.c_void_p(out.data_ptr()), smcgm.SMC_STATIC_RESAMPLE_MAX + 1, 1, 0,
+                                         ctypes.c_void_p(out.data_ptr()), None)
+    assert st == smcgm.SMC_EINVAL
+    assert b"SMC_STATIC_RESAMPLE_MAX" in lib.smc_last_error(None)
