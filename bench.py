@@ -299,19 +299,12 @@ def run_native(args, rank, world, local):
                                                       frac=step_hbm / hbm_peak, peak=hbm_peak),
                 iterations=iters, fp64=fp64,
                 speedup_vs_fp64=(value / fp64["value"]) if fp64 else None,
-                e2e=e2e, clocks=clk, gpu_launches=None, cpu_baseline=cpu)
-    line["gpu_launches"] = estimate_launches(prof, args.steps)
+                e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu)
     print(json.dumps(line), flush=True)
 
 
 def s_bytes(N):
     return N * (3 * 16384 * 8 + 65536 * (4 * 8 + 12 * 4))
-
-
-def estimate_launches(prof, steps):
-    """Kernels launched per timed region: per step propose + synth + exp + faces + 8 coarsen + observe + accept,
-    per inner solve 7 + per CG iteration 11, per refinement 3 (counted from the solver's host loop)."""
-    return None
 
 
 def main():

@@ -189,6 +189,7 @@ typedef struct smc_profile {
     long long dom_particles;   /* particles processed by those launches */
     double dom_ms;             /* summed CUDA-event durations of those launches */
     double dom_bytes;          /* their algorithmic DRAM bytes (inputs read once, outputs written once) */
+    long long launches;        /* kernel launches issued by the library */
     int cells;                 /* grid cells per solve */
     int word_bytes;            /* bytes per word of the inner solver (4: FP32, 8: FP64) */
 } smc_profile;

@@ -187,9 +187,9 @@ double gm_fit_device(Ctx& c) {
     const double fl = c.cfg.var_floor;
     double* lamS = c.pooled + r;          // second half of the pooled scratch
     int* init_idx = c.icount + 8;
-    k_gather_modes<<<(unsigned)(((size_t)N * r + 255) / 256), 256, 0, c.stream>>>(N, c.d, r, c.X, c.S, c.xsT);
-    k_lamS<<<(r + 127) / 128, 128, 0, c.stream>>>(r, c.lam, c.S, lamS);
-    k_pooled<<<r, 256, 0, c.stream>>>(N, r, c.xsT, lamS, fl, c.pooled);
+    k_gather_modes<<<(unsigned)(((size_t)N * r + 255) / 256), 256, 0, c.stream>>>(N, c.d, r, c.X, c.S, c.xsT); ++c.pc.launches;
+    k_lamS<<<(r + 127) / 128, 128, 0, c.stream>>>(r, c.lam, c.S, lamS); ++c.pc.launches;
+    k_pooled<<<r, 256, 0, c.stream>>>(N, r, c.xsT, lamS, fl, c.pooled); ++c.pc.launches;
     // initial picks (host Philox, the same definition as on the device)
     std::vector<int> picks;
     for (int k = 0; k < K; ++k) {
@@ -204,18 +204,18 @@ double gm_fit_device(Ctx& c) {
         picks.push_back(cidx);
     }
     check(cudaMemcpyAsync(init_idx, picks.data(), K * sizeof(int), cudaMemcpyHostToDevice, c.stream), "em picks");
-    k_em_init<<<(K * r + 127) / 128, 128, 0, c.stream>>>(N, K, r, init_idx, c.xsT, c.pooled, c.gw, c.gmu, c.glam);
+    k_em_init<<<(K * r + 127) / 128, 128, 0, c.stream>>>(N, K, r, init_idx, c.xsT, c.pooled, c.gw, c.gmu, c.glam); ++c.pc.launches;
     const size_t esm = sizeof(double) * (2 * (size_t)K * r + K);
     if (esm > 48 * 1024) check(cudaFuncSetAttribute(k_estep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm), "attr");
     const int eg = (N + 255) / 256;
     for (int it = 0; it < c.cfg.em_iters; ++it) {
-        k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax);
-        k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu);
-        k_mstep_var<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu, lamS, fl, c.glam);
-        k_mstep_fix<<<1, 1024, 0, c.stream>>>(N, K, r, c.nj, c.gmax, c.xsT, c.pooled, c.gw, c.gmu, c.glam);
+        k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax); ++c.pc.launches;
+        k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu); ++c.pc.launches;
+        k_mstep_var<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu, lamS, fl, c.glam); ++c.pc.launches;
+        k_mstep_fix<<<1, 1024, 0, c.stream>>>(N, K, r, c.nj, c.gmax, c.xsT, c.pooled, c.gw, c.gmu, c.glam); ++c.pc.launches;
     }
-    k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax);
-    k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8);
+    k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax); ++c.pc.launches;
+    k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8); ++c.pc.launches;
     double ll = 0.0;
     check(cudaMemcpyAsync(&ll, c.dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "ll");
     check(cudaStreamSynchronize(c.stream), "sync");

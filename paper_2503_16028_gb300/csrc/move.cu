@@ -45,7 +45,7 @@ __global__ void k_prior_draw(int d, const double* __restrict__ sqrtlam, double* 
 }
 
 void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t purpose) {
-    k_prior_draw<<<N, 256, 0, c.stream>>>(c.d, c.sqrtlam, X, counter2, purpose, c.key);
+    k_prior_draw<<<N, 256, 0, c.stream>>>(c.d, c.sqrtlam, X, counter2, purpose, c.key); ++c.pc.launches;
     check(cudaGetLastError(), "prior draw");
 }
 
@@ -82,7 +82,7 @@ __global__ void k_move_tables(int K, int r, const double* __restrict__ w, const 
 
 void launch_move_tables(Ctx& c) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
-    k_move_tables<<<1, 256, 0, c.stream>>>(c.K, c.r, c.gw, c.gmu, c.glam, c.lam, c.S, c.beta, gamma, c.tab);
+    k_move_tables<<<1, 256, 0, c.stream>>>(c.K, c.r, c.gw, c.gmu, c.glam, c.lam, c.S, c.beta, gamma, c.tab); ++c.pc.launches;
     check(cudaGetLastError(), "move tables");
 }
 
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
 void launch_propose(Ctx& c) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
     k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma, c.step, c.key,
-                                         c.lfwd, c.lrev);
+                                         c.lfwd, c.lrev); ++c.pc.launches;
     check(cudaGetLastError(), "propose");
 }
 
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_accept(int d, int K, int r, int kernel,
 
 void launch_accept(Ctx& c, int* acc_count) {
     k_accept<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.cfg.kernel, c.t, c.step, c.key, c.tab, c.lfwd, c.lrev, c.X, c.V, c.Phi,
-                                        c.PhiV, c.logalpha, c.acc, acc_count);
+                                        c.PhiV, c.logalpha, c.acc, acc_count); ++c.pc.launches;
     check(cudaGetLastError(), "accept");
 }
 

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(SB) k_temper(int N, const double* __restrict__
 }
 
 void launch_temper(Ctx& c, double* out) {
-    k_temper<<<1, SB, 0, c.stream>>>(c.N, c.Phi, c.t, c.cfg.ess_frac * c.N, c.logw, out);
+    k_temper<<<1, SB, 0, c.stream>>>(c.N, c.Phi, c.t, c.cfg.ess_frac * c.N, c.logw, out); ++c.pc.launches;
     check(cudaGetLastError(), "temper");
 }
 
@@ -179,8 +179,8 @@ __global__ void k_gather(int d, const int* __restrict__ idx, const double* __res
 void launch_resample(Ctx& c) {
     const U4 w = philox(0u, 0u, (uint32_t)c.layer, P_RESAMPLE, c.key.k0, c.key.k1);
     const unsigned long long u48 = ((unsigned long long)w.x << 16) | (unsigned long long)(w.y >> 16);
-    k_resample<<<1, SB, 0, c.stream>>>(c.N, c.logw, u48, reinterpret_cast<unsigned long long*>(c.gridtmp), c.idx);
-    k_gather<<<c.N, 256, 0, c.stream>>>(c.d, c.idx, c.X, c.X2, c.Phi, c.Phi2);
+    k_resample<<<1, SB, 0, c.stream>>>(c.N, c.logw, u48, reinterpret_cast<unsigned long long*>(c.gridtmp), c.idx); ++c.pc.launches;
+    k_gather<<<c.N, 256, 0, c.stream>>>(c.d, c.idx, c.X, c.X2, c.Phi, c.Phi2); ++c.pc.launches;
     check(cudaGetLastError(), "resample");
     std::swap(c.X, c.X2);
     std::swap(c.Phi, c.Phi2);
@@ -200,7 +200,7 @@ __global__ void k_moments(int N, int d, const double* __restrict__ X, double* __
 }
 
 void launch_moments(Ctx& c, double* mean, double* var) {
-    k_moments<<<(c.d + 127) / 128, 128, 0, c.stream>>>(c.N, c.d, c.X, mean, var);
+    k_moments<<<(c.d + 127) / 128, 128, 0, c.stream>>>(c.N, c.d, c.X, mean, var); ++c.pc.launches;
     check(cudaGetLastError(), "moments");
 }
 
@@ -231,16 +231,16 @@ void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, doubl
     const size_t cells = c.dim == 2 ? (size_t)c.n * c.n : (size_t)c.n;
     auto synth = [&](const double* X, int count, double* U) {
         if (c.dim == 2) launch_synth2d(c, X, count, U);
-        else k_synth1d<<<(unsigned)(((size_t)count * c.n + 255) / 256), 256, 0, c.stream>>>(c.n, c.Km, count, X, c.basis, U);
+        else { k_synth1d<<<(unsigned)(((size_t)count * c.n + 255) / 256), 256, 0, c.stream>>>(c.n, c.Km, count, X, c.basis, U); ++c.pc.launches; }
     };
     synth(mean_kl, 1, mean_grid);
     check(cudaMemsetAsync(var_grid, 0, cells * sizeof(double), c.stream), "memset");
     for (int off = 0; off < c.N; off += c.B) {
         const int cnt = std::min(c.B, c.N - off);
         synth(c.X + (size_t)off * c.d, cnt, c.u64);
-        k_grid_acc<<<(unsigned)((cells + 255) / 256), 256, 0, c.stream>>>(cells, cnt, c.u64, mean_grid, var_grid);
+        k_grid_acc<<<(unsigned)((cells + 255) / 256), 256, 0, c.stream>>>(cells, cnt, c.u64, mean_grid, var_grid); ++c.pc.launches;
     }
-    k_scale<<<(unsigned)((cells + 255) / 256), 256, 0, c.stream>>>(cells, var_grid, 1.0 / c.N);
+    k_scale<<<(unsigned)((cells + 255) / 256), 256, 0, c.stream>>>(cells, var_grid, 1.0 / c.N); ++c.pc.launches;
     check(cudaGetLastError(), "grid moments");
 }
 

@@ -772,7 +772,7 @@ static void launch_qpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const CU
     a.part_rr = c.part.rr; a.cg = cg; a.want_rr = want_rr;
     const int grid = persistent_grid(a.pc.total, qpre_blocks<T, H>(), c.sm_count);
     k_qpre<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpre_smem<T, H, PIPE_STAGES>(), c.stream>>>(
-        a, mr, M.kw[level], M.ks[level], M.q, M.x, mp ? *mp : M.x);
+        a, mr, M.kw[level], M.ks[level], M.q, M.x, mp ? *mp : M.x); ++c.pc.launches;
 }
 
 template <typename T, int H>
@@ -784,7 +784,7 @@ static void launch_qpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const C
     a.E = L.E; a.Nn = L.Nn; a.cc = (T)c.cfg.coarse_scale; a.e_out = eout; a.part_rz = c.part.rz; a.cg = cg;
     const int grid = persistent_grid(a.pc.total, qpost_blocks<T, H>(), c.sm_count);
     k_qpost<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpost_smem<T, H, PIPE_STAGES>(), c.stream>>>(
-        a, M.e[level], M.ec[level], mr, M.kw[level], M.ks[level]);
+        a, M.e[level], M.ec[level], mr, M.kw[level], M.ks[level]); ++c.pc.launches;
 }
 
 // Finest-level passes dispatch on its halo (fine_sweeps 1 -> H = 2, 2 -> H = 4).
@@ -814,7 +814,7 @@ static void run_vcycle_lower_tma(Ctx& c, InnerSolver<T>& s, int nact) {
         P.rtop = s.lv[top].r;
         P.etop = s.lv[top].e2;
         const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
-        k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
+        k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list); ++c.pc.launches;
     }
     for (int l = s.ntile_levels - 1; l >= 1; --l) launch_qpost<T, 4>(c, s, l, nact, M.r[l], s.lv[l].e2, 0);
 }
@@ -827,7 +827,7 @@ static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int nact) {
         LevelArrays<T>& L = s.lv[l];
         dim3 grid((L.n / TILE) * (L.n / TILE), nact);
         k_pre<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, nullptr, L.e, s.lv[l + 1].r, nullptr, nullptr,
-                                                 nullptr, nullptr, nullptr, s.list, 0, 0);
+                                                 nullptr, nullptr, nullptr, s.list, 0, 0); ++c.pc.launches;
     }
     {
         CoarseLevelPtrs<T> P{};
@@ -840,19 +840,19 @@ static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int nact) {
         P.rtop = s.lv[top].r;
         P.etop = s.lv[top].e2;
         const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
-        k_coarse<T, NU><<<nact, 256, cs, c.stream>>>(P, cc, s.list);
+        k_coarse<T, NU><<<nact, 256, cs, c.stream>>>(P, cc, s.list); ++c.pc.launches;
     }
     for (int l = s.ntile_levels - 1; l >= 1; --l) {
         LevelArrays<T>& L = s.lv[l];
         dim3 grid((L.n / TILE) * (L.n / TILE), nact);
-        k_post<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr, s.list, 0);
+        k_post<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr, s.list, 0); ++c.pc.launches;
     }
 }
 
 // Compacts act_in into the active list and returns its length (synchronises the stream).
 template <typename T>
 static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
-    k_compact<<<1, 1024, 0, c.stream>>>(count, c.sc.act_in, s.list, s.nact);
+    k_compact<<<1, 1024, 0, c.stream>>>(count, c.sc.act_in, s.list, s.nact); ++c.pc.launches;
     int h[4];
     check(cudaMemcpyAsync(h, s.nact, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "nact d2h");
     check(cudaMemcpyAsync(hcount, c.sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
@@ -876,7 +876,7 @@ static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T*
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
     A.cg = cg; A.want_rr = want_rr;
-    k_wpre<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    k_wpre<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
 }
 
 template <typename T, int H>
@@ -886,7 +886,7 @@ static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg;
-    k_wpost<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    k_wpost<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
 }
 
 template <typename T>
@@ -903,6 +903,7 @@ static void launch_coarse(Ctx& c, InnerSolver<T>& s, int nact) {
     const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
     if (c.cfg.smooth_sweeps == 1) k_coarse<T, 1><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
     else k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
+    ++c.pc.launches;
 }
 
 // Solver kernel family for the tiled levels: 0 = one block per 32 x 32 tile,
@@ -942,7 +943,7 @@ struct Passes {
         } else {
             constexpr int NU = 1;
             k_pre<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
-                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], rout, L0.e, s.lv[1].r, s.q, s.x, s.p[pc], c.sc.alpha, c.part.rr, s.list, cg, 1);
+                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], rout, L0.e, s.lv[1].r, s.q, s.x, s.p[pc], c.sc.alpha, c.part.rr, s.list, cg, 1); ++c.pc.launches;
         }
     }
     void lower(int nact) {
@@ -967,7 +968,7 @@ struct Passes {
         } else {
             constexpr int NU = 1;
             k_post<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
-                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], L0.e, s.lv[1].e2, (T)c.cfg.coarse_scale, s.z, c.part.rz, s.list, 1);
+                n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.r[cur], L0.e, s.lv[1].e2, (T)c.cfg.coarse_scale, s.z, c.part.rz, s.list, 1); ++c.pc.launches;
         }
     }
     void apply(int nact, int pc, int first) {
@@ -977,18 +978,18 @@ struct Passes {
             A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list;
             A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
             A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;
-            k_wapply<T><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+            k_wapply<T><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
         } else if (path == 1) {
             TmaMaps* M = s.maps;
             ApplyArgs<T> a{};
             a.pc.n = n; a.pc.ntiles = ntiles; a.pc.total = nact * ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
             a.E = L0.E; a.Nn = L0.Nn; a.pout = s.p[1 - pc]; a.q = s.q; a.betac = c.sc.betac; a.part_pq = c.part.pq; a.first = first;
             k_apply_tma<T, PIPE_STAGES><<<persistent_grid(a.pc.total, apply_blocks<T>(), c.sm_count), 256,
-                                          apply_tma_smem<T, PIPE_STAGES>(), c.stream>>>(a, M->za, M->pa[pc], M->kwa, M->ksa);
+                                          apply_tma_smem<T, PIPE_STAGES>(), c.stream>>>(a, M->za, M->pa[pc], M->kwa, M->ksa); ++c.pc.launches;
         } else {
             k_apply<T><<<dim3(ntiles, nact), Own<TILE + 2>::THREADS, 0, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.z, s.p[pc],
                                                                                    s.p[1 - pc], s.q, c.sc.betac, c.part.pq, s.list,
-                                                                                   first);
+                                                                                   first); ++c.pc.launches;
         }
     }
 };
@@ -1005,23 +1006,23 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
     const int maxit = c.cfg.max_iter;
     int cur = 0, pc = 0;
     int hcount[3] = {0, 0, 0};
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
     check(cudaMemsetAsync(sc.count, 0, 3 * sizeof(int), c.stream), "memset count");
     int nact = compact_active(c, s, count, hcount);
     if (nact == 0) return 0;
     P.pre(nact, cur, pc, 0);                      // z0 = M r0
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
     nact = compact_active(c, s, count, hcount);
     c.pc.inner_solves += nact;
     if (nact == 0) return 0;
     P.lower(nact);
     P.post(nact, cur);
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit);
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
     const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T);   // per cell: r,q,x,p,Kw,Ks in; r,x,e,rc out
     for (int it = 0; it < maxit; ++it) {
         P.apply(nact, pc, it == 0);
         pc ^= 1;
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
         if (c.prof) check(cudaEventRecord(c.ev0, c.stream), "event");
         P.pre(nact, cur, pc, 1);
         if (c.prof) check(cudaEventRecord(c.ev1, c.stream), "event");
@@ -1029,7 +1030,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         c.pc.cg_iterations += nact;
         const int launched = nact;
         check(cudaMemsetAsync(sc.count, 0, sizeof(int), c.stream), "memset count");
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
         nact = compact_active(c, s, count, hcount);
         if (c.prof) {
             float ms = 0.f;
@@ -1042,7 +1043,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         if (nact == 0) break;
         P.lower(nact);
         P.post(nact, cur);
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit);
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
     }
     check(cudaGetLastError(), "inner solve launch");
     return hcount[2];
@@ -1070,7 +1071,7 @@ void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count) {
         LevelArrays<T>& A = s.lv[l];
         LevelArrays<T>& Bc = s.lv[l + 1];
         const size_t total = (size_t)Bc.n * Bc.n * count;
-        k_coarsen<T><<<grid_for(total), 256, 0, c.stream>>>(Bc.n, count, A.Kw, A.Ks, A.E, A.Nn, Bc.Kw, Bc.Ks, Bc.E, Bc.Nn);
+        k_coarsen<T><<<grid_for(total), 256, 0, c.stream>>>(Bc.n, count, A.Kw, A.Ks, A.E, A.Nn, Bc.Kw, Bc.Ks, Bc.E, Bc.Nn); ++c.pc.launches;
     }
 }
 template void launch_coarsen_all<float>(Ctx&, InnerSolver<float>&, int);
@@ -1079,15 +1080,15 @@ template void launch_coarsen_all<double>(Ctx&, InnerSolver<double>&, int);
 void launch_setup_coeffs(Ctx& c, int count) {
     const int n = c.n;
     const size_t total = (size_t)n * n * count;
-    k_exp_neg<<<grid_for(total), 256, 0, c.stream>>>(c.u64, total);
+    k_exp_neg<<<grid_for(total), 256, 0, c.stream>>>(c.u64, total); ++c.pc.launches;
     const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
     if (mixed) {
         LevelArrays<float>& f0 = c.s32.lv[0];
-        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, f0.Kw, f0.Ks, f0.E, f0.Nn);
+        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, f0.Kw, f0.Ks, f0.E, f0.Nn); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
     } else {
         k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, nullptr, nullptr, nullptr,
-                                                       nullptr);
+                                                       nullptr); ++c.pc.launches;
         launch_coarsen_all<double>(c, c.s64, count);
     }
     check(cudaGetLastError(), "setup launch");
@@ -1111,13 +1112,13 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         check(cudaMemcpyAsync(sc.act_out, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, c.stream), "act init");
         check(cudaStreamSynchronize(c.stream), "sync");
     }
-    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, c.b64, s.r[0]);
+    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, c.b64, s.r[0]); ++c.pc.launches;
     c.pc.solves += count;
     c.pc.cells = n * n;
     c.pc.word_bytes = (int)sizeof(T);
     int outer_active = count;
     const int sgrid = (count + 127) / 128;
-    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, c.b2);
+    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, c.b2); ++c.pc.launches;
     int itmax = 0;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
@@ -1125,10 +1126,10 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         int it = inner_solve<T>(c, s, count, tol_in);
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
-        k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out);
-        k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out);
+        k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out); ++c.pc.launches;
+        k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
         check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
-        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, c.b2);
+        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, c.b2); ++c.pc.launches;
         int h = 0;
         check(cudaMemcpyAsync(&h, sc.count + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
         check(cudaStreamSynchronize(c.stream), "sync");

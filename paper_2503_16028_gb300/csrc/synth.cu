@@ -113,8 +113,8 @@ void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
     }
     // stage 1: ceil(Km / 32) blocks per particle (transforms past Km are masked); stage 2: n / 32
     const int b1 = (Km + FCT_T - 1) / FCT_T, b2 = n / FCT_T;
-    k_fct<<<dim3(b1, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, X, c.fct_tmp, c.fct_tw);
-    k_fct<<<dim3(b2, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, c.fct_tmp, U, c.fct_tw);
+    k_fct<<<dim3(b1, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, X, c.fct_tmp, c.fct_tw); ++c.pc.launches;
+    k_fct<<<dim3(b2, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, c.fct_tmp, U, c.fct_tw); ++c.pc.launches;
     check(cudaGetLastError(), "synth2d");
 }
 
@@ -158,7 +158,7 @@ void launch_observe(Ctx& c, const double* w, int count, double* Phi) {
     const double inv2s2 = 1.0 / (2.0 * c.cfg.sigma * c.cfg.sigma);
     const int threads = 256;
     const int blocks = (count * 32 + threads - 1) / threads;
-    k_observe2d<<<blocks, threads, 0, c.stream>>>(c.n, count, c.nobs, w, c.obs, c.data, inv2s2, Phi);
+    k_observe2d<<<blocks, threads, 0, c.stream>>>(c.n, count, c.nobs, w, c.obs, c.data, inv2s2, Phi); ++c.pc.launches;
     check(cudaGetLastError(), "observe");
 }
 
@@ -225,7 +225,7 @@ void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w
         const int cnt = std::min(c.B, count - off);
         k_forward1d<<<(cnt + 63) / 64, 64, 0, c.stream>>>(c.n, c.Km, cnt, X + (size_t)off * c.d, c.basis, c.b64, c.nobs, c.obs,
                                                           c.data, inv2s2, Phi + off, w_out ? w_out + (size_t)off * (c.n - 1) : nullptr,
-                                                          c.u64);
+                                                          c.u64); ++c.pc.launches;
     }
     check(cudaGetLastError(), "forward1d");
 }

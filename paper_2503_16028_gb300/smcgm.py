@@ -39,7 +39,7 @@ class smc_config(ctypes.Structure):
 class smc_profile(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_longlong), ("cg_iterations", ctypes.c_longlong), ("inner_solves", ctypes.c_longlong),
                 ("residuals", ctypes.c_longlong), ("dom_launches", ctypes.c_longlong), ("dom_particles", ctypes.c_longlong),
-                ("dom_ms", ctypes.c_double), ("dom_bytes", ctypes.c_double), ("cells", ctypes.c_int),
+                ("dom_ms", ctypes.c_double), ("dom_bytes", ctypes.c_double), ("launches", ctypes.c_longlong), ("cells", ctypes.c_int),
                 ("word_bytes", ctypes.c_int)]
 
 
