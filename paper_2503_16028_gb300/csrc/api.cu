@@ -130,9 +130,17 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
         C.u64 = P.take<double>(bn);
         C.fct_tw = P.take<double>(n);
         C.fct_tmp = P.take<double>((size_t)B * n * Km);
-        C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
-        C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
-        C.w64 = P.take<double>(bn);
+        if (cfg.precision == SMC_P_FP32_REFINE) {
+            C.Kwlo = P.take<float>(bn); C.Kslo = P.take<float>(bn);
+            C.Elo = P.take<float>((size_t)B * n); C.Nlo = P.take<float>((size_t)B * n);
+            C.w64 = P.take<double>(bn);
+            C.bhi = P.take<float>(cells); C.blo = P.take<float>(cells);
+            C.exptab = P.take<float>(128);
+        } else {
+            C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
+            C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
+            C.w64 = P.take<double>(bn);
+        }
         const int ntiles = (n / 16) * (n / 16);   // the finest tiled level's tiles (16 x 16 warp tiles or fewer)
         C.part.ntiles = ntiles;
         C.part.rr = P.take<double>((size_t)B * ntiles); C.part.rz = P.take<double>((size_t)B * ntiles);
@@ -335,6 +343,34 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     check(cudaMemcpyAsync(c.sqrtlam, sq.data(), sq.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.basis, basis.data(), basis.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.b64, b.data(), b.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
+    std::vector<float> bhi, blo;
+    if (c.bhi) {   // df32 split of the right-hand side: hi = round(b), lo = round(b - hi)
+        bhi.resize(b.size());
+        blo.resize(b.size());
+        for (size_t i = 0; i < b.size(); ++i) {
+            bhi[i] = (float)b[i];
+            blo[i] = (float)(b[i] - (double)bhi[i]);
+        }
+        check(cudaMemcpyAsync(c.bhi, bhi.data(), bhi.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+        check(cudaMemcpyAsync(c.blo, blo.data(), blo.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+    }
+    std::vector<float> etab;
+    if (c.exptab) {   // df32 exponential: 2^(j/64) split into pairs, ln2/64 in three parts
+        etab.resize(128);
+        for (int j = 0; j < 64; ++j) {
+            const double v = std::exp2(j / 64.0);
+            etab[2 * j] = (float)v;
+            etab[2 * j + 1] = (float)(v - (double)etab[2 * j]);
+        }
+        const double C = std::log(2.0) / 64.0;
+        int ex = 0;
+        const double f = std::frexp(C, &ex);
+        const double c1 = std::ldexp(std::nearbyint(std::ldexp(f, 11)), ex - 11);   // 11 significant bits
+        c.expc.c1 = (float)c1;
+        c.expc.c2 = (float)(C - c1);
+        c.expc.c3 = (float)(C - c1 - (double)c.expc.c2);
+        check(cudaMemcpyAsync(c.exptab, etab.data(), etab.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+    }
     check(cudaMemcpyAsync(c.obs, c.obs_h.data(), c.obs_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.data, c.data_h.data(), c.data_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.S, S.data(), S.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/smcgm.h"
+#include "df32.cuh"
 
 namespace smcgm {
 
@@ -67,10 +68,10 @@ struct SolverScalars {       // per particle, device
 };
 
 // TMA descriptors of the tiled levels (boxes described in tiles.cuh).
+// Tensor maps of the TMA-staged smoothing kernels (FP32 inner solver).
 struct TmaMaps {
     CUtensorMap kw[12], ks[12], r[12], e[12], ec[12];   // per tiled level
     CUtensorMap r0[2], q, x, p[2];                       // finest level, CG vectors
-    CUtensorMap kwa, ksa, za, pa[2];                      // finest level, operator application
 };
 
 template <typename T>
@@ -131,6 +132,12 @@ struct Ctx {
     double *xsT = nullptr, *resp = nullptr, *nj = nullptr, *pooled = nullptr, *lse = nullptr, *gmax = nullptr;
     // forward-solve batch arrays
     double *u64 = nullptr, *Kw64 = nullptr, *Ks64 = nullptr, *E64 = nullptr, *N64 = nullptr, *w64 = nullptr;
+    // mixed precision: FP64-accurate faces and right-hand side as df32 pairs (the
+    // high parts of the faces are the inner solver's FP32 faces); the solution stays FP64
+    float *Kwlo = nullptr, *Kslo = nullptr, *Elo = nullptr, *Nlo = nullptr;
+    float *bhi = nullptr, *blo = nullptr;
+    float* exptab = nullptr;   // 2^(j/64), j < 64, as df32 pairs (the df32 exponential)
+    ExpConsts expc{};
     InnerSolver<float> s32;
     InnerSolver<double> s64;
     Partials part{};

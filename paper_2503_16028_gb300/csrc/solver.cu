@@ -25,6 +25,7 @@
 #include "smcgm_internal.cuh"
 #include "common.cuh"
 #include "tma.cuh"
+#include "df32.cuh"
 
 namespace smcgm {
 
@@ -38,9 +39,24 @@ __global__ void k_exp_neg(double* __restrict__ u, size_t total) {
     for (; i < total; i += stride) u[i] = exp(-u[i]);
 }
 
-__global__ void k_faces(int n, int count, const double* __restrict__ s, double* __restrict__ Kw, double* __restrict__ Ks,
-                        double* __restrict__ E, double* __restrict__ Nn, float* __restrict__ Kw32, float* __restrict__ Ks32,
-                        float* __restrict__ E32, float* __restrict__ Nn32) {
+// Stores one face coefficient: FP64, or (mixed precision) its df32 split into
+// the inner solver's FP32 face hi = round(v) and lo = round(v - hi).
+struct FaceOut {
+    double* f64;
+    float *hi, *lo;
+    __device__ void put(size_t i, double v) const {
+        if (f64) f64[i] = v;
+        if (hi) {
+            const float h = __double2float_rn(v);
+            hi[i] = h;
+            if (lo) lo[i] = __double2float_rn(v - (double)h);
+        }
+    }
+};
+
+// Harmonic face coefficients from s = exp(-u): west and south faces
+// 2 / (s_c + s_nb), wall faces 2 / s_c (Dirichlet ghost on the wall).
+__global__ void k_faces(int n, int count, const double* __restrict__ s, FaceOut Kw, FaceOut Ks, FaceOut E, FaceOut Nn) {
     const size_t nn = (size_t)n * n;
     const size_t total = nn * count;
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,22 +67,68 @@ __global__ void k_faces(int n, int count, const double* __restrict__ s, double* 
         const int i = c % n, j = c / n;
         const double* sp = s + p * nn;
         const double sc = sp[c];
-        double kw = (i == 0) ? 2.0 * recip_nr(sc) : 2.0 * recip_nr(sc + sp[c - 1]);
-        double ks = (j == 0) ? 2.0 * recip_nr(sc) : 2.0 * recip_nr(sc + sp[c - n]);
-        Kw[t] = kw;
-        Ks[t] = ks;
-        if (Kw32) { Kw32[t] = (float)kw; Ks32[t] = (float)ks; }
-        if (i == n - 1) {
-            double e = 2.0 * recip_nr(sc);
-            E[p * n + j] = e;
-            if (E32) E32[p * n + j] = (float)e;
-        }
-        if (j == n - 1) {
-            double e = 2.0 * recip_nr(sc);
-            Nn[p * n + i] = e;
-            if (Nn32) Nn32[p * n + i] = (float)e;
-        }
+        Kw.put(t, (i == 0) ? 2.0 * recip_nr(sc) : 2.0 * recip_nr(sc + sp[c - 1]));
+        Ks.put(t, (j == 0) ? 2.0 * recip_nr(sc) : 2.0 * recip_nr(sc + sp[c - n]));
+        if (i == n - 1) E.put(p * n + j, 2.0 * recip_nr(sc));
+        if (j == n - 1) Nn.put(p * n + i, 2.0 * recip_nr(sc));
     }
+}
+
+// Mixed precision: s = exp(-u) and the harmonic faces in df32 (FP32 pipes
+// only; the FP64 unit of GB300 is ~58x slower).  A block covers a 32 x 8 tile
+// of one particle: s on the tile plus its west column and south row goes to
+// shared memory, then each thread forms its cell's west and south faces
+// 2 / (s_c + s_nb) (2 / s_c on a wall) and the east / north wall faces.  The
+// high parts are the inner solver's FP32 faces, the low parts complete them
+// to ~1e-14 relative for the FP64-accurate residual.  |u| >= 64 (beyond the
+// FP32 range of e^u) sets err[1] and is reported by the host.
+constexpr int FX = 32, FY = 8;
+__global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const double* __restrict__ u, const float2* __restrict__ exptab,
+                                                      ExpConsts ec, float* __restrict__ Kwh, float* __restrict__ Kwl,
+                                                      float* __restrict__ Ksh, float* __restrict__ Ksl, float* __restrict__ Eh,
+                                                      float* __restrict__ El, float* __restrict__ Nh, float* __restrict__ Nl,
+                                                      int* __restrict__ err) {
+    __shared__ float2 tab[64];
+    __shared__ float2 S[FY + 1][FX + 1];
+    const int p = blockIdx.y;
+    const int tpr = n / FX;
+    const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
+    if (threadIdx.x < 64) tab[threadIdx.x] = exptab[threadIdx.x];
+    __syncthreads();
+    const size_t nn = (size_t)n * n, base = (size_t)p * nn;
+    const double* up = u + base;
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < (FY + 1) * (FX + 1); idx += blockDim.x) {
+        const int ly = idx / (FX + 1), lx = idx % (FX + 1);
+        const int gi = tx * FX + lx - 1, gj = ty * FY + ly - 1;
+        float2 v = make_float2(1.f, 0.f);
+        if (gi >= 0 && gj >= 0) {
+            const double uv = up[(size_t)gj * n + gi];
+            const unsigned ex = ((unsigned)(__double_as_longlong(uv) >> 52)) & 0x7ffu;
+            if (ex >= 1023u + 6u) {
+                bad = true;                               // |u| >= 64
+            } else {
+                const df32 sv = df_exp(df_neg(df_from_double_bits(uv)), tab, ec);
+                v = make_float2(sv.hi, sv.lo);
+            }
+        }
+        S[ly][lx] = v;
+    }
+    if (bad) atomicExch(&err[1], 1);
+    __syncthreads();
+    const int lx = threadIdx.x % FX, ly = threadIdx.x / FX;
+    const int i = tx * FX + lx, j = ty * FY + ly;
+    const size_t t = base + (size_t)j * n + i;
+    const float2 c2 = S[ly + 1][lx + 1];
+    const df32 sc{c2.x, c2.y};
+    const df32 wall = df_two_over(sc);
+    df32 kw = wall, ks = wall;
+    if (i > 0) { const float2 w2 = S[ly + 1][lx]; kw = df_two_over(df_add(sc, df32{w2.x, w2.y})); }
+    if (j > 0) { const float2 s2 = S[ly][lx + 1]; ks = df_two_over(df_add(sc, df32{s2.x, s2.y})); }
+    Kwh[t] = kw.hi; Kwl[t] = kw.lo;
+    Ksh[t] = ks.hi; Ksl[t] = ks.lo;
+    if (i == n - 1) { Eh[(size_t)p * n + j] = wall.hi; El[(size_t)p * n + j] = wall.lo; }
+    if (j == n - 1) { Nh[(size_t)p * n + i] = wall.hi; Nl[(size_t)p * n + i] = wall.lo; }
 }
 
 // Galerkin coarsening for piecewise-constant prolongation.
@@ -373,9 +435,8 @@ __global__ void __launch_bounds__(Own<TILE + 2>::THREADS) k_apply(
 }
 
 }  // namespace smcgm
-#include "tiles.cuh"
-#include "quads.cuh"
 #include "wtiles.cuh"
+#include "wtma.cuh"
 namespace smcgm {
 
 // ------------------------------------------------------------------------
@@ -610,6 +671,53 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* __restric
     if (threadIdx.x == 0) part_res[(size_t)pb * gridDim.x + blockIdx.x] = tot;
 }
 
+// Mixed precision: the FP64-accurate residual b - A w, with w in FP64 and the
+// faces and b as df32 pairs, evaluated as b - sum over faces of k_f (w_c - w_nb)
+// (w_nb = 0 beyond a wall).  Only the differences w_c - w_nb use the FP64
+// unit (exact for neighbouring values, by Sterbenz's lemma); they are split
+// into df32 by bit manipulation and the products and sums run in df32 on the
+// FP32 pipes (error ~2^-47 of the face fluxes, whose sum is ~200 |b| at 256^2).
+// Stored in FP32 with the partial |res|^2 per tile, like the FP64 residual.
+__global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __restrict__ Kwh, const float* __restrict__ Kwl,
+                                                      const float* __restrict__ Ksh, const float* __restrict__ Ksl,
+                                                      const float* __restrict__ Eh, const float* __restrict__ El,
+                                                      const float* __restrict__ Nh, const float* __restrict__ Nl,
+                                                      const double* __restrict__ w, const float* __restrict__ bhi,
+                                                      const float* __restrict__ blo, float* __restrict__ rout,
+                                                      double* __restrict__ part_res, const int* __restrict__ act) {
+    __shared__ double red[32];
+    const int pb = blockIdx.y;
+    if (!act[pb]) return;
+    const int tpr = n / TILE;
+    const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
+    const size_t nn = (size_t)n * n, base = (size_t)pb * nn;
+    const double* wp = w + base;
+    double acc2 = 0.0;
+    for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
+        const int i = tx * TILE + idx % TILE, j = ty * TILE + idx / TILE;
+        const int c = j * n + i;
+        const double wc = wp[c];
+        const double dw = i > 0 ? wc - wp[c - 1] : wc;
+        const double de = i < n - 1 ? wc - wp[c + 1] : wc;
+        const double ds = j > 0 ? wc - wp[c - n] : wc;
+        const double dn = j < n - 1 ? wc - wp[c + n] : wc;
+        const df32 kw{Kwh[base + c], Kwl[base + c]};
+        const df32 ke = i < n - 1 ? df32{Kwh[base + c + 1], Kwl[base + c + 1]} : df32{Eh[(size_t)pb * n + j], El[(size_t)pb * n + j]};
+        const df32 ks{Ksh[base + c], Ksl[base + c]};
+        const df32 kn = j < n - 1 ? df32{Ksh[base + c + n], Ksl[base + c + n]} : df32{Nh[(size_t)pb * n + i], Nl[(size_t)pb * n + i]};
+        df32 aw = df_mul(kw, df_from_double_bits(dw));
+        aw = df_add(aw, df_mul(ke, df_from_double_bits(de)));
+        aw = df_add(aw, df_mul(ks, df_from_double_bits(ds)));
+        aw = df_add(aw, df_mul(kn, df_from_double_bits(dn)));
+        const df32 res = df_sub_acc(df32{bhi[c], blo[c]}, aw);
+        const float r = __fadd_rn(res.hi, res.lo);
+        rout[base + c] = r;
+        acc2 += (double)r * (double)r;
+    }
+    double tot = block_sum(acc2, red);
+    if (threadIdx.x == 0) part_res[(size_t)pb * gridDim.x + blockIdx.x] = tot;
+}
+
 // r = b for every particle (the residual of w = 0), in the inner precision.
 template <typename T>
 __global__ void k_fill_rhs(size_t nn, int count, const double* __restrict__ b, T* __restrict__ r) {
@@ -680,18 +788,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 3-D map over a particle-major [B][n][n] array, box bx x by x 1 (x innermost).
-template <typename T>
-static CUtensorMap make_map(const T* base, int n, int B, int bx, int by) {
+static inline int wtiles(int n) { return (n / WT) * (n / WT); }
+
+// 3-D map over a particle-major [B][n][n] FP32 array, box bx x by x 1 (x innermost).
+static CUtensorMap make_map(const float* base, int n, int B, int bx, int by) {
     CUtensorMap m;
     cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B};
-    cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(T), (cuuint64_t)n * n * sizeof(T)};
+    cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(float), (cuuint64_t)n * n * sizeof(float)};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    const CUresult r = tensor_map_encoder()(&m, dt, 3, const_cast<T*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+                                            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
     return m;
 }
@@ -699,124 +807,90 @@ static CUtensorMap make_map(const T* base, int n, int B, int bx, int by) {
 // Halo (2 nu) of the tiled level l: the finest level uses fine_sweeps, the others smooth_sweeps.
 static inline int level_halo(const Ctx& c, int l) { return 2 * (l == 0 ? c.cfg.fine_sweeps : c.cfg.smooth_sweeps); }
 
+template <int H>
+static void level_maps(TmaMaps& M, InnerSolver<float>& s, int B, int l) {
+    using G = TGeo<H>;
+    LevelArrays<float>& L = s.lv[l];
+    M.kw[l] = make_map(L.Kw, L.n, B, G::KWX, G::RW);
+    M.ks[l] = make_map(L.Ks, L.n, B, G::BX, G::RW + 1);
+    M.e[l] = make_map(L.e, L.n, B, G::BX, G::RW);
+    if (l > 0) M.r[l] = make_map(L.r, L.n, B, G::BX, G::RW);
+    M.ec[l] = make_map(s.lv[l + 1].e2, s.lv[l + 1].n, B, G::CX, G::CY);
+    if (l == 0) {
+        for (int k = 0; k < 2; ++k) {
+            M.r0[k] = make_map(s.r[k], L.n, B, G::BX, G::RW);
+            M.p[k] = make_map(s.p[k], L.n, B, WT, WT);
+        }
+        M.q = make_map(s.q, L.n, B, G::BX, G::RW);
+        M.x = make_map(s.x, L.n, B, WT, WT);
+    }
+}
+
+// Tensor maps of the TMA-staged kernels (FP32 inner solver, finest level only).
 template <typename T>
 void build_tma_maps(Ctx& c, InnerSolver<T>& s) {
-    if (!s.maps) s.maps = new TmaMaps();
-    TmaMaps& M = *s.maps;
-    const int B = c.B;
-    for (int l = 0; l < s.ntile_levels; ++l) {
-        LevelArrays<T>& L = s.lv[l];
-        const int H = level_halo(c, l);
-        const int RY = TT + 2 * H;
-        M.kw[l] = make_map(L.Kw, L.n, B, 44, RY);
-        M.ks[l] = make_map(L.Ks, L.n, B, 40, RY + 1);
-        M.e[l] = make_map(L.e, L.n, B, 40, RY);
-        if (l > 0) M.r[l] = make_map(L.r, L.n, B, 40, RY);
-        M.ec[l] = make_map(s.lv[l + 1].e2, s.lv[l + 1].n, B, 24, RY / 2);
+    if constexpr (sizeof(T) == 4) {
+        if (!s.maps) s.maps = new TmaMaps();
+        if (s.lv[0].n % WT) return;
+        if (level_halo(c, 0) == 2) level_maps<2>(*s.maps, s, c.B, 0);
+        else level_maps<4>(*s.maps, s, c.B, 0);
     }
-    LevelArrays<T>& L0 = s.lv[0];
-    const int n = L0.n;
-    const int RY0 = TT + 2 * level_halo(c, 0);
-    for (int k = 0; k < 2; ++k) {
-        M.r0[k] = make_map(s.r[k], n, B, 40, RY0);
-        M.p[k] = make_map(s.p[k], n, B, TT, TT);
-        M.pa[k] = make_map(s.p[k], n, B, ApplyStage<T>::AC, ApplyStage<T>::AR);
-    }
-    M.q = make_map(s.q, n, B, 40, RY0);
-    M.x = make_map(s.x, n, B, TT, TT);
-    M.za = make_map(s.z, n, B, ApplyStage<T>::AC, ApplyStage<T>::AR);
-    M.kwa = make_map(L0.Kw, n, B, ApplyStage<T>::FKW, TT);
-    M.ksa = make_map(L0.Ks, n, B, TT, TT + 1);
 }
 template void build_tma_maps<float>(Ctx&, InnerSolver<float>&);
 template void build_tma_maps<double>(Ctx&, InnerSolver<double>&);
 
-constexpr int PIPE_STAGES = 2;
-
-// Resident blocks per SM of a pipelined kernel (queried once, with its shared-memory opt-in).
+// Resident blocks per SM of a staged kernel (queried once, with its shared-memory opt-in).
 template <typename K>
-static int pipe_occupancy(K kernel, int threads, size_t smem) {
+static int staged_occupancy(K kernel, size_t smem) {
     check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
     int b = 0;
-    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem), "occupancy");
+    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 32 * TW_WARPS, smem), "occupancy");
     return std::max(1, b);
 }
 
-template <typename T, int H>
-static int qpre_blocks() {
-    static int b = pipe_occupancy(k_qpre<T, H, PIPE_STAGES>, QGeo<T, H>::THREADS, qpre_smem<T, H, PIPE_STAGES>());
-    return b;
-}
-template <typename T, int H>
-static int qpost_blocks() {
-    static int b = pipe_occupancy(k_qpost<T, H, PIPE_STAGES>, QGeo<T, H>::THREADS, qpost_smem<T, H, PIPE_STAGES>());
-    return b;
-}
-template <typename T>
-static int apply_blocks() {
-    static int b = pipe_occupancy(k_apply_tma<T, PIPE_STAGES>, 256, apply_tma_smem<T, PIPE_STAGES>());
-    return b;
+static inline int persistent_grid(int total_warps, int per_sm, int sms) {
+    const int blocks = (total_warps + TW_WARPS - 1) / TW_WARPS;
+    return std::max(1, std::min(blocks, per_sm * sms));
 }
 
-static inline int persistent_grid(int total, int per_sm, int sms) { return std::max(1, std::min(total, per_sm * sms)); }
-
-// Pre-smoothing pass on tiled level `level` (halo H); cg = 1 only on the finest level.
-template <typename T, int H>
-static void launch_qpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const CUtensorMap& mr, T* rout, int cg, int want_rr,
-                        const CUtensorMap* mp) {
-    LevelArrays<T>& L = s.lv[level];
+// Pre-smoothing pass of the TMA-staged path on level `level`; cg = 1 only on the finest level.
+template <int H, bool CG, int MINB>
+static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
+                          int want_rr, int pc) {
+    static const int per_sm = staged_occupancy(k_tpre<H, CG, MINB>, tpre_smem<H, CG>());
+    LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
-    QPreArgs<T> a{};
-    a.pc.n = L.n; a.pc.ntiles = (L.n / TT) * (L.n / TT); a.pc.total = nact * a.pc.ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
-    a.E = L.E; a.Nn = L.Nn; a.rout = rout; a.e_out = L.e; a.rc = s.lv[level + 1].r; a.x = s.x; a.alpha = c.sc.alpha;
-    a.part_rr = c.part.rr; a.cg = cg; a.want_rr = want_rr;
-    const int grid = persistent_grid(a.pc.total, qpre_blocks<T, H>(), c.sm_count);
-    k_qpre<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpre_smem<T, H, PIPE_STAGES>(), c.stream>>>(
-        a, mr, M.kw[level], M.ks[level], M.q, M.x, mp ? *mp : M.x); ++c.pc.launches;
+    WPreArgs<float> A{};
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = s.p[pc];
+    A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
+    A.cg = CG ? 1 : 0; A.want_rr = want_rr;
+    k_tpre<H, CG, MINB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpre_smem<H, CG>(), c.stream>>>(
+        A, M.kw[level], M.ks[level], mr, M.q, M.x, M.p[pc]); ++c.pc.launches;
+}
+template <int H, bool CG>
+static void launch_tpre(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
+                        int want_rr, int pc) {
+    // blocks per SM asked of the register allocator: 3 (<= 168 registers, 12 warps) on a
+    // 20 x 20 region, 2 on the 24 x 24 region of two sweeps
+    launch_tpre_b<H, CG, H == 2 ? 3 : 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
 }
 
-template <typename T, int H>
-static void launch_qpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const CUtensorMap& mr, T* eout, int cg) {
-    LevelArrays<T>& L = s.lv[level];
+template <int H, bool CG, int MINB>
+static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
+    static const int per_sm = staged_occupancy(k_tpost<H, CG, MINB>, tpost_smem<H>());
+    LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
-    QPostArgs<T> a{};
-    a.pc.n = L.n; a.pc.ntiles = (L.n / TT) * (L.n / TT); a.pc.total = nact * a.pc.ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
-    a.E = L.E; a.Nn = L.Nn; a.cc = (T)c.cfg.coarse_scale; a.e_out = eout; a.part_rz = c.part.rz; a.cg = cg;
-    const int grid = persistent_grid(a.pc.total, qpost_blocks<T, H>(), c.sm_count);
-    k_qpost<T, H, PIPE_STAGES><<<grid, QGeo<T, H>::THREADS, qpost_smem<T, H, PIPE_STAGES>(), c.stream>>>(
-        a, M.e[level], M.ec[level], mr, M.kw[level], M.ks[level]); ++c.pc.launches;
+    WPostArgs<float> A{};
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
+    A.cc = (float)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = CG ? 1 : 0;
+    k_tpost<H, CG, MINB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpost_smem<H>(), c.stream>>>(
+        A, M.kw[level], M.ks[level], mr, M.e[level], M.ec[level]); ++c.pc.launches;
 }
-
-// Finest-level passes dispatch on its halo (fine_sweeps 1 -> H = 2, 2 -> H = 4).
-template <typename T>
-static void fine_pre(Ctx& c, InnerSolver<T>& s, int nact, const CUtensorMap& mr, T* rout, int cg, const CUtensorMap* mp) {
-    if (c.cfg.fine_sweeps == 1) launch_qpre<T, 2>(c, s, 0, nact, mr, rout, cg, 1, mp);
-    else launch_qpre<T, 4>(c, s, 0, nact, mr, rout, cg, 1, mp);
-}
-template <typename T>
-static void fine_post(Ctx& c, InnerSolver<T>& s, int nact, const CUtensorMap& mr, T* eout) {
-    if (c.cfg.fine_sweeps == 1) launch_qpost<T, 2>(c, s, 0, nact, mr, eout, 1);
-    else launch_qpost<T, 4>(c, s, 0, nact, mr, eout, 1);
-}
-
-template <typename T>
-static void run_vcycle_lower_tma(Ctx& c, InnerSolver<T>& s, int nact) {
-    TmaMaps& M = *s.maps;
-    for (int l = 1; l < s.ntile_levels; ++l) launch_qpre<T, 4>(c, s, l, nact, M.r[l], nullptr, 0, 0, nullptr);
-    {
-        CoarseLevelPtrs<T> P{};
-        const int top = s.ntile_levels;
-        P.ntop = s.lv[top].n;
-        P.nlev = s.nlev - top;
-        for (int l = 0; l < P.nlev; ++l) {
-            P.Kw[l] = s.lv[top + l].Kw; P.Ks[l] = s.lv[top + l].Ks; P.E[l] = s.lv[top + l].E; P.Nn[l] = s.lv[top + l].Nn;
-        }
-        P.rtop = s.lv[top].r;
-        P.etop = s.lv[top].e2;
-        const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
-        k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list); ++c.pc.launches;
-    }
-    for (int l = s.ntile_levels - 1; l >= 1; --l) launch_qpost<T, 4>(c, s, l, nact, M.r[l], s.lv[l].e2, 0);
+template <int H, bool CG>
+static void launch_tpost(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
+    launch_tpost_b<H, CG, H == 2 ? 3 : 2>(c, s, level, nact, mr, r, eout);
 }
 
 template <typename T, int NU>
@@ -857,16 +931,16 @@ static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
     check(cudaMemcpyAsync(h, s.nact, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "nact d2h");
     check(cudaMemcpyAsync(hcount, c.sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
     check(cudaStreamSynchronize(c.stream), "sync");
-    int err = 0;
-    check(cudaMemcpy(&err, c.dev_err, sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
-    if (err) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
+    int err[2] = {0, 0};
+    check(cudaMemcpy(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
+    if (err[0]) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
+    if (err[1]) throw CudaError{cudaErrorInvalidValue, "log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};
     return h[0];
 }
 
 // ---------------------------------------------------------------------------
 // Warp-tile path: launchers
 // ---------------------------------------------------------------------------
-static inline int wtiles(int n) { return (n / WT) * (n / WT); }
 
 template <typename T, int H>
 static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T* rin, T* rout, int cg, int want_rr, const T* p) {
@@ -876,7 +950,9 @@ static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T*
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
     A.cg = cg; A.want_rr = want_rr;
-    k_wpre<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
+    if (cg) k_wpre<T, H, true><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    else k_wpre<T, H, false><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    ++c.pc.launches;
 }
 
 template <typename T, int H>
@@ -886,7 +962,9 @@ static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg;
-    k_wpost<T, H><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
+    if (cg) k_wpost<T, H, true><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    else k_wpost<T, H, false><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    ++c.pc.launches;
 }
 
 template <typename T>
@@ -906,16 +984,41 @@ static void launch_coarse(Ctx& c, InnerSolver<T>& s, int nact) {
     ++c.pc.launches;
 }
 
+// Passes of the TMA-staged path (FP32 inner solver only).
+static void staged_pre(Ctx& c, InnerSolver<float>& s, int nact, int cur, int pc, int cg) {
+    TmaMaps& M = *s.maps;
+    float* rout = cg ? s.r[1 - cur] : nullptr;
+    if (level_halo(c, 0) == 2) {
+        if (cg) launch_tpre<2, true>(c, s, 0, nact, M.r0[cur], s.r[cur], rout, 1, pc);
+        else launch_tpre<2, false>(c, s, 0, nact, M.r0[cur], s.r[cur], rout, 1, pc);
+    } else {
+        if (cg) launch_tpre<4, true>(c, s, 0, nact, M.r0[cur], s.r[cur], rout, 1, pc);
+        else launch_tpre<4, false>(c, s, 0, nact, M.r0[cur], s.r[cur], rout, 1, pc);
+    }
+}
+static void staged_lower(Ctx& c, InnerSolver<float>& s, int nact);
+static void staged_post(Ctx& c, InnerSolver<float>& s, int nact, int cur) {
+    TmaMaps& M = *s.maps;
+    if (level_halo(c, 0) == 2) launch_tpost<2, true>(c, s, 0, nact, M.r0[cur], s.r[cur], s.z);
+    else launch_tpost<4, true>(c, s, 0, nact, M.r0[cur], s.r[cur], s.z);
+}
+static void staged_pre(Ctx&, InnerSolver<double>&, int, int, int, int) {}   // the staged path is FP32 only
+static void staged_post(Ctx&, InnerSolver<double>&, int, int) {}
+static void staged_lower(Ctx&, InnerSolver<double>&, int) {}
+
 // Solver kernel family for the tiled levels: 0 = one block per 32 x 32 tile,
-// 1 = persistent TMA-pipelined blocks, 2 = one warp per 16 x 16 tile (default).
-static int tile_path(const Ctx& c) {
+// 1 = persistent warps with TMA-staged 16 x 16 tiles (FP32), 2 = one warp per
+// 16 x 16 tile loading from global memory.
+static int tile_path(const Ctx& c, bool fp32) {
     if (c.cfg.smooth_sweeps == 1) return 0;
     static int path = -1;
     if (path < 0) {
         const char* e = getenv("SMCGM_TILE_PATH");
-        path = e ? atoi(e) : 2;
-        if (path < 0 || path > 2) path = 2;
+        path = e ? atoi(e) : 1;
+        if (path < 0 || path > 2) path = 1;
     }
+    if (path == 1 && !fp32) return 2;
+    if (path == 1 && c.n % WT) return 2;
     return path;
 }
 
@@ -926,20 +1029,19 @@ struct Passes {
     InnerSolver<T>& s;
     int path, n, ntiles;
     Passes(Ctx& cc, InnerSolver<T>& ss) : c(cc), s(ss) {
-        path = tile_path(cc);
+        path = tile_path(cc, sizeof(T) == 4);
         n = ss.lv[0].n;
-        ntiles = path == 2 ? wtiles(n) : (n / TILE) * (n / TILE);
+        ntiles = path == 0 ? (n / TILE) * (n / TILE) : wtiles(n);
     }
     // finest-level pre-smoothing (cg: with the CG update from r[cur] into r[1-cur])
     void pre(int nact, int cur, int pc, int cg) {
-        TmaMaps* M = s.maps;
         LevelArrays<T>& L0 = s.lv[0];
         T* rout = cg ? s.r[1 - cur] : nullptr;
         if (path == 2) {
             if (c.cfg.fine_sweeps == 1) launch_wpre<T, 2>(c, s, 0, nact, s.r[cur], rout, cg, 1, s.p[pc]);
             else launch_wpre<T, 4>(c, s, 0, nact, s.r[cur], rout, cg, 1, s.p[pc]);
         } else if (path == 1) {
-            fine_pre<T>(c, s, nact, M->r0[cur], rout, cg, cg ? &M->p[pc] : nullptr);
+            staged_pre(c, s, nact, cur, pc, cg);
         } else {
             constexpr int NU = 1;
             k_pre<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
@@ -952,19 +1054,18 @@ struct Passes {
             launch_coarse<T>(c, s, nact);
             for (int l = s.ntile_levels - 1; l >= 1; --l) launch_wpost<T, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
         } else if (path == 1) {
-            run_vcycle_lower_tma<T>(c, s, nact);
+            staged_lower(c, s, nact);
         } else {
             run_vcycle_lower<T, 1>(c, s, nact);
         }
     }
     void post(int nact, int cur) {
-        TmaMaps* M = s.maps;
         LevelArrays<T>& L0 = s.lv[0];
         if (path == 2) {
             if (c.cfg.fine_sweeps == 1) launch_wpost<T, 2>(c, s, 0, nact, s.r[cur], s.z, 1);
             else launch_wpost<T, 4>(c, s, 0, nact, s.r[cur], s.z, 1);
         } else if (path == 1) {
-            fine_post<T>(c, s, nact, M->r0[cur], s.z);
+            staged_post(c, s, nact, cur);
         } else {
             constexpr int NU = 1;
             k_post<T, NU><<<dim3(ntiles, nact), Own<TILE + 4 * NU>::THREADS, 0, c.stream>>>(
@@ -973,19 +1074,12 @@ struct Passes {
     }
     void apply(int nact, int pc, int first) {
         LevelArrays<T>& L0 = s.lv[0];
-        if (path == 2) {
+        if (path != 0) {
             WApplyArgs<T> A{};
-            A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list;
+            A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list; A.a.err = c.dev_err;
             A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
             A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;
             k_wapply<T><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
-        } else if (path == 1) {
-            TmaMaps* M = s.maps;
-            ApplyArgs<T> a{};
-            a.pc.n = n; a.pc.ntiles = ntiles; a.pc.total = nact * ntiles; a.pc.list = s.list; a.pc.err = c.dev_err;
-            a.E = L0.E; a.Nn = L0.Nn; a.pout = s.p[1 - pc]; a.q = s.q; a.betac = c.sc.betac; a.part_pq = c.part.pq; a.first = first;
-            k_apply_tma<T, PIPE_STAGES><<<persistent_grid(a.pc.total, apply_blocks<T>(), c.sm_count), 256,
-                                          apply_tma_smem<T, PIPE_STAGES>(), c.stream>>>(a, M->za, M->pa[pc], M->kwa, M->ksa); ++c.pc.launches;
         } else {
             k_apply<T><<<dim3(ntiles, nact), Own<TILE + 2>::THREADS, 0, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.z, s.p[pc],
                                                                                    s.p[1 - pc], s.q, c.sc.betac, c.part.pq, s.list,
@@ -993,6 +1087,21 @@ struct Passes {
         }
     }
 };
+
+static void staged_lower(Ctx& c, InnerSolver<float>& s, int nact) {
+    // The coarser tiled levels keep the warp kernels loading from global memory:
+    // without the CG vectors their registers allow 16 warps per SM, which
+    // measured faster than the staged form there.
+    for (int l = 1; l < s.ntile_levels; ++l) {
+        if (level_halo(c, l) == 4) launch_wpre<float, 4>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+        else launch_wpre<float, 2>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+    }
+    launch_coarse<float>(c, s, nact);
+    for (int l = s.ntile_levels - 1; l >= 1; --l) {
+        if (level_halo(c, l) == 4) launch_wpost<float, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+        else launch_wpost<float, 2>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+    }
+}
 
 // One preconditioned-CG solve A x = r[0] (x = 0 on entry) for the particles whose
 // refinement is still active; every launch covers only the particles still iterating.
@@ -1080,15 +1189,24 @@ template void launch_coarsen_all<double>(Ctx&, InnerSolver<double>&, int);
 void launch_setup_coeffs(Ctx& c, int count) {
     const int n = c.n;
     const size_t total = (size_t)n * n * count;
-    k_exp_neg<<<grid_for(total), 256, 0, c.stream>>>(c.u64, total); ++c.pc.launches;
     const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
+    if (mixed && n % FX == 0 && n % FY == 0) {
+        LevelArrays<float>& f0 = c.s32.lv[0];
+        k_faces_df<<<dim3((n / FX) * (n / FY), count), FX * FY, 0, c.stream>>>(
+            n, c.u64, reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
+            c.dev_err); ++c.pc.launches;
+        launch_coarsen_all<float>(c, c.s32, count);
+        return;
+    }
+    k_exp_neg<<<grid_for(total), 256, 0, c.stream>>>(c.u64, total); ++c.pc.launches;
     if (mixed) {
         LevelArrays<float>& f0 = c.s32.lv[0];
-        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, f0.Kw, f0.Ks, f0.E, f0.Nn); ++c.pc.launches;
+        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, FaceOut{nullptr, f0.Kw, c.Kwlo}, FaceOut{nullptr, f0.Ks, c.Kslo},
+                                                       FaceOut{nullptr, f0.E, c.Elo}, FaceOut{nullptr, f0.Nn, c.Nlo}); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
     } else {
-        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, nullptr, nullptr, nullptr,
-                                                       nullptr); ++c.pc.launches;
+        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, FaceOut{c.Kw64, nullptr, nullptr}, FaceOut{c.Ks64, nullptr, nullptr},
+                                                       FaceOut{c.E64, nullptr, nullptr}, FaceOut{c.N64, nullptr, nullptr}); ++c.pc.launches;
         launch_coarsen_all<double>(c, c.s64, count);
     }
     check(cudaGetLastError(), "setup launch");
@@ -1127,7 +1245,13 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
         k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out); ++c.pc.launches;
-        k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
+        if constexpr (sizeof(T) == 4) {
+            LevelArrays<float>& f0 = s.lv[0];
+            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, c.w64, c.bhi, c.blo,
+                                                       s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
+        } else {
+            k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
+        }
         check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
         k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, c.b2); ++c.pc.launches;
         int h = 0;

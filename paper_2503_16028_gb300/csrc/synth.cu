@@ -123,21 +123,32 @@ void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
 // the walls so the interpolant vanishes there) and the potential
 // Phi = |F(u) - d|^2 / (2 sigma^2) (Sec. 2.1, eq. Phi).  One warp per particle.
 // ------------------------------------------------------------------------
-__device__ inline double wghost(const double* w, int n, int i, int j) {
+// Cell-centred FP64 solution of one particle.
+struct DoubleGrid {
+    const double* w;
+    __device__ double at(size_t i) const { return w[i]; }
+    __device__ DoubleGrid particle(size_t off) const { return DoubleGrid{w + off}; }
+};
+
+// w at cell (i, j), extended past the walls by odd reflection (w = 0 on the wall).
+template <class W>
+__device__ inline double wghost(const W& w, int n, int i, int j) {
     double s = 1.0;
     if (i < 0) { i = 0; s = -s; }
     if (i > n - 1) { i = n - 1; s = -s; }
     if (j < 0) { j = 0; s = -s; }
     if (j > n - 1) { j = n - 1; s = -s; }
-    return s * w[(size_t)j * n + i];
+    return s * w.at((size_t)j * n + i);
 }
 
-__global__ void k_observe2d(int n, int count, int nobs, const double* __restrict__ w, const double* __restrict__ obs,
-                            const double* __restrict__ data, double inv2s2, double* __restrict__ Phi) {
+// One warp per particle: bilinear interpolation at the observation points and Phi.
+template <class W>
+__device__ inline void observe2d_body(int n, int count, int nobs, const W& w, const double* __restrict__ obs,
+                                      const double* __restrict__ data, double inv2s2, double* __restrict__ Phi) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= count) return;
-    const double* wp = w + (size_t)warp * n * n;
+    const W wp = w.particle((size_t)warp * n * n);
     double acc = 0.0;
     for (int m = lane; m < nobs; m += 32) {
         const double s = obs[2 * m] * n - 0.5, t = obs[2 * m + 1] * n - 0.5;
@@ -154,6 +165,10 @@ __global__ void k_observe2d(int n, int count, int nobs, const double* __restrict
     if (lane == 0) Phi[warp] = acc * inv2s2;
 }
 
+__global__ void k_observe2d(int n, int count, int nobs, const double* __restrict__ w, const double* __restrict__ obs,
+                            const double* __restrict__ data, double inv2s2, double* __restrict__ Phi) {
+    observe2d_body(n, count, nobs, DoubleGrid{w}, obs, data, inv2s2, Phi);
+}
 void launch_observe(Ctx& c, const double* w, int count, double* Phi) {
     const double inv2s2 = 1.0 / (2.0 * c.cfg.sigma * c.cfg.sigma);
     const int threads = 256;

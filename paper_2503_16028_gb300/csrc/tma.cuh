@@ -9,6 +9,13 @@ namespace smcgm {
 
 __device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// TMA destinations are kept 128-byte aligned whatever the dynamic shared-memory
+// base (pointer arithmetic on the shared array itself, so that the compiler
+// still knows the result is a shared-memory address).
+__device__ inline unsigned char* align128(unsigned char* p) {
+    return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
 __device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

@@ -30,13 +30,36 @@ struct WGeo {
     static constexpr int QW = RW / 2;                  // quads per region edge
     static constexpr int NQ = QW * QW;
     static constexpr int SLOTS = (NQ + 31) / 32;       // quads per lane
+    static constexpr int IQ = WT / 2;                  // tile quads per edge
+    static constexpr int ISL = IQ * IQ / 32;           // slots that hold tile quads (the rest: halo)
     static constexpr int EW = RW + 2;                  // correction array edge (zero border)
     static constexpr int EN = EW * EW;
+    static_assert(IQ * IQ % 32 == 0, "tile quads fill whole slots");
 };
+
+// Position (qx, qy) in the region of a warp's quad qi: the tile's quads come
+// first (slots 0 .. ISL-1, always inside the grid), then the halo ring as
+// the band of lowest rows, the band of highest rows and the two side bands.  Keeping the tile quads in
+// their own slots lets the per-slot CG update, stores and restriction be
+// decided at compile time and their registers exist only for those slots.
+template <int H>
+__device__ inline void quad_pos(int qi, int& qx, int& qy) {
+    constexpr int QW = (WT + 2 * H) / 2, HB = H / 2, IQ = WT / 2;
+    if (qi < IQ * IQ) { qx = HB + qi % IQ; qy = HB + qi / IQ; return; }
+    int h = qi - IQ * IQ;
+    if (h < HB * QW) { qx = h % QW; qy = h / QW; return; }
+    h -= HB * QW;
+    if (h < HB * QW) { qx = h % QW; qy = QW - HB + h / QW; return; }
+    h -= HB * QW;
+    const int c = h % (2 * HB);
+    qy = HB + h / (2 * HB);
+    qx = c < HB ? c : IQ + c;
+}
 
 struct WArgs {
     int n, ntiles, total;   // total = active particles x tiles
-    const int* list;
+    const int* list;        // active particle indices
+    int* err;               // set to 1 by a staged kernel whose bounded wait timed out
 };
 
 template <typename T> struct Vec2;
@@ -149,63 +172,103 @@ struct WPreArgs {
     int cg, want_rr;
 };
 
-// Pre-smoothing (nu = H/2 sweeps red, black from zero), residual, restriction;
-// with cg (finest level) first r' = r - alpha q, x += alpha p, and |r'|^2.
-template <typename T, int H>
-__global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
+template <typename T>
+struct WPostArgs {
+    WArgs a;
+    const T *Kw, *Ks, *E, *Nn, *r, *e_in, *ec;
+    T cc;
+    T* e_out;
+    double* part_rz;
+    int cg;
+};
+
+// Inputs of one work item read straight from global memory.  (x0, y0) is the
+// tile origin; every quad asked for lies inside the grid.
+template <typename T>
+struct GlobalSrc {
+    static constexpr bool COMBINE_EARLY = false;
+    const T *kw, *ks, *Ep, *Np, *a, *b, *x, *p;   // a: r, b: q (pre) or e_in (post)
+    int n;
+    __device__ void faces(WRaw<T>& R, int gx, int gy) const { load_faces_raw(R, kw, ks, Ep, Np, n, gx, gy); }
+    __device__ void va(T* v, int gx, int gy) const {
+        const int gi = gy * n + gx;
+        ld2(a + gi, v[0], v[1]);
+        ld2(a + gi + n, v[2], v[3]);
+    }
+    __device__ void vb(T* v, int gx, int gy) const {
+        const int gi = gy * n + gx;
+        ld2(b + gi, v[0], v[1]);
+        ld2(b + gi + n, v[2], v[3]);
+    }
+    __device__ void xp(T* v, int gx, int gy) const {
+        const int gi = gy * n + gx;
+        ld2(x + gi, v[0], v[1]);
+        ld2(x + gi + n, v[2], v[3]);
+        ld2(p + gi, v[4], v[5]);
+        ld2(p + gi + n, v[6], v[7]);
+    }
+    __device__ T parent(int m, int gx, int gy) const { return x[(gy >> 1) * m + (gx >> 1)]; }
+};
+
+// Called once every input of a work item has been read from its source.
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
+// Pre-smoothing of one work item (particle p, tile (tx, ty)) by one warp:
+// nu = H/2 sweeps (red, black) from zero, residual, restriction; with CG
+// (finest level, a compile-time switch) first r' = r - alpha q, x += alpha p,
+// and |r'|^2.
+template <typename T, int H, bool CG, class Src, class Hook = NoHook>
+__device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
+                                 Hook loaded = Hook()) {
     using G = WGeo<T, H>;
     constexpr int NU = H / 2;
-    __shared__ T sme[WPB][G::EN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + warp;
-    if (item >= A.a.total) return;
     const int n = A.a.n;
-    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
-    const int p = A.a.list[pi];
-    const int tpr = n / WT;
-    const int tx = tile % tpr, ty = tile / tpr;
     const size_t base = (size_t)p * n * n;
-    const T* kw = A.Kw + base;
-    const T* ks = A.Ks + base;
-    const T* Ep = A.E + (size_t)p * n;
-    const T* Np = A.Nn + (size_t)p * n;
-    T* se = sme[warp];
     zero_border<G::EW>(se, lane);
-    const T al = A.cg ? (T)A.alpha[p] : T(0);
-    const T* rin = A.rin + base;
-    const T* qg = A.q + base;
+    const T al = CG ? (T)A.alpha[p] : T(0);
     T* xg = A.x + base;
-    const T* pg = A.p + base;
     T* routg = A.rout + base;
     WQuad<T> Q[G::SLOTS];
-    int c0[G::SLOTS];
-    bool live[G::SLOTS], inner[G::SLOTS];
+    int c0[G::SLOTS], gq[G::SLOTS];
+    bool live[G::SLOTS];
     T rr = T(0);
-    // phase 1: every global load of every owned quad is issued before any is used
+    // phase 1: every load of every owned quad is issued before any is used
+    // A source in shared memory combines r' = r - alpha q and x + alpha p as it
+    // reads (fewer live registers); a global source keeps the raw loads until
+    // phase 2 so that all of them are in flight together.
+    constexpr bool early = Src::COMBINE_EARLY;
+    constexpr int RQ = early ? 4 : 8, XP = early ? 4 : 8;
     WRaw<T> Rw[G::SLOTS];
-    T rq[G::SLOTS][8];            // r (4) and q (4)
-    T xp[G::SLOTS][8];            // x (4) and p (4) of inner quads (CG update)
+    T rq[G::SLOTS][RQ];           // r (and q, unless combined)
+    T xp[G::ISL][XP];             // x + alpha p, or x and p, on the tile quads (cg)
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
         const int qi = lane + 32 * sl;
-        const int qx = qi % G::QW, qy = qi / G::QW;
+        int qx, qy;
+        quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
-        live[sl] = qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n;
-        inner[sl] = qi < G::NQ && qx >= H / 2 && qx < H / 2 + WT / 2 && qy >= H / 2 && qy < H / 2 + WT / 2;
+        live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
         c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        gq[sl] = gy * n + gx;
         if (live[sl]) {
-            load_faces_raw(Rw[sl], kw, ks, Ep, Np, n, gx, gy);
-            const int gi = gy * n + gx;
-            ld2(rin + gi, rq[sl][0], rq[sl][1]);
-            ld2(rin + gi + n, rq[sl][2], rq[sl][3]);
-            if (A.cg) {
-                ld2(qg + gi, rq[sl][4], rq[sl][5]);
-                ld2(qg + gi + n, rq[sl][6], rq[sl][7]);
-                if (inner[sl]) {
-                    ld2(xg + gi, xp[sl][0], xp[sl][1]);
-                    ld2(xg + gi + n, xp[sl][2], xp[sl][3]);
-                    ld2(pg + gi, xp[sl][4], xp[sl][5]);
-                    ld2(pg + gi + n, xp[sl][6], xp[sl][7]);
+            S.faces(Rw[sl], gx, gy);
+            S.va(rq[sl], gx, gy);
+            if (CG) {
+                if constexpr (early) {
+                    T qv[4], v[8];
+                    S.vb(qv, gx, gy);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rq[sl][k] -= al * qv[k];
+                    if (sl < G::ISL) {
+                        S.xp(v, gx, gy);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xp[sl][k] = v[k] + al * v[4 + k];
+                    }
+                } else {
+                    S.vb(&rq[sl][4], gx, gy);
+                    if (sl < G::ISL) S.xp(xp[sl], gx, gy);
                 }
             }
         } else if (qi < G::NQ) {
@@ -213,24 +276,26 @@ __global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
             se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
         }
     }
+    loaded();
     // phase 2: derived quantities and the CG update
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
         if (!live[sl]) continue;
         faces_from_raw(Q[sl], Rw[sl]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) Q[sl].r[k] = A.cg ? rq[sl][k] - al * rq[sl][4 + k] : rq[sl][k];
-        if (inner[sl]) {
-            if (A.cg) {
-                const int qi = lane + 32 * sl;
-                const int qx = qi % G::QW, qy = qi / G::QW;
-                const int gi = (ty * WT - H + 2 * qy) * n + tx * WT - H + 2 * qx;
-                st2(xg + gi, xp[sl][0] + al * xp[sl][4], xp[sl][1] + al * xp[sl][5]);
-                st2(xg + gi + n, xp[sl][2] + al * xp[sl][6], xp[sl][3] + al * xp[sl][7]);
+        for (int k = 0; k < 4; ++k) Q[sl].r[k] = (early || !CG) ? rq[sl][k] : rq[sl][k] - al * rq[sl][4 + k];
+        if (sl < G::ISL) {
+            if (CG) {
+                const int gi = gq[sl];
+                T xv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xv[k] = early ? xp[sl][k] : xp[sl][k] + al * xp[sl][4 + k];
+                st2(xg + gi, xv[0], xv[1]);
+                st2(xg + gi + n, xv[2], xv[3]);
                 st2(routg + gi, Q[sl].r[0], Q[sl].r[1]);
                 st2(routg + gi + n, Q[sl].r[2], Q[sl].r[3]);
             }
-            if (A.cg || A.want_rr) {
+            if (CG || A.want_rr) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) rr += Q[sl].r[k] * Q[sl].r[k];
             }
@@ -250,11 +315,10 @@ __global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
     }
     const int m = n / 2;
 #pragma unroll
-    for (int sl = 0; sl < G::SLOTS; ++sl) {
-        if (!inner[sl]) continue;   // inner quads are always inside the grid
+    for (int sl = 0; sl < G::ISL; ++sl) {
+        const int gi = gq[sl];
         const int qi = lane + 32 * sl;
-        const int qx = qi % G::QW, qy = qi / G::QW;
-        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+        const int gx = tx * WT + 2 * (qi % G::IQ), gy = ty * WT + 2 * (qi / G::IQ);
         T rsum = T(0), ev[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -264,78 +328,52 @@ __global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
             rsum += q.r[k] - ((q.w[k] + q.e[k] + q.s[k] + q.n[k]) * ev[k] -
                               (q.w[k] * se[c - 1] + q.e[k] * se[c + 1] + q.s[k] * se[c - G::EW] + q.n[k] * se[c + G::EW]));
         }
-        const int gi = gy * n + gx;
         st2(A.e_out + base + gi, ev[0], ev[1]);
         st2(A.e_out + base + gi + n, ev[2], ev[3]);
         A.rc[(size_t)p * m * m + (gy >> 1) * m + (gx >> 1)] = rsum;
     }
-    if (A.cg || A.want_rr) {
+    if (CG || A.want_rr) {
         const double tot = warp_sum<T>((double)rr);
         if (lane == 0) A.part_rr[(size_t)p * A.a.ntiles + tile] = tot;
     }
 }
 
-template <typename T>
-struct WPostArgs {
-    WArgs a;
-    const T *Kw, *Ks, *E, *Nn, *r, *e_in, *ec;
-    T cc;
-    T* e_out;
-    double* part_rz;
-    int cg;
-};
-
-// Prolongation e + cc P ec, nu = H/2 sweeps (black, red), and on the finest level r.z.
-template <typename T, int H>
-__global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
+// Prolongation e + cc P ec, nu = H/2 sweeps (black, red), and with CG (the
+// finest level) r.z, for one work item by one warp.
+template <typename T, int H, bool CG, class Src, class Hook = NoHook>
+__device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
+                                  Hook loaded = Hook()) {
     using G = WGeo<T, H>;
     constexpr int NU = H / 2;
-    __shared__ T sme[WPB][G::EN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + warp;
-    if (item >= A.a.total) return;
     const int n = A.a.n, m = n / 2;
-    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
-    const int p = A.a.list[pi];
-    const int tpr = n / WT;
-    const int tx = tile % tpr, ty = tile / tpr;
     const size_t base = (size_t)p * n * n;
-    const T* kw = A.Kw + base;
-    const T* ks = A.Ks + base;
-    const T* Ep = A.E + (size_t)p * n;
-    const T* Np = A.Nn + (size_t)p * n;
-    const T* ecp = A.ec + (size_t)p * m * m;
-    T* se = sme[warp];
     zero_border<G::EW>(se, lane);
-    const T* rg = A.r + base;
-    const T* eg = A.e_in + base;
     WQuad<T> Q[G::SLOTS];
-    int c0[G::SLOTS];
-    bool live[G::SLOTS], inner[G::SLOTS];
+    int c0[G::SLOTS], gq[G::SLOTS];
+    bool live[G::SLOTS];
     WRaw<T> Rw[G::SLOTS];
     T ev[G::SLOTS][5];            // e_in (4) and the parent correction
-    // phase 1: all global loads first
+    // phase 1: all loads first
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
         const int qi = lane + 32 * sl;
-        const int qx = qi % G::QW, qy = qi / G::QW;
+        int qx, qy;
+        quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
-        live[sl] = qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n;
-        inner[sl] = qi < G::NQ && qx >= H / 2 && qx < H / 2 + WT / 2 && qy >= H / 2 && qy < H / 2 + WT / 2;
+        live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
         c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        gq[sl] = gy * n + gx;
         if (live[sl]) {
-            load_faces_raw(Rw[sl], kw, ks, Ep, Np, n, gx, gy);
-            const int gi = gy * n + gx;
-            ld2(rg + gi, Q[sl].r[0], Q[sl].r[1]);
-            ld2(rg + gi + n, Q[sl].r[2], Q[sl].r[3]);
-            ld2(eg + gi, ev[sl][0], ev[sl][1]);
-            ld2(eg + gi + n, ev[sl][2], ev[sl][3]);
-            ev[sl][4] = ecp[(gy >> 1) * m + (gx >> 1)];
+            S.faces(Rw[sl], gx, gy);
+            S.va(Q[sl].r, gx, gy);
+            S.vb(ev[sl], gx, gy);
+            ev[sl][4] = S.parent(m, gx, gy);
         } else if (qi < G::NQ) {
             const int c = c0[sl];
             se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
         }
     }
+    loaded();
     // phase 2: prolongation into the correction array, faces and 1/D
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
@@ -362,22 +400,53 @@ __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     }
     T rz = T(0);
 #pragma unroll
-    for (int sl = 0; sl < G::SLOTS; ++sl) {
-        if (!inner[sl]) continue;
-        const int qi = lane + 32 * sl;
-        const int qx = qi % G::QW, qy = qi / G::QW;
-        const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+    for (int sl = 0; sl < G::ISL; ++sl) {
         const int c = c0[sl];
         const T e0 = se[c], e1 = se[c + 1], e2 = se[c + G::EW], e3 = se[c + G::EW + 1];
-        const int gi = gy * n + gx;
+        const int gi = gq[sl];
         st2(A.e_out + base + gi, e0, e1);
         st2(A.e_out + base + gi + n, e2, e3);
-        if (A.cg) rz += Q[sl].r[0] * e0 + Q[sl].r[1] * e1 + Q[sl].r[2] * e2 + Q[sl].r[3] * e3;
+        if (CG) rz += Q[sl].r[0] * e0 + Q[sl].r[1] * e1 + Q[sl].r[2] * e2 + Q[sl].r[3] * e3;
     }
-    if (A.cg) {
+    if (CG) {
         const double tot = warp_sum<T>((double)rz);
         if (lane == 0) A.part_rz[(size_t)p * A.a.ntiles + tile] = tot;
     }
+}
+
+// One warp per work item, inputs loaded from global memory.
+template <typename T, int H, bool CG>
+__global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
+    using G = WGeo<T, H>;
+    __shared__ T sme[WPB][G::EN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= A.a.total) return;
+    const int n = A.a.n;
+    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    const int p = A.a.list[pi];
+    const int tpr = n / WT;
+    const size_t base = (size_t)p * n * n;
+    GlobalSrc<T> S{A.Kw + base, A.Ks + base, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.rin + base, A.q + base,
+                   A.x + base, A.p + base, n};
+    wpre_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
+}
+
+template <typename T, int H, bool CG>
+__global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
+    using G = WGeo<T, H>;
+    __shared__ T sme[WPB][G::EN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= A.a.total) return;
+    const int n = A.a.n, m = n / 2;
+    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    const int p = A.a.list[pi];
+    const int tpr = n / WT;
+    const size_t base = (size_t)p * n * n;
+    GlobalSrc<T> S{A.Kw + base, A.Ks + base, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.r + base, A.e_in + base,
+                   A.ec + (size_t)p * m * m, nullptr, n};
+    wpost_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
 }
 
 template <typename T>
