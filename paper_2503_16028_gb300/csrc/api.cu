@@ -136,6 +136,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
             C.w64 = P.take<double>(bn);
             C.bhi = P.take<float>(cells); C.blo = P.take<float>(cells);
             C.exptab = P.take<float>(128);
+            C.fct_tw_df = P.take<float>(2 * (size_t)n);
         } else {
             C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
             C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
@@ -375,12 +376,21 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     check(cudaMemcpyAsync(c.data, c.data_h.data(), c.data_h.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.S, S.data(), S.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     std::vector<double> tw;
+    std::vector<float> twdf;
     if (c.dim == 2) {
         // twiddles of the fast cosine synthesis, block M/2 - 1 .. M - 2 for M = 2, 4, ..., n
         tw.assign(c.n, 0.0);
         for (int M = 2; M <= c.n; M *= 2)
             for (int i = 0; i < M / 2; ++i) tw[M / 2 - 1 + i] = 1.0 / (2.0 * std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * M)));
         check(cudaMemcpyAsync(c.fct_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
+        if (c.fct_tw_df) {
+            twdf.resize(2 * tw.size());
+            for (size_t i = 0; i < tw.size(); ++i) {
+                twdf[2 * i] = (float)tw[i];
+                twdf[2 * i + 1] = (float)(tw[i] - (double)twdf[2 * i]);
+            }
+            check(cudaMemcpyAsync(c.fct_tw_df, twdf.data(), twdf.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+        }
     }
     check(cudaMemcpyAsync(c.slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemsetAsync(c.dev_err, 0, 4 * sizeof(int), c.stream), "memset err");

@@ -94,6 +94,7 @@ struct Ctx;
 // kernels / launchers (defined in the .cu files)
 void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t purpose);
 void launch_synth2d(Ctx& c, const double* X, int count, double* U);
+void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U);
 void launch_setup_coeffs(Ctx& c, int count);
 template <typename T> void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count);
 template <typename T> void build_tma_maps(Ctx& c, InnerSolver<T>& s);
@@ -146,6 +147,7 @@ struct Ctx {
     double* gridtmp = nullptr;
     // fast cosine synthesis: twiddles 1/(2 cos(pi (2i+1) / (2M))) for M = 2, 4, .., n and the stage-1 output
     double *fct_tw = nullptr, *fct_tmp = nullptr;
+    float* fct_tw_df = nullptr;   // the twiddles as df32 pairs (mixed precision)
     double b2 = 0.0;           // |h^2 f|^2 on the grid (the initial FP64 residual of w = 0)
     // host state
     double t = 0.0, beta = 0.2;

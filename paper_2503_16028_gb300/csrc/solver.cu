@@ -83,7 +83,7 @@ __global__ void k_faces(int n, int count, const double* __restrict__ s, FaceOut 
 // to ~1e-14 relative for the FP64-accurate residual.  |u| >= 64 (beyond the
 // FP32 range of e^u) sets err[1] and is reported by the host.
 constexpr int FX = 32, FY = 8;
-__global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const double* __restrict__ u, const float2* __restrict__ exptab,
+__global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __restrict__ u, const float2* __restrict__ exptab,
                                                       ExpConsts ec, float* __restrict__ Kwh, float* __restrict__ Kwl,
                                                       float* __restrict__ Ksh, float* __restrict__ Ksl, float* __restrict__ Eh,
                                                       float* __restrict__ El, float* __restrict__ Nh, float* __restrict__ Nl,
@@ -96,19 +96,18 @@ __global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const double* __res
     if (threadIdx.x < 64) tab[threadIdx.x] = exptab[threadIdx.x];
     __syncthreads();
     const size_t nn = (size_t)n * n, base = (size_t)p * nn;
-    const double* up = u + base;
+    const float2* up = u + base;
     bool bad = false;
     for (int idx = threadIdx.x; idx < (FY + 1) * (FX + 1); idx += blockDim.x) {
         const int ly = idx / (FX + 1), lx = idx % (FX + 1);
         const int gi = tx * FX + lx - 1, gj = ty * FY + ly - 1;
         float2 v = make_float2(1.f, 0.f);
         if (gi >= 0 && gj >= 0) {
-            const double uv = up[(size_t)gj * n + gi];
-            const unsigned ex = ((unsigned)(__double_as_longlong(uv) >> 52)) & 0x7ffu;
-            if (ex >= 1023u + 6u) {
-                bad = true;                               // |u| >= 64
+            const float2 uv = up[(size_t)gj * n + gi];
+            if (!(fabsf(uv.x) < 64.f)) {
+                bad = true;
             } else {
-                const df32 sv = df_exp(df_neg(df_from_double_bits(uv)), tab, ec);
+                const df32 sv = df_exp(df32{-uv.x, -uv.y}, tab, ec);
                 v = make_float2(sv.hi, sv.lo);
             }
         }
@@ -1010,7 +1009,6 @@ static void staged_lower(Ctx&, InnerSolver<double>&, int) {}
 // 1 = persistent warps with TMA-staged 16 x 16 tiles (FP32), 2 = one warp per
 // 16 x 16 tile loading from global memory.
 static int tile_path(const Ctx& c, bool fp32) {
-    if (c.cfg.smooth_sweeps == 1) return 0;
     static int path = -1;
     if (path < 0) {
         const char* e = getenv("SMCGM_TILE_PATH");
@@ -1050,9 +1048,15 @@ struct Passes {
     }
     void lower(int nact) {
         if (path == 2) {
-            for (int l = 1; l < s.ntile_levels; ++l) launch_wpre<T, 4>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+            for (int l = 1; l < s.ntile_levels; ++l) {
+                if (level_halo(c, l) == 4) launch_wpre<T, 4>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+                else launch_wpre<T, 2>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
+            }
             launch_coarse<T>(c, s, nact);
-            for (int l = s.ntile_levels - 1; l >= 1; --l) launch_wpost<T, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+            for (int l = s.ntile_levels - 1; l >= 1; --l) {
+                if (level_halo(c, l) == 4) launch_wpost<T, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+                else launch_wpost<T, 2>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
+            }
         } else if (path == 1) {
             staged_lower(c, s, nact);
         } else {
@@ -1193,7 +1197,7 @@ void launch_setup_coeffs(Ctx& c, int count) {
     if (mixed && n % FX == 0 && n % FY == 0) {
         LevelArrays<float>& f0 = c.s32.lv[0];
         k_faces_df<<<dim3((n / FX) * (n / FY), count), FX * FY, 0, c.stream>>>(
-            n, c.u64, reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
+            n, reinterpret_cast<const float2*>(c.u64), reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
             c.dev_err); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
         return;
@@ -1273,7 +1277,11 @@ int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w
     const size_t nn = (size_t)c.n * c.n;
     for (int off = 0; off < count; off += c.B) {
         const int cnt = std::min(c.B, count - off);
-        launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
+        // the mixed-precision set-up takes the field as df32 pairs (in the FP64 field's storage)
+        if (c.cfg.precision == SMC_P_FP32_REFINE && c.n % FX == 0 && c.n % FY == 0)
+            launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
+        else
+            launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
         launch_setup_coeffs(c, cnt);
         int it = c.cfg.precision == SMC_P_FP32_REFINE ? solve_batch_t<float>(c, c.s32, cnt) : solve_batch_t<double>(c, c.s64, cnt);
         itmax = std::max(itmax, it);

@@ -27,9 +27,40 @@ namespace smcgm {
 constexpr int FCT_T = 32;            // transforms per block
 constexpr int FCT_WARPS = 8;
 
-__device__ inline void fct_warp(double* b0, double* b1, int N, int lgN, const double* __restrict__ tw, int lane) {
-    double* src = b0;
-    double* dst = b1;
+// Arithmetic of the transforms: FP64, or df32 on the FP32 pipes for the
+// mixed-precision forward solve (u to ~1e-13 absolute; the coefficients need
+// FP64 accuracy only to ~1e-13 relative, far below the solver tolerance).
+struct F64Ops {
+    using V = double;
+    using W = double;    // twiddle
+    static __device__ V zero() { return 0.0; }
+    static __device__ V add(V a, V b) { return a + b; }
+    static __device__ V sub(V a, V b) { return a - b; }
+    static __device__ V mul(V a, W t) { return a * t; }
+    static __device__ V from_input(double x) { return x; }
+};
+struct DfOps {
+    using V = df32;
+    using W = float2;
+    static __device__ V zero() { return df32{0.f, 0.f}; }
+    static __device__ V add(V a, V b) { return df_add(a, b); }
+    static __device__ V sub(V a, V b) { return df_add(a, df_neg(b)); }
+    static __device__ V mul(V a, W t) { return df_mul(a, df32{t.x, t.y}); }
+    static __device__ V from_input(double x) { return df_from_double_bits(x); }
+};
+
+template <class O> __device__ inline typename O::W sqrt2_of();
+template <> __device__ inline double sqrt2_of<F64Ops>() { return M_SQRT2; }
+template <> __device__ inline float2 sqrt2_of<DfOps>() {   // df32 split of sqrt(2): hi = round(sqrt 2), lo = round(sqrt 2 - hi)
+    return make_float2(1.41421353816986083984375f, 2.42032343e-8f);
+}
+
+template <class O>
+__device__ inline void fct_warp(typename O::V* b0, typename O::V* b1, int N, int lgN, const typename O::W* __restrict__ tw,
+                                int lane) {
+    using V = typename O::V;
+    V* src = b0;
+    V* dst = b1;
     const int half = N >> 1;
     // top-down splitting: segment size M -> [even | odd sums]
     for (int lm = lgN; lm >= 1; --lm) {
@@ -37,36 +68,41 @@ __device__ inline void fct_warp(double* b0, double* b1, int N, int lgN, const do
         for (int idx = lane; idx < half; idx += 32) {
             const int o = (idx >> lh) << lm, m = idx & (h - 1);
             dst[o + m] = src[o + 2 * m];
-            dst[o + h + m] = m > 0 ? src[o + 2 * m + 1] + src[o + 2 * m - 1] : src[o + 2 * m + 1];
+            dst[o + h + m] = m > 0 ? O::add(src[o + 2 * m + 1], src[o + 2 * m - 1]) : src[o + 2 * m + 1];
         }
         __syncwarp();
-        double* t = src; src = dst; dst = t;
+        V* t = src; src = dst; dst = t;
     }
     // bottom-up butterflies
     for (int lm = 1; lm <= lgN; ++lm) {
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        const double* twm = tw + (h - 1);
+        const typename O::W* twm = tw + (h - 1);
         for (int idx = lane; idx < half; idx += 32) {
             const int o = (idx >> lh) << lm, i = idx & (h - 1);
-            const double g = src[o + i];
-            const double hp = src[o + h + i] * twm[i];
-            dst[o + i] = g + hp;
-            dst[o + M - 1 - i] = g - hp;
+            const V g = src[o + i];
+            const V hp = O::mul(src[o + h + i], twm[i]);
+            dst[o + i] = O::add(g, hp);
+            dst[o + M - 1 - i] = O::sub(g, hp);
         }
         __syncwarp();
-        double* t = src; src = dst; dst = t;
+        V* t = src; src = dst; dst = t;
     }
     // after 2 lgN swaps the result is back in b0
 }
 
-// stage: 0 = along x (input V[k][l], one transform per l, output T^T[i][l]),
+// stage: 0 = along x (input V[k][l], FP64, one transform per l, output T^T[i][l]),
 //        1 = along y (input T^T[i][l], one transform per i, output U[j][i]).
-__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lgn, int Km, const double* __restrict__ in,
-                                                      double* __restrict__ out, const double* __restrict__ tw) {
-    extern __shared__ __align__(16) double fsm[];
+// The FP64 input of stage 0 is scaled by c_k in FP64 and then converted.
+template <class O>
+__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
+                                                      const typename O::V* __restrict__ in, typename O::V* __restrict__ out,
+                                                      const typename O::W* __restrict__ tw) {
+    using V = typename O::V;
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    V* fsm = reinterpret_cast<V*>(fsm_raw);
     const int SP = n + 1;                               // padded staging row
-    double* stg = fsm;                                  // FCT_T x SP
-    double* work = fsm + FCT_T * SP;                    // FCT_WARPS x 2n
+    V* stg = fsm;                                       // FCT_T x SP
+    V* work = fsm + FCT_T * SP;                         // FCT_WARPS x 2n
     const int p = blockIdx.y;
     const int t0 = blockIdx.x * FCT_T;                  // first transform of the block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -76,19 +112,20 @@ __global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lg
     for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
         if (stage == 0) {
             const int k = idx / FCT_T, t = idx % FCT_T;
-            stg[t * SP + k] = t0 + t < Km ? in[inb + (size_t)k * Km + t0 + t] * (k == 0 ? 1.0 : M_SQRT2) : 0.0;
+            stg[t * SP + k] = t0 + t < Km ? O::from_input(in64[inb + (size_t)k * Km + t0 + t] * (k == 0 ? 1.0 : M_SQRT2)) : O::zero();
         } else {
             const int t = idx / Km, l = idx % Km;
-            stg[t * SP + l] = in[inb + (size_t)(t0 + t) * Km + l] * (l == 0 ? 1.0 : M_SQRT2);
+            const V v = in[inb + (size_t)(t0 + t) * Km + l];
+            stg[t * SP + l] = l == 0 ? v : O::mul(v, sqrt2_of<O>());
         }
     }
     __syncthreads();
-    double* b0 = work + warp * 2 * n;
-    double* b1 = b0 + n;
+    V* b0 = work + warp * 2 * n;
+    V* b1 = b0 + n;
     for (int t = warp; t < FCT_T; t += FCT_WARPS) {
-        for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : 0.0;
+        for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : O::zero();
         __syncwarp();
-        fct_warp(b0, b1, n, lgn, tw, lane);
+        fct_warp<O>(b0, b1, n, lgn, tw, lane);
         for (int k = lane; k < n; k += 32) stg[t * SP + k] = b0[k];
         __syncwarp();
     }
@@ -101,21 +138,32 @@ __global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lg
     }
 }
 
-void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
+template <class O>
+static void launch_fct(Ctx& c, const double* X, int count, typename O::V* tmp, typename O::V* U, const typename O::W* tw) {
     const int n = c.n, Km = c.Km;
     int lgn = 0;
     while ((1 << lgn) < n) ++lgn;
-    const size_t smem = sizeof(double) * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
+    const size_t smem = 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
     static size_t attr = 0;
     if (attr < smem) {
-        check(cudaFuncSetAttribute(k_fct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
+        check(cudaFuncSetAttribute(k_fct<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
         attr = smem;
     }
     // stage 1: ceil(Km / 32) blocks per particle (transforms past Km are masked); stage 2: n / 32
     const int b1 = (Km + FCT_T - 1) / FCT_T, b2 = n / FCT_T;
-    k_fct<<<dim3(b1, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, X, c.fct_tmp, c.fct_tw); ++c.pc.launches;
-    k_fct<<<dim3(b2, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, c.fct_tmp, U, c.fct_tw); ++c.pc.launches;
+    k_fct<O><<<dim3(b1, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, X, nullptr, tmp, tw); ++c.pc.launches;
+    k_fct<O><<<dim3(b2, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, nullptr, tmp, U, tw); ++c.pc.launches;
     check(cudaGetLastError(), "synth2d");
+}
+
+void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
+    launch_fct<F64Ops>(c, X, count, c.fct_tmp, U, c.fct_tw);
+}
+
+// The field of the mixed-precision forward solve, as df32 pairs.
+void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U) {
+    launch_fct<DfOps>(c, X, count, reinterpret_cast<df32*>(c.fct_tmp), reinterpret_cast<df32*>(U),
+                      reinterpret_cast<const float2*>(c.fct_tw_df));
 }
 
 // ------------------------------------------------------------------------

@@ -32,8 +32,16 @@ struct WGeo {
     static constexpr int SLOTS = (NQ + 31) / 32;       // quads per lane
     static constexpr int IQ = WT / 2;                  // tile quads per edge
     static constexpr int ISL = IQ * IQ / 32;           // slots that hold tile quads (the rest: halo)
-    static constexpr int EW = RW + 2;                  // correction array edge (zero border)
-    static constexpr int EN = EW * EW;
+    // The correction lives in four planes, one per quad cell k, each a grid of
+    // quads with a zero border: cell k of the quad at (qx, qy) is at
+    // k PL + (qy + 1) QS + qx + 1.  With the quad-row stride QS = 24 (= 24 mod
+    // 32) the 8 x 4 quads of a tile slot fall on 32 distinct banks, so the
+    // same-colour accesses of a half-sweep are conflict-free.
+    static constexpr int QS = 24;
+    static constexpr int QR = QW + 2;
+    static constexpr int PL = QS * QR;
+    static constexpr int EN = 4 * PL;
+    static_assert(QW + 2 <= QS, "quad row fits the plane stride");
     static_assert(IQ * IQ % 32 == 0, "tile quads fill whole slots");
 };
 
@@ -134,32 +142,42 @@ __device__ inline void faces_from_raw(WQuad<T>& Q, const WRaw<T>& R) {
     for (int k = 0; k < 4; ++k) Q.inv[k] = smoother_rcp(Q.w[k] + Q.e[k] + Q.s[k] + Q.n[k]);
 }
 
-// Zeroes the border ring of a warp's correction array (interior cells are
-// always written before they are read, or belong to quads outside the grid,
-// which their owners zero).
-template <int EW>
-__device__ inline void zero_border(float* se, int lane) {
-    for (int i = lane; i < 4 * (EW - 1); i += 32) {
-        const int side = i / (EW - 1), j = i % (EW - 1);
-        const int c = side == 0 ? j : side == 1 ? (EW - 1) * EW + j + 1 : side == 2 ? (j + 1) * EW : j * EW + EW - 1;
-        se[c] = 0.f;
-    }
+// Offset, from the quad base b = (qy + 1) QS + qx + 1, of cell k of the quad
+// (dir = 4) or of its west, east, south, north neighbour (dir = 0..3).
+template <int QS, int PL>
+__device__ __forceinline__ constexpr int qoff(int k, int dir) {
+    // cells: 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1)
+    return dir == 4 ? k * PL
+         : k == 0 ? (dir == 0 ? PL - 1 : dir == 1 ? PL : dir == 2 ? 2 * PL - QS : 2 * PL)
+         : k == 1 ? (dir == 0 ? 0 : dir == 1 ? 1 : dir == 2 ? 3 * PL - QS : 3 * PL)
+         : k == 2 ? (dir == 0 ? 3 * PL - 1 : dir == 1 ? 3 * PL : dir == 2 ? 0 : QS)
+                  : (dir == 0 ? 2 * PL : dir == 1 ? 2 * PL + 1 : dir == 2 ? PL : PL + QS);
 }
-template <int EW>
-__device__ inline void zero_border(double* se, int lane) {
-    for (int i = lane; i < 4 * (EW - 1); i += 32) {
-        const int side = i / (EW - 1), j = i % (EW - 1);
-        const int c = side == 0 ? j : side == 1 ? (EW - 1) * EW + j + 1 : side == 2 ? (j + 1) * EW : j * EW + EW - 1;
-        se[c] = 0.0;
+
+// Zeroes the border quads of the correction planes that the region's edge
+// cells read (west border: planes 1, 3; east: 0, 2; south: 2, 3; north: 0, 1).
+// Interior quads are always written before they are read, or belong to quads
+// outside the grid, which their owners zero.
+template <typename T, int QW, int QS, int PL>
+__device__ inline void zero_border(T* se, int lane) {
+    for (int i = lane; i < 8 * QW; i += 32) {
+        const int side = i / (2 * QW), rem = i % (2 * QW), which = rem / QW, j = rem % QW;
+        int plane, pos;
+        if (side == 0) { plane = which ? 3 : 1; pos = (j + 1) * QS; }
+        else if (side == 1) { plane = which ? 2 : 0; pos = (j + 1) * QS + QW + 1; }
+        else if (side == 2) { plane = which ? 3 : 2; pos = j + 1; }
+        else { plane = which ? 1 : 0; pos = (QW + 1) * QS + j + 1; }
+        se[plane * PL + pos] = T(0);
     }
 }
 
-template <typename T, int EW>
-__device__ inline void wgs(T* se, int c0, const WQuad<T>& Q, int k, bool pointwise) {
-    const int c = c0 + (k >> 1) * EW + (k & 1);
+template <typename T, int QS, int PL>
+__device__ __forceinline__ void wgs(T* se, int b, const WQuad<T>& Q, int k, bool pointwise) {
     T num = Q.r[k];
-    if (!pointwise) num += Q.w[k] * se[c - 1] + Q.e[k] * se[c + 1] + Q.s[k] * se[c - EW] + Q.n[k] * se[c + EW];
-    se[c] = num * Q.inv[k];
+    if (!pointwise)
+        num += Q.w[k] * se[b + qoff<QS, PL>(k, 0)] + Q.e[k] * se[b + qoff<QS, PL>(k, 1)] + Q.s[k] * se[b + qoff<QS, PL>(k, 2)] +
+               Q.n[k] * se[b + qoff<QS, PL>(k, 3)];
+    se[b + qoff<QS, PL>(k, 4)] = num * Q.inv[k];
 }
 
 template <typename T>
@@ -226,7 +244,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     constexpr int NU = H / 2;
     const int n = A.a.n;
     const size_t base = (size_t)p * n * n;
-    zero_border<G::EW>(se, lane);
+    zero_border<T, G::QW, G::QS, G::PL>(se, lane);
     const T al = CG ? (T)A.alpha[p] : T(0);
     T* xg = A.x + base;
     T* routg = A.rout + base;
@@ -250,7 +268,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
         live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
-        c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        c0[sl] = (qy + 1) * G::QS + qx + 1;
         gq[sl] = gy * n + gx;
         if (live[sl]) {
             S.faces(Rw[sl], gx, gy);
@@ -273,7 +291,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
             }
         } else if (qi < G::NQ) {
             const int c = c0[sl];
-            se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
+            se[c] = T(0); se[c + G::PL] = T(0); se[c + 2 * G::PL] = T(0); se[c + 3 * G::PL] = T(0);
         }
     }
     loaded();
@@ -306,11 +324,11 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G::EW>(se, c0[sl], Q[sl], 3, sw == 0); }
+            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, sw == 0); }
         __syncwarp();
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 1, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 2, false); }
+            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 1, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 2, false); }
         __syncwarp();
     }
     const int m = n / 2;
@@ -322,11 +340,12 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         T rsum = T(0), ev[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int c = c0[sl] + (k >> 1) * G::EW + (k & 1);
+            const int b = c0[sl];
             const WQuad<T>& q = Q[sl];
-            ev[k] = se[c];
+            ev[k] = se[b + qoff<G::QS, G::PL>(k, 4)];
             rsum += q.r[k] - ((q.w[k] + q.e[k] + q.s[k] + q.n[k]) * ev[k] -
-                              (q.w[k] * se[c - 1] + q.e[k] * se[c + 1] + q.s[k] * se[c - G::EW] + q.n[k] * se[c + G::EW]));
+                              (q.w[k] * se[b + qoff<G::QS, G::PL>(k, 0)] + q.e[k] * se[b + qoff<G::QS, G::PL>(k, 1)] +
+                               q.s[k] * se[b + qoff<G::QS, G::PL>(k, 2)] + q.n[k] * se[b + qoff<G::QS, G::PL>(k, 3)]));
         }
         st2(A.e_out + base + gi, ev[0], ev[1]);
         st2(A.e_out + base + gi + n, ev[2], ev[3]);
@@ -347,7 +366,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
     constexpr int NU = H / 2;
     const int n = A.a.n, m = n / 2;
     const size_t base = (size_t)p * n * n;
-    zero_border<G::EW>(se, lane);
+    zero_border<T, G::QW, G::QS, G::PL>(se, lane);
     WQuad<T> Q[G::SLOTS];
     int c0[G::SLOTS], gq[G::SLOTS];
     bool live[G::SLOTS];
@@ -361,7 +380,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
         live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
-        c0[sl] = (2 * qy + 1) * G::EW + 2 * qx + 1;
+        c0[sl] = (qy + 1) * G::QS + qx + 1;
         gq[sl] = gy * n + gx;
         if (live[sl]) {
             S.faces(Rw[sl], gx, gy);
@@ -370,7 +389,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
             ev[sl][4] = S.parent(m, gx, gy);
         } else if (qi < G::NQ) {
             const int c = c0[sl];
-            se[c] = T(0); se[c + 1] = T(0); se[c + G::EW] = T(0); se[c + G::EW + 1] = T(0);
+            se[c] = T(0); se[c + G::PL] = T(0); se[c + 2 * G::PL] = T(0); se[c + 3 * G::PL] = T(0);
         }
     }
     loaded();
@@ -382,27 +401,27 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         const T up = A.cc * ev[sl][4];
         const int c = c0[sl];
         se[c] = ev[sl][0] + up;
-        se[c + 1] = ev[sl][1] + up;
-        se[c + G::EW] = ev[sl][2] + up;
-        se[c + G::EW + 1] = ev[sl][3] + up;
+        se[c + G::PL] = ev[sl][1] + up;
+        se[c + 2 * G::PL] = ev[sl][2] + up;
+        se[c + 3 * G::PL] = ev[sl][3] + up;
     }
     __syncwarp();
 #pragma unroll
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 1, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 2, false); }
+            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 1, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 2, false); }
         __syncwarp();
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::EW>(se, c0[sl], Q[sl], 0, false); wgs<T, G::EW>(se, c0[sl], Q[sl], 3, false); }
+            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, false); }
         __syncwarp();
     }
     T rz = T(0);
 #pragma unroll
     for (int sl = 0; sl < G::ISL; ++sl) {
         const int c = c0[sl];
-        const T e0 = se[c], e1 = se[c + 1], e2 = se[c + G::EW], e3 = se[c + G::EW + 1];
+        const T e0 = se[c], e1 = se[c + G::PL], e2 = se[c + 2 * G::PL], e3 = se[c + 3 * G::PL];
         const int gi = gq[sl];
         st2(A.e_out + base + gi, e0, e1);
         st2(A.e_out + base + gi + n, e2, e3);
