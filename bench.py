@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "darcy256_precision"
+TRAFFIC_BYTES_PER_CELL = 36.05   # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tpre<2,1,3> per cell
 METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
 UNIT = "solves/s"
 
@@ -203,9 +204,11 @@ def model_bytes_per_solve(prof, n, d):
     # per CG iteration (per cell): apply 6 words, fine pre 9.25, fine post 5.25, level-1 pre+post 2.3, coarse 0.35
     cg = (6 + 9.25 + 5.25 + 2.3 + 0.35) * w
     start = (4.25 + 5.25 + 2.3 + 0.35) * w                     # z0 = M r0 per inner solve
-    fp64 = 28.0 + 24.0                                        # residual (w, 2 faces in; r out) + w += x
-    setup = 8 + 16 + 16 + 2 * w + 0.7 * w + 8                 # u out, exp in/out, faces, FP32 copies, coarsening, w memset
-    per_cell = it * cg + inner * start + res * fp64 / 2 + setup
+    refine = 24.0 + 28.0                                      # w += x (w, x in and out); residual (w, faces hi/lo in; r out)
+    # set-up: synthesis passes (T^T out and in, u out: 16 B), faces (u in, faces hi/lo out: 24 B),
+    # coarsening (2.7 words), w and x cleared and r = b (16 B)
+    setup = 16.0 + 24.0 + 2.7 * w + 16.0
+    per_cell = it * cg + inner * start + res * refine + setup
     kl = 4 * d * 8                                            # X read, V write, accept copy (worst case) and the synthesis read
     return per_cell * cells + kl
 
@@ -259,7 +262,11 @@ def run_native(args, rank, world, local):
     value = whole_job_rate(N * args.steps, world, ms_max)
     # roofline of the dominant kernel (finest-level CG update + pre-smoothing + restriction)
     dom_ach = prof["dom_bytes"] / (prof["dom_ms"] / 1000.0) / 1e9 if prof["dom_ms"] > 0 else 0.0
-    roof = dict(bound="hbm", achieved=dom_ach, peak=hbm_peak, unit="GB/s", frac=dom_ach / hbm_peak, traffic=None,
+    # DRAM bytes per cell of the dominant kernel from one ncu capture of the current kernel on
+    # the 512-particle case, scaled to the average particles of a launch here
+    traffic = TRAFFIC_BYTES_PER_CELL * 65536 * prof["dom_particles"] / max(1, prof["dom_launches"])
+    roof = dict(bound="hbm", achieved=dom_ach, peak=hbm_peak, unit="GB/s", frac=dom_ach / hbm_peak, traffic=traffic,
+                algorithmic_bytes_per_launch=prof["dom_bytes"] / max(1, prof["dom_launches"]),
                 kernel="k_tpre<2,CG> (finest level, CG update + pre-smoothing + restriction, TMA-staged)", peak_source=peak_src,
                 launches=prof["dom_launches"], ms_per_launch=prof["dom_ms"] / max(1, prof["dom_launches"]))
     bps = model_bytes_per_solve(prof, 256, d)

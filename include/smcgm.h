@@ -54,8 +54,11 @@ typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2 } smc_kernel;
 
 /* Arithmetic of the forward solve.  SMC_P_FP64: FP64 multigrid-preconditioned
  * CG to tol_outer.  SMC_P_FP32_REFINE: FP32 multigrid-preconditioned CG inner
- * solves to tol_inner, corrected by FP64 iterative refinement (FP64 residual
- * with FP64 coefficients) until the FP64 relative residual is <= tol_outer. */
+ * solves to tol_inner, corrected by iterative refinement on the FP64 solution
+ * with an FP64-accurate residual until its relative residual is <= tol_outer;
+ * the coefficients (e^u and the harmonic faces) and the residual's products
+ * are formed in double-float (pairs of FP32) arithmetic, ~1e-14 relative, and
+ * need |u| < 64 (else the call fails; use SMC_P_FP64). */
 typedef enum { SMC_P_FP64 = 0, SMC_P_FP32_REFINE = 1 } smc_precision;
 
 typedef struct smc_config {
@@ -78,12 +81,12 @@ typedef struct smc_config {
     double ess_frac;    /* ESS target as a fraction of N (App. C) */
     int kernel;         /* smc_kernel */
     int precision;      /* smc_precision */
-    double tol_inner;   /* FP32 inner solve: relative residual reduction */
+    double tol_inner;   /* FP32 inner solve: relative residual reduction (default 2e-4) */
     double tol_outer;   /* final FP64 relative residual |b - A w| / |b| */
     int max_iter;       /* CG iterations per inner solve */
     int max_refine;     /* refinement (outer) iterations */
     int smooth_sweeps;  /* red-black Gauss-Seidel sweeps per pre/post smoothing on coarse levels (1 or 2) */
-    int fine_sweeps;    /* the same on the finest level (1 or 2; used when smooth_sweeps = 2) */
+    int fine_sweeps;    /* the same on the finest level (1 or 2) */
     double coarse_scale;/* multigrid coarse-correction factor */
     int solve_batch;    /* particles per forward-solve batch (0: all N) */
     unsigned long long seed;
