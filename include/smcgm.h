@@ -95,7 +95,8 @@ typedef struct smc_config {
 /* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */
 smc_status smc_config_init(smc_config* cfg);
 
-/* Device bytes smc_init() needs for cfg. */
+/* Device bytes smc_init() needs for cfg; SMC_EINVAL for an invalid cfg, with the
+ * reason in smc_last_error(NULL). */
 smc_status smc_workspace_size(const smc_config* cfg, size_t* bytes);
 
 /* Sets up a context on `stream` (a cudaStream_t, NULL = default stream):

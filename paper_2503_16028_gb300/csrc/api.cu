@@ -238,6 +238,10 @@ using namespace smcgm;
 #define API_BEGIN try {
 #define API_END(ctxp)                                                                           \
     }                                                                                           \
+    catch (const InputError& ie) {                                                              \
+        if (ctxp) (ctxp)->c.err = ie.what;                                                      \
+        return SMC_EINVAL;                                                                      \
+    }                                                                                           \
     catch (const CudaError& ce) {                                                               \
         if (ctxp) (ctxp)->c.err = std::string(ce.what) + ": " + cudaGetErrorString(ce.e);     \
         return SMC_ECUDA;                                                                       \
@@ -306,7 +310,10 @@ smc_status smc_config_init(smc_config* cfg) {
 
 smc_status smc_workspace_size(const smc_config* cfg, size_t* bytes) {
     if (!cfg || !bytes) return SMC_EINVAL;
-    if (validate(*cfg)) return SMC_EINVAL;
+    if (const char* why = validate(*cfg)) {
+        set_global_error(why);
+        return SMC_EINVAL;
+    }
     *bytes = plan(*cfg, nullptr, nullptr);
     return SMC_OK;
 }

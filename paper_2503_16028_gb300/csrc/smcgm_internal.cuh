@@ -168,6 +168,7 @@ struct Ctx {
 
 // status helper
 struct CudaError { cudaError_t e; const char* what; };
+struct InputError { const char* what; };   // input the solver cannot take (reported as SMC_EINVAL)
 void set_global_error(const char* msg);
 std::string& global_error();
 void check(cudaError_t e, const char* what);   // throws CudaError

@@ -932,8 +932,9 @@ static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
     check(cudaStreamSynchronize(c.stream), "sync");
     int err[2] = {0, 0};
     check(cudaMemcpy(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
+    if (err[0] || err[1]) check(cudaMemset(c.dev_err, 0, 2 * sizeof(int)), "err reset");   // the context stays usable
     if (err[0]) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
-    if (err[1]) throw CudaError{cudaErrorInvalidValue, "log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};
+    if (err[1]) throw InputError{"log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};
     return h[0];
 }
 

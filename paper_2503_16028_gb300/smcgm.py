@@ -158,7 +158,7 @@ class Sampler:
 
     def _check(self, st, ctx, allow=()):
         if st != SMC_OK and st not in allow:
-            msg = self.lib.smc_last_error(ctx).decode() if ctx is not None else ""
+            msg = self.lib.smc_last_error(ctx).decode()
             raise SMCError(st, msg)
         return st
 

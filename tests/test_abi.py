@@ -57,6 +57,9 @@ def test_workspace_size_and_validation(lib):
     assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
     bad = smcgm.make_config(wl, n_particles=40000)
     assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    bad = smcgm.make_config(wl, n_particles=1)           # a single particle's weights carry no information
+    assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    assert b"n_particles" in lib.smc_last_error(None)
     obs = np.array([[0.5, 1.5]])
     bad = smcgm.make_config(dict(wl, obs=obs, data=np.zeros(1)))
     assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
