@@ -907,7 +907,7 @@ static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, c
 }
 template <int H, bool CG>
 static void launch_tpost(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
-    launch_tpost_b<H, CG, H == 2 ? 3 : 2>(c, s, level, nact, mr, r, eout);
+    launch_tpost_b<H, CG, H == 2 ? 4 : 2>(c, s, level, nact, mr, r, eout);
 }
 
 template <typename T, int NU>

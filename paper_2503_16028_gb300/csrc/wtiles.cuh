@@ -412,9 +412,13 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         for (int sl = 0; sl < G::SLOTS; ++sl)
             if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 1, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 2, false); }
         __syncwarp();
+        // the last (red) half-sweep matters only on the tile: no later update reads the halo
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, false); }
+            if (live[sl] && (sw < NU - 1 || sl < G::ISL)) {
+                wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, false);
+                wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, false);
+            }
         __syncwarp();
     }
     T rz = T(0);
