@@ -888,9 +888,9 @@ static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, co
 template <int H, bool CG>
 static void launch_tpre(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
                         int want_rr, int pc) {
-    // blocks per SM asked of the register allocator: 3 (<= 168 registers, 12 warps) on a
+    // blocks per SM asked of the register allocator: 4 (<= 128 registers, 16 warps) on a
     // 20 x 20 region, 2 on the 24 x 24 region of two sweeps
-    launch_tpre_b<H, CG, H == 2 ? 3 : 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
+    launch_tpre_b<H, CG, H == 2 ? 4 : 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
 }
 
 template <int H, bool CG, int MINB>

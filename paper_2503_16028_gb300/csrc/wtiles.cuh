@@ -29,7 +29,13 @@ struct WGeo {
     static constexpr int RW = WT + 2 * H;              // region edge
     static constexpr int QW = RW / 2;                  // quads per region edge
     static constexpr int NQ = QW * QW;
-    static constexpr int SLOTS = (NQ + 31) / 32;       // quads per lane
+    // With one sweep (H = 2) the region's four corner quads feed the tile only
+    // through one red cell each (two of them, none for the other two corners),
+    // so they leave the slots and are handled by a short separate step: the
+    // remaining 96 quads fill exactly three slots.
+    static constexpr bool CORNERS = (H == 2);
+    static constexpr int NQM = CORNERS ? NQ - 4 : NQ;  // quads kept in the slots
+    static constexpr int SLOTS = (NQM + 31) / 32;      // quads per lane
     static constexpr int IQ = WT / 2;                  // tile quads per edge
     static constexpr int ISL = IQ * IQ / 32;           // slots that hold tile quads (the rest: halo)
     // The correction lives in four planes, one per quad cell k, each a grid of
@@ -40,21 +46,37 @@ struct WGeo {
     static constexpr int QS = 24;
     static constexpr int QR = QW + 2;
     static constexpr int PL = QS * QR;
-    static constexpr int EN = 4 * PL;
+    // When two planes fit side by side in a quad row (H = 2: 2 x 12 <= 24),
+    // planes 1 and 3 sit 12 words to the right of planes 0 and 2 (a constant
+    // shift keeps the accesses conflict-free) and the array halves.
+    static constexpr bool PACK = 2 * QR <= QS;
+    static constexpr int PO1 = PACK ? QR : PL;            // offset of plane 1 from plane 0
+    static constexpr int PO2 = PACK ? PL : 2 * PL;        // plane 2
+    static constexpr int PO3 = PO2 + PO1;                 // plane 3
+    static constexpr int EN = PACK ? 2 * PL : 4 * PL;
+    static constexpr __host__ __device__ int po(int k) { return k == 0 ? 0 : k == 1 ? PO1 : k == 2 ? PO2 : PO3; }
     static_assert(QW + 2 <= QS, "quad row fits the plane stride");
     static_assert(IQ * IQ % 32 == 0, "tile quads fill whole slots");
 };
 
 // Position (qx, qy) in the region of a warp's quad qi: the tile's quads come
-// first (slots 0 .. ISL-1, always inside the grid), then the halo ring as
-// the band of lowest rows, the band of highest rows and the two side bands.  Keeping the tile quads in
-// their own slots lets the per-slot CG update, stores and restriction be
-// decided at compile time and their registers exist only for those slots.
+// first (slots 0 .. ISL-1, always inside the grid), then the halo ring.  Keeping
+// the tile quads in their own slots lets the per-slot CG update, stores and
+// restriction be decided at compile time and their registers exist only for
+// those slots.  H = 2: the ring without its corners (low band, high band, west
+// side, east side; 8 quads each).  Otherwise the whole ring as the band of
+// lowest rows, the band of highest rows and the two side bands.
 template <int H>
 __device__ inline void quad_pos(int qi, int& qx, int& qy) {
     constexpr int QW = (WT + 2 * H) / 2, HB = H / 2, IQ = WT / 2;
     if (qi < IQ * IQ) { qx = HB + qi % IQ; qy = HB + qi / IQ; return; }
     int h = qi - IQ * IQ;
+    if (H == 2) {
+        const int side = h / IQ, j = 1 + h % IQ;
+        qx = side == 0 || side == 1 ? j : side == 2 ? 0 : QW - 1;
+        qy = side == 2 || side == 3 ? j : side == 0 ? 0 : QW - 1;
+        return;
+    }
     if (h < HB * QW) { qx = h % QW; qy = h / QW; return; }
     h -= HB * QW;
     if (h < HB * QW) { qx = h % QW; qy = QW - HB + h / QW; return; }
@@ -144,22 +166,24 @@ __device__ inline void faces_from_raw(WQuad<T>& Q, const WRaw<T>& R) {
 
 // Offset, from the quad base b = (qy + 1) QS + qx + 1, of cell k of the quad
 // (dir = 4) or of its west, east, south, north neighbour (dir = 0..3).
-template <int QS, int PL>
+template <class G>
 __device__ __forceinline__ constexpr int qoff(int k, int dir) {
     // cells: 0 = (0,0), 1 = (1,0), 2 = (0,1), 3 = (1,1)
-    return dir == 4 ? k * PL
-         : k == 0 ? (dir == 0 ? PL - 1 : dir == 1 ? PL : dir == 2 ? 2 * PL - QS : 2 * PL)
-         : k == 1 ? (dir == 0 ? 0 : dir == 1 ? 1 : dir == 2 ? 3 * PL - QS : 3 * PL)
-         : k == 2 ? (dir == 0 ? 3 * PL - 1 : dir == 1 ? 3 * PL : dir == 2 ? 0 : QS)
-                  : (dir == 0 ? 2 * PL : dir == 1 ? 2 * PL + 1 : dir == 2 ? PL : PL + QS);
+    constexpr int QS = G::QS, P1 = G::PO1, P2 = G::PO2, P3 = G::PO3;
+    return dir == 4 ? G::po(k)
+         : k == 0 ? (dir == 0 ? P1 - 1 : dir == 1 ? P1 : dir == 2 ? P2 - QS : P2)
+         : k == 1 ? (dir == 0 ? 0 : dir == 1 ? 1 : dir == 2 ? P3 - QS : P3)
+         : k == 2 ? (dir == 0 ? P3 - 1 : dir == 1 ? P3 : dir == 2 ? 0 : QS)
+                  : (dir == 0 ? P2 : dir == 1 ? P2 + 1 : dir == 2 ? P1 : P1 + QS);
 }
 
 // Zeroes the border quads of the correction planes that the region's edge
 // cells read (west border: planes 1, 3; east: 0, 2; south: 2, 3; north: 0, 1).
 // Interior quads are always written before they are read, or belong to quads
 // outside the grid, which their owners zero.
-template <typename T, int QW, int QS, int PL>
+template <typename T, class G>
 __device__ inline void zero_border(T* se, int lane) {
+    constexpr int QW = G::QW, QS = G::QS;
     for (int i = lane; i < 8 * QW; i += 32) {
         const int side = i / (2 * QW), rem = i % (2 * QW), which = rem / QW, j = rem % QW;
         int plane, pos;
@@ -167,17 +191,17 @@ __device__ inline void zero_border(T* se, int lane) {
         else if (side == 1) { plane = which ? 2 : 0; pos = (j + 1) * QS + QW + 1; }
         else if (side == 2) { plane = which ? 3 : 2; pos = j + 1; }
         else { plane = which ? 1 : 0; pos = (QW + 1) * QS + j + 1; }
-        se[plane * PL + pos] = T(0);
+        se[G::po(plane) + pos] = T(0);
     }
 }
 
-template <typename T, int QS, int PL>
+template <typename T, class G>
 __device__ __forceinline__ void wgs(T* se, int b, const WQuad<T>& Q, int k, bool pointwise) {
     T num = Q.r[k];
     if (!pointwise)
-        num += Q.w[k] * se[b + qoff<QS, PL>(k, 0)] + Q.e[k] * se[b + qoff<QS, PL>(k, 1)] + Q.s[k] * se[b + qoff<QS, PL>(k, 2)] +
-               Q.n[k] * se[b + qoff<QS, PL>(k, 3)];
-    se[b + qoff<QS, PL>(k, 4)] = num * Q.inv[k];
+        num += Q.w[k] * se[b + qoff<G>(k, 0)] + Q.e[k] * se[b + qoff<G>(k, 1)] + Q.s[k] * se[b + qoff<G>(k, 2)] +
+               Q.n[k] * se[b + qoff<G>(k, 3)];
+    se[b + qoff<G>(k, 4)] = num * Q.inv[k];
 }
 
 template <typename T>
@@ -226,6 +250,16 @@ struct GlobalSrc {
         ld2(p + gi + n, v[6], v[7]);
     }
     __device__ T parent(int m, int gx, int gy) const { return x[(gy >> 1) * m + (gx >> 1)]; }
+    // right-hand side (and q) and the four faces of the single cell (gx, gy)
+    __device__ void cell(int gx, int gy, bool withq, T& rv, T& qv, T& fw, T& fe, T& fs, T& fn) const {
+        const int gi = gy * n + gx;
+        rv = a[gi];
+        qv = withq ? b[gi] : T(0);
+        fw = kw[gi];
+        fe = gx + 1 < n ? kw[gi + 1] : Ep[gy];
+        fs = ks[gi];
+        fn = gy + 1 < n ? ks[gi + n] : Np[gx];
+    }
 };
 
 // Called once every input of a work item has been read from its source.
@@ -244,7 +278,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     constexpr int NU = H / 2;
     const int n = A.a.n;
     const size_t base = (size_t)p * n * n;
-    zero_border<T, G::QW, G::QS, G::PL>(se, lane);
+    zero_border<T, G>(se, lane);
     const T al = CG ? (T)A.alpha[p] : T(0);
     T* xg = A.x + base;
     T* routg = A.rout + base;
@@ -267,7 +301,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         int qx, qy;
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
-        live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
+        live[sl] = sl < G::ISL || (qi < G::NQM && gx >= 0 && gx < n && gy >= 0 && gy < n);
         c0[sl] = (qy + 1) * G::QS + qx + 1;
         gq[sl] = gy * n + gx;
         if (live[sl]) {
@@ -289,9 +323,33 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
                     if (sl < G::ISL) S.xp(xp[sl], gx, gy);
                 }
             }
-        } else if (qi < G::NQ) {
+        } else if (qi < G::NQM) {
             const int c = c0[sl];
-            se[c] = T(0); se[c + G::PL] = T(0); se[c + 2 * G::PL] = T(0); se[c + 3 * G::PL] = T(0);
+            se[c] = T(0); se[c + G::PO1] = T(0); se[c + G::PO2] = T(0); se[c + G::PO3] = T(0);
+        }
+    }
+    if constexpr (G::CORNERS) {
+        // Corner quads (lane 0: west-south, 1: east-south, 2: west-north, 3: east-north).
+        // Only the red cells diagonal to the tile's corners, region (1, 1) and
+        // (RW-2, RW-2), are ever read (by the black half-sweep next to the tile);
+        // they get their pointwise first half-sweep value, the rest zeros.
+        if (lane < 4) {
+            const int qx = (lane & 1) ? G::QW - 1 : 0, qy = (lane & 2) ? G::QW - 1 : 0;
+            T val = T(0);
+            if (lane == 0 || lane == 3) {
+                const int d = lane == 0 ? 1 : 0;          // cell (1,1) of the west-south quad, (0,0) of the east-north one
+                const int gx = tx * WT - H + 2 * qx + d, gy = ty * WT - H + 2 * qy + d;
+                if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                    T rv, qv, fw, fe, fs, fn;
+                    S.cell(gx, gy, CG, rv, qv, fw, fe, fs, fn);
+                    val = (CG ? rv - al * qv : rv) * smoother_rcp(fw + fe + fs + fn);
+                }
+            }
+            const int c = (qy + 1) * G::QS + qx + 1;
+            se[c] = lane == 3 ? val : T(0);
+            se[c + G::PO1] = T(0);
+            se[c + G::PO2] = T(0);
+            se[c + G::PO3] = lane == 0 ? val : T(0);
         }
     }
     loaded();
@@ -324,11 +382,11 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, sw == 0); }
+            if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G>(se, c0[sl], Q[sl], 3, sw == 0); }
         __syncwarp();
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 1, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 2, false); }
+            if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 1, false); wgs<T, G>(se, c0[sl], Q[sl], 2, false); }
         __syncwarp();
     }
     const int m = n / 2;
@@ -342,10 +400,10 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         for (int k = 0; k < 4; ++k) {
             const int b = c0[sl];
             const WQuad<T>& q = Q[sl];
-            ev[k] = se[b + qoff<G::QS, G::PL>(k, 4)];
+            ev[k] = se[b + qoff<G>(k, 4)];
             rsum += q.r[k] - ((q.w[k] + q.e[k] + q.s[k] + q.n[k]) * ev[k] -
-                              (q.w[k] * se[b + qoff<G::QS, G::PL>(k, 0)] + q.e[k] * se[b + qoff<G::QS, G::PL>(k, 1)] +
-                               q.s[k] * se[b + qoff<G::QS, G::PL>(k, 2)] + q.n[k] * se[b + qoff<G::QS, G::PL>(k, 3)]));
+                              (q.w[k] * se[b + qoff<G>(k, 0)] + q.e[k] * se[b + qoff<G>(k, 1)] +
+                               q.s[k] * se[b + qoff<G>(k, 2)] + q.n[k] * se[b + qoff<G>(k, 3)]));
         }
         st2(A.e_out + base + gi, ev[0], ev[1]);
         st2(A.e_out + base + gi + n, ev[2], ev[3]);
@@ -366,7 +424,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
     constexpr int NU = H / 2;
     const int n = A.a.n, m = n / 2;
     const size_t base = (size_t)p * n * n;
-    zero_border<T, G::QW, G::QS, G::PL>(se, lane);
+    zero_border<T, G>(se, lane);
     WQuad<T> Q[G::SLOTS];
     int c0[G::SLOTS], gq[G::SLOTS];
     bool live[G::SLOTS];
@@ -379,7 +437,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         int qx, qy;
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
-        live[sl] = sl < G::ISL || (qi < G::NQ && gx >= 0 && gx < n && gy >= 0 && gy < n);
+        live[sl] = sl < G::ISL || (qi < G::NQM && gx >= 0 && gx < n && gy >= 0 && gy < n);
         c0[sl] = (qy + 1) * G::QS + qx + 1;
         gq[sl] = gy * n + gx;
         if (live[sl]) {
@@ -387,9 +445,26 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
             S.va(Q[sl].r, gx, gy);
             S.vb(ev[sl], gx, gy);
             ev[sl][4] = S.parent(m, gx, gy);
-        } else if (qi < G::NQ) {
+        } else if (qi < G::NQM) {
             const int c = c0[sl];
-            se[c] = T(0); se[c + G::PL] = T(0); se[c + 2 * G::PL] = T(0); se[c + 3 * G::PL] = T(0);
+            se[c] = T(0); se[c + G::PO1] = T(0); se[c + G::PO2] = T(0); se[c + G::PO3] = T(0);
+        }
+    }
+    if constexpr (G::CORNERS) {
+        // Corner quads: only their prolongated values are read (by the black
+        // half-sweep next to the tile); no corner cell is updated.
+        if (lane < 4) {
+            const int qx = (lane & 1) ? G::QW - 1 : 0, qy = (lane & 2) ? G::QW - 1 : 0;
+            const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
+            T v[4] = {T(0), T(0), T(0), T(0)};
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                S.vb(v, gx, gy);
+                const T up = A.cc * S.parent(m, gx, gy);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] += up;
+            }
+            const int c = (qy + 1) * G::QS + qx + 1;
+            se[c] = v[0]; se[c + G::PO1] = v[1]; se[c + G::PO2] = v[2]; se[c + G::PO3] = v[3];
         }
     }
     loaded();
@@ -401,23 +476,23 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         const T up = A.cc * ev[sl][4];
         const int c = c0[sl];
         se[c] = ev[sl][0] + up;
-        se[c + G::PL] = ev[sl][1] + up;
-        se[c + 2 * G::PL] = ev[sl][2] + up;
-        se[c + 3 * G::PL] = ev[sl][3] + up;
+        se[c + G::PO1] = ev[sl][1] + up;
+        se[c + G::PO2] = ev[sl][2] + up;
+        se[c + G::PO3] = ev[sl][3] + up;
     }
     __syncwarp();
 #pragma unroll
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
-            if (live[sl]) { wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 1, false); wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 2, false); }
+            if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 1, false); wgs<T, G>(se, c0[sl], Q[sl], 2, false); }
         __syncwarp();
         // the last (red) half-sweep matters only on the tile: no later update reads the halo
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
             if (live[sl] && (sw < NU - 1 || sl < G::ISL)) {
-                wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 0, false);
-                wgs<T, G::QS, G::PL>(se, c0[sl], Q[sl], 3, false);
+                wgs<T, G>(se, c0[sl], Q[sl], 0, false);
+                wgs<T, G>(se, c0[sl], Q[sl], 3, false);
             }
         __syncwarp();
     }
@@ -425,7 +500,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
 #pragma unroll
     for (int sl = 0; sl < G::ISL; ++sl) {
         const int c = c0[sl];
-        const T e0 = se[c], e1 = se[c + G::PL], e2 = se[c + 2 * G::PL], e3 = se[c + 3 * G::PL];
+        const T e0 = se[c], e1 = se[c + G::PO1], e2 = se[c + G::PO2], e3 = se[c + G::PO3];
         const int gi = gq[sl];
         st2(A.e_out + base + gi, e0, e1);
         st2(A.e_out + base + gi + n, e2, e3);

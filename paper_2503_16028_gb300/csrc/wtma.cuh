@@ -92,6 +92,16 @@ struct StagedSrc {
         ld2(p + c + WT, v[6], v[7]);
     }
     __device__ float parent(int, int gx, int gy) const { return x[((gy >> 1) - cy0) * G::CX + (gx >> 1) - cx0]; }
+    // right-hand side (and q) and the four faces of the single cell (gx, gy)
+    __device__ void cell(int gx, int gy, bool withq, float& rv, float& qv, float& fw, float& fe, float& fs, float& fn) const {
+        const int bx = gx - x0, by = gy - y0;
+        rv = a[by * G::BX + bx];
+        qv = withq ? b[by * G::BX + bx] : 0.f;
+        fw = kw[by * G::KWX + bx];
+        fe = gx + 1 < n ? kw[by * G::KWX + bx + 1] : Ep[gy];
+        fs = ks[by * G::BX + bx];
+        fn = gy + 1 < n ? ks[(by + 1) * G::BX + bx] : Np[gx];
+    }
 };
 
 __device__ inline void item_decode(const WArgs& a, int item, int& p, int& tile, int& tx, int& ty) {
