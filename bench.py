@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "darcy256_precision"
-TRAFFIC_BYTES_PER_CELL = 36.05   # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tpre<2,1,3> per cell
+TRAFFIC_BYTES_PER_CELL = 36.03   # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tpre<2,1,4> per cell
 METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
 UNIT = "solves/s"
 
