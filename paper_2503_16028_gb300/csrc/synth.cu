@@ -38,6 +38,14 @@ struct F64Ops {
     static __device__ V sub(V a, V b) { return a - b; }
     static __device__ V mul(V a, W t) { return a * t; }
     static __device__ V from_input(double x) { return x; }
+    // the pair (v[0], v[1]) of a 16-byte aligned address, in one load
+    static __device__ void load_pair(const V* v, V& a, V& b) {
+        const double2 t = *reinterpret_cast<const double2*>(v);
+        a = t.x;
+        b = t.y;
+    }
+    static __device__ V shfl_up(V v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+    static __device__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 };
 struct DfOps {
     using V = df32;
@@ -47,6 +55,15 @@ struct DfOps {
     static __device__ V sub(V a, V b) { return df_add(a, df_neg(b)); }
     static __device__ V mul(V a, W t) { return df_mul(a, df32{t.x, t.y}); }
     static __device__ V from_input(double x) { return df_from_double_bits(x); }
+    static __device__ void load_pair(const V* v, V& a, V& b) {
+        const float4 t = *reinterpret_cast<const float4*>(v);
+        a = df32{t.x, t.y};
+        b = df32{t.z, t.w};
+    }
+    static __device__ V shfl_up(V v, int d) {
+        return df32{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+    }
+    static __device__ V shfl(V v, int src) { return df32{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)}; }
 };
 
 template <class O> __device__ inline typename O::W sqrt2_of();
@@ -62,13 +79,21 @@ __device__ inline void fct_warp(typename O::V* b0, typename O::V* b1, int N, int
     V* src = b0;
     V* dst = b1;
     const int half = N >> 1;
-    // top-down splitting: segment size M -> [even | odd sums]
+    // top-down splitting: segment size M -> [even | odd sums].  Thread idx reads
+    // its pair (2m, 2m+1) in one 16-byte load and takes element 2m-1 from the
+    // thread before it (a shuffle, or the last lane of the previous round).
     for (int lm = lgN; lm >= 1; --lm) {
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        for (int idx = lane; idx < half; idx += 32) {
+        V carry = O::zero();
+        for (int idx = lane; idx < half; idx += 32) {        // half is a multiple of 32: all lanes take part
             const int o = (idx >> lh) << lm, m = idx & (h - 1);
-            dst[o + m] = src[o + 2 * m];
-            dst[o + h + m] = m > 0 ? O::add(src[o + 2 * m + 1], src[o + 2 * m - 1]) : src[o + 2 * m + 1];
+            V a0, a1;
+            O::load_pair(src + o + 2 * m, a0, a1);
+            V prev = O::shfl_up(a1, 1);
+            if (lane == 0) prev = carry;
+            carry = O::shfl(a1, 31);
+            dst[o + m] = a0;
+            dst[o + h + m] = m > 0 ? O::add(a1, prev) : a1;
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;

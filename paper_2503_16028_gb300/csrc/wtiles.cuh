@@ -110,11 +110,14 @@ __device__ inline void st2(T* p, T a, T b) {
     *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
 }
 
+// Sum over the warp in the solver's own precision (a tile's partial of a CG
+// dot product: FP32 for the FP32 solver, keeping the FP64 pipe free), widened
+// to double for the per-particle sums over tiles.
 template <typename T>
-__device__ inline double warp_sum(double v) {
+__device__ inline double warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    return (double)v;
 }
 
 // Quad data: cells k = 0..3 are (0,0), (1,0), (0,1), (1,1).
@@ -410,7 +413,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         A.rc[(size_t)p * m * m + (gy >> 1) * m + (gx >> 1)] = rsum;
     }
     if (CG || A.want_rr) {
-        const double tot = warp_sum<T>((double)rr);
+        const double tot = warp_sum<T>(rr);
         if (lane == 0) A.part_rr[(size_t)p * A.a.ntiles + tile] = tot;
     }
 }
@@ -507,7 +510,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         if (CG) rz += Q[sl].r[0] * e0 + Q[sl].r[1] * e1 + Q[sl].r[2] * e2 + Q[sl].r[3] * e3;
     }
     if (CG) {
-        const double tot = warp_sum<T>((double)rz);
+        const double tot = warp_sum<T>(rz);
         if (lane == 0) A.part_rz[(size_t)p * A.a.ntiles + tile] = tot;
     }
 }
@@ -558,12 +561,15 @@ struct WApplyArgs {
 };
 
 // p <- z + beta p on the tile plus a one-cell ring, then q = A p and p.q on the tile.
-// Lane l covers columns 2 (l % 8), +1 of rows l / 8 + 4 k; all global loads
-// (z, p, ring, faces) are issued before any is used.
+// Lane l covers column l % 16 of rows l / 16 + 2 k (k < 8), so one warp access
+// touches 16 consecutive words of two rows: in global memory two 64-byte row
+// segments, in the staged p (row stride 48 = 16 mod 32) 32 distinct banks.
+// All global loads (z, p, ring, faces) are issued before any is used.
 template <typename T>
 __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
-    constexpr int PW = WT + 2;                // staged p edge (tile + ring)
-    __shared__ T smp[WPB][PW * PW];
+    constexpr int PW = 48;                    // staged p row stride (tile + ring: 18 columns used)
+    constexpr int PR = WT + 2;                // staged rows
+    __shared__ T smp[WPB][PR * PW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WPB + warp;
     if (item >= A.a.total) return;
@@ -580,24 +586,22 @@ __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     const bool first = A.first != 0;
     const T b = first ? T(0) : (T)A.betac[p];
     T* sp = smp[warp];
-    const int cx = 2 * (lane & 7), ry = lane >> 3;
+    const int cx = lane & 15, ry = lane >> 4;
     const int gx = tx * WT + cx;
     // phase 1: loads
-    T zv[8], pv0[8], rz[2], rp[2];
-    T w0[4], w1[4], e1[4], s0[4], s1[4], t0[4], t1[4];
+    T pv[8], pold[8], fw[8], fe[8], fs[8], fn[8], rz[2], rp[2];
     int rgi[2];
     bool rin[2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int gy = ty * WT + ry + 4 * k;
+    for (int k = 0; k < 8; ++k) {
+        const int gy = ty * WT + ry + 2 * k;
         const int gi = gy * n + gx;
-        ld2(zg + gi, zv[2 * k], zv[2 * k + 1]);
-        if (!first) ld2(pg + gi, pv0[2 * k], pv0[2 * k + 1]);
-        ld2(kw + gi, w0[k], w1[k]);
-        e1[k] = gx + 2 < n ? kw[gi + 2] : A.E[(size_t)p * n + gy];
-        ld2(ks + gi, s0[k], s1[k]);
-        if (gy + 1 < n) ld2(ks + gi + n, t0[k], t1[k]);
-        else { t0[k] = A.Nn[(size_t)p * n + gx]; t1[k] = A.Nn[(size_t)p * n + gx + 1]; }
+        pv[k] = zg[gi];
+        pold[k] = first ? T(0) : pg[gi];
+        fw[k] = kw[gi];
+        fe[k] = gx + 1 < n ? kw[gi + 1] : A.E[(size_t)p * n + gy];
+        fs[k] = ks[gi];
+        fn[k] = gy + 1 < n ? ks[gi + n] : A.Nn[(size_t)p * n + gx];
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -615,38 +619,32 @@ __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     }
     // phase 2: p_new into shared memory
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int yy = ry + 4 * k;
-        if (!first) { zv[2 * k] += b * pv0[2 * k]; zv[2 * k + 1] += b * pv0[2 * k + 1]; }
-        sp[(yy + 1) * PW + cx + 1] = zv[2 * k];
-        sp[(yy + 1) * PW + cx + 2] = zv[2 * k + 1];
+    for (int k = 0; k < 8; ++k) {
+        pv[k] += b * pold[k];
+        sp[(ry + 2 * k + 1) * PW + cx + 1] = pv[k];
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int i = lane + 32 * h;
         const int side = i / WT, j = i % WT;
-        const int lx = side == 0 ? 0 : side == 1 ? PW - 1 : j + 1;
-        const int ly = side == 2 ? 0 : side == 3 ? PW - 1 : j + 1;
+        const int lx = side == 0 ? 0 : side == 1 ? PR - 1 : j + 1;
+        const int ly = side == 2 ? 0 : side == 3 ? PR - 1 : j + 1;
         sp[ly * PW + lx] = rz[h] + b * rp[h];
     }
     __syncwarp();
     T pq = T(0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int yy = ry + 4 * k;
-        const int gy = ty * WT + yy;
+    for (int k = 0; k < 8; ++k) {
+        const int yy = ry + 2 * k;
         const int c = (yy + 1) * PW + cx + 1;
-        const T p0 = zv[2 * k], p1 = zv[2 * k + 1];
-        const T q0 = (w0[k] + w1[k] + s0[k] + t0[k]) * p0 -
-                     (w0[k] * sp[c - 1] + w1[k] * sp[c + 1] + s0[k] * sp[c - PW] + t0[k] * sp[c + PW]);
-        const T q1 = (w1[k] + e1[k] + s1[k] + t1[k]) * p1 -
-                     (w1[k] * sp[c] + e1[k] * sp[c + 2] + s1[k] * sp[c + 1 - PW] + t1[k] * sp[c + 1 + PW]);
-        const size_t gi = base + (size_t)gy * n + gx;
-        st2(A.pout + gi, p0, p1);
-        st2(A.q + gi, q0, q1);
-        pq += p0 * q0 + p1 * q1;
+        const T q = (fw[k] + fe[k] + fs[k] + fn[k]) * pv[k] -
+                    (fw[k] * sp[c - 1] + fe[k] * sp[c + 1] + fs[k] * sp[c - PW] + fn[k] * sp[c + PW]);
+        const size_t gi = base + (size_t)(ty * WT + yy) * n + gx;
+        A.pout[gi] = pv[k];
+        A.q[gi] = q;
+        pq += pv[k] * q;
     }
-    const double tot = warp_sum<T>((double)pq);
+    const double tot = warp_sum<T>(pq);
     if (lane == 0) A.part_pq[(size_t)p * A.a.ntiles + tile] = tot;
 }
 
