@@ -120,6 +120,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     C.lfwd = P.take<double>((size_t)N * K); C.lrev = P.take<double>((size_t)N * K);
     C.acc = P.take<unsigned char>(N); C.idx = P.take<int>(N);
     C.icount = P.take<int>(64); C.dscal = P.take<double>(64); C.dev_err = P.take<int>(4);
+    C.normtab = P.take<float>(2 * NORMAL_TAB);
     C.gw = P.take<double>(K); C.gmu = P.take<double>((size_t)K * r); C.glam = P.take<double>((size_t)K * r);
     C.tab = P.take<double>(4 * (size_t)K * r + r + 2 * K);
     C.xsT = P.take<double>((size_t)r * N); C.resp = P.take<double>((size_t)K * N); C.nj = P.take<double>(K);
@@ -362,6 +363,28 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
         check(cudaMemcpyAsync(c.bhi, bhi.data(), bhi.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
         check(cudaMemcpyAsync(c.blo, blo.data(), blo.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     }
+    // df32 Box-Muller: logarithm table and constants (df32 pairs hi = round(v), lo = round(v - hi))
+    auto split = [](double v) { const float h = (float)v; return float2{h, (float)(v - (double)h)}; };
+    std::vector<float2> ntab(NORMAL_TAB);
+    for (int j = 0; j <= 64; ++j) {
+        const double F = 1.0 + j / 64.0;
+        ntab[j] = split(j < 32 ? std::log(F) : std::log(F / 2.0));
+        ntab[65 + j] = split(1.0 / F);
+    }
+    {
+        const double ln2 = std::log(2.0);
+        int ex = 0;
+        const double f = std::frexp(ln2, &ex);
+        const double a = std::ldexp(std::nearbyint(std::ldexp(f, 16)), ex - 16);   // 16 significant bits
+        c.normc.ln2a = (float)a;
+        c.normc.ln2b = (float)(ln2 - a);
+        c.normc.ln2c = (float)(ln2 - a - (double)c.normc.ln2b);
+        c.normc.pi = split(M_PI);
+        c.normc.s3 = split(1.0 / 6.0); c.normc.s5 = split(1.0 / 120.0); c.normc.s7 = split(1.0 / 5040.0); c.normc.s9 = split(1.0 / 362880.0);
+        c.normc.c2 = split(0.5); c.normc.c4 = split(1.0 / 24.0); c.normc.c6 = split(1.0 / 720.0); c.normc.c8 = split(1.0 / 40320.0);
+        c.normc.third = split(1.0 / 3.0);
+    }
+    check(cudaMemcpyAsync(c.normtab, ntab.data(), ntab.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream), "h2d");
     std::vector<float> etab;
     if (c.exptab) {   // df32 exponential: 2^(j/64) split into pairs, ln2/64 in three parts
         etab.resize(128);

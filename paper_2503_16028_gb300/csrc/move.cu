@@ -12,6 +12,7 @@
 //                                     - LSE_j(log w_j + log r_j(v|u)).
 #include "smcgm_internal.cuh"
 #include "common.cuh"
+#include "dfnormal.cuh"
 
 namespace smcgm {
 
@@ -25,6 +26,23 @@ __device__ inline void normal_pair(uint32_t m, uint32_t c1, uint32_t c2, uint32_
     sincospi(2.0 * u2, &s, &c);
     z0 = R * c;
     z1 = R * s;
+}
+
+// The same pair with the logarithm and sin/cos in df32 (see dfnormal.cuh):
+// agrees with normal_pair to ~1e-14 relative and keeps the proposal kernel off
+// the FP64 pipe.  `tab` is the logarithm table in shared memory.
+__device__ inline void normal_pair_df(uint32_t m, uint32_t c1, uint32_t c2, uint32_t purpose, Key k, const float2* tab,
+                                      const NormalConsts& C, double& z0, double& z1) {
+    U4 w = philox(m, c1, c2, purpose, k.k0, k.k1);
+    const unsigned long long a = ((unsigned long long)(w.x >> 5) << 26) | (unsigned long long)(w.y >> 6);
+    const unsigned long long b = ((unsigned long long)(w.z >> 5) << 26) | (unsigned long long)(w.w >> 6);
+    const df32 lg = df_log_u54(a, tab, C);                      // log U1, U1 = (2a + 1) 2^-54
+    const df32 R = df_sqrt(df32{-2.f * lg.hi, -2.f * lg.lo});
+    df32 sn, cs;
+    df_sincospi_u53(b, C, sn, cs);                              // of pi t, t = 2 U2 = (2b + 1) 2^-53
+    const df32 r0 = df_mul(R, cs), r1 = df_mul(R, sn);
+    z0 = (double)r0.hi + (double)r0.lo;
+    z1 = (double)r1.hi + (double)r1.lo;
 }
 
 __global__ void k_prior_draw(int d, const double* __restrict__ sqrtlam, double* __restrict__ X, uint32_t c2, uint32_t purpose,
@@ -90,8 +108,11 @@ void launch_move_tables(Ctx& c) {
 __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const double* __restrict__ X, double* __restrict__ V,
                                                  const double* __restrict__ sqrtlam, const int* __restrict__ slot,
                                                  const int* __restrict__ S, const double* __restrict__ tab, double beta, double gamma,
-                                                 uint32_t step, Key key, double* __restrict__ lfwd, double* __restrict__ lrev) {
+                                                 uint32_t step, Key key, double* __restrict__ lfwd, double* __restrict__ lrev,
+                                                 const float2* __restrict__ ntab, NormalConsts nc) {
     __shared__ int s_j;
+    __shared__ float2 tab_s[NORMAL_TAB];
+    for (int i = threadIdx.x; i < NORMAL_TAB; i += blockDim.x) tab_s[i] = ntab[i];
     const int p = blockIdx.x;
     const int Kr = K * r;
     const double* cumw = tab + 4 * Kr + r + K;
@@ -111,7 +132,7 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
     const double* sq = tab + 3 * Kr + (size_t)j * r;
     for (int m = threadIdx.x; m < (d + 1) / 2; m += blockDim.x) {
         double z[2];
-        normal_pair((uint32_t)m, (uint32_t)p, step, P_NORMAL, key, z[0], z[1]);
+        normal_pair_df((uint32_t)m, (uint32_t)p, step, P_NORMAL, key, tab_s, nc, z[0], z[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int cidx = 2 * m + h;
@@ -154,7 +175,7 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
 void launch_propose(Ctx& c) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
     k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma, c.step, c.key,
-                                         c.lfwd, c.lrev); ++c.pc.launches;
+                                         c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab), c.normc); ++c.pc.launches;
     check(cudaGetLastError(), "propose");
 }
 

@@ -9,6 +9,7 @@
 
 #include "../../include/smcgm.h"
 #include "df32.cuh"
+#include "dfnormal.cuh"
 
 namespace smcgm {
 
@@ -139,6 +140,8 @@ struct Ctx {
     float *bhi = nullptr, *blo = nullptr;
     float* exptab = nullptr;   // 2^(j/64), j < 64, as df32 pairs (the df32 exponential)
     ExpConsts expc{};
+    float* normtab = nullptr;  // logarithm table of the df32 Box-Muller normals (NORMAL_TAB pairs)
+    NormalConsts normc{};
     InnerSolver<float> s32;
     InnerSolver<double> s64;
     Partials part{};
