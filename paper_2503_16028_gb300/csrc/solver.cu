@@ -622,15 +622,17 @@ __global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Part
     }
 }
 
-// w64 += x, x = 0, for particles still refining.
+// w64 += x, x = 0, for particles still refining.  Grid (nn / 1024, particles):
+// a block covers 1024 cells of one particle and returns at once if that
+// particle has converged, so the late refinement steps cost little.
 template <typename T>
-__global__ void k_update_w(int nn, int count, double* __restrict__ w, T* __restrict__ x, const int* __restrict__ act) {
-    const size_t total = (size_t)nn * count;
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (; t < total; t += stride) {
-        const int p = (int)(t / nn);
-        if (!act[p]) continue;
+__global__ void __launch_bounds__(256) k_update_w(int nn, double* __restrict__ w, T* __restrict__ x, const int* __restrict__ act) {
+    const int p = blockIdx.y;
+    if (!act[p]) return;
+    const size_t base = (size_t)p * nn + (size_t)blockIdx.x * 1024;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t t = base + threadIdx.x + 256 * k;
         w[t] += (double)x[t];
         x[t] = T(0);
     }
@@ -1267,7 +1269,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         int it = inner_solve<T>(c, s, count, tol_in);
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
-        k_update_w<T><<<grid_for(total), 256, 0, c.stream>>>(n * n, count, c.w64, s.x, sc.act_out); ++c.pc.launches;
+        k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, c.w64, s.x, sc.act_out); ++c.pc.launches;
         if constexpr (sizeof(T) == 4) {
             LevelArrays<float>& f0 = s.lv[0];
             k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, c.w64, c.bhi, c.blo,
