@@ -55,7 +55,9 @@ typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2 } smc_kernel;
 /* Arithmetic of the forward solve.  SMC_P_FP64: FP64 multigrid-preconditioned
  * CG to tol_outer.  SMC_P_FP32_REFINE: FP32 multigrid-preconditioned CG inner
  * solves to tol_inner, corrected by iterative refinement on the FP64 solution
- * with an FP64-accurate residual until its relative residual is <= tol_outer;
+ * with an FP64-accurate residual until its relative residual is <= tol_outer
+ * (an inner solve stops once its residual has fallen by tol_inner or below
+ * tol_outer / 2 of the right-hand side, whichever comes first);
  * the coefficients (e^u and the harmonic faces) and the residual's products
  * are formed in double-float (pairs of FP32) arithmetic, ~1e-14 relative, and
  * need |u| < 64 (else the call fails; use SMC_P_FP64). */
@@ -81,7 +83,7 @@ typedef struct smc_config {
     double ess_frac;    /* ESS target as a fraction of N (App. C) */
     int kernel;         /* smc_kernel */
     int precision;      /* smc_precision */
-    double tol_inner;   /* FP32 inner solve: relative residual reduction (default 2e-4) */
+    double tol_inner;   /* FP32 inner solve: relative residual reduction per refinement step (default 5e-4) */
     double tol_outer;   /* final FP64 relative residual |b - A w| / |b| */
     int max_iter;       /* CG iterations per inner solve */
     int max_refine;     /* refinement (outer) iterations */

@@ -304,7 +304,7 @@ smc_status smc_config_init(smc_config* cfg) {
     cfg->sigma = 0.01; cfg->source_kind = 1; cfg->src_amp = 10.0; cfg->src_width = 50.0;
     cfg->n_particles = 1024; cfg->n_components = 4; cfg->gm_rank = 64; cfg->em_iters = 50; cfg->var_floor = 1e-3;
     cfg->beta0 = 0.2; cfg->ess_frac = 0.5; cfg->kernel = SMC_K_PCN_GM; cfg->precision = SMC_P_FP32_REFINE;
-    cfg->tol_inner = 2e-4; cfg->tol_outer = 1e-10; cfg->max_iter = 60; cfg->max_refine = 6;
+    cfg->tol_inner = 5e-4; cfg->tol_outer = 1e-10; cfg->max_iter = 60; cfg->max_refine = 6;
     cfg->smooth_sweeps = 2; cfg->fine_sweeps = 1; cfg->coarse_scale = 2.0; cfg->solve_batch = 0; cfg->seed = 2503016028ull;
     return SMC_OK;
 }

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(Own<TILE + 2>::THREADS) k_apply(
             load_cell_faces(Kw + base, Ks + base, E + (size_t)pb * n, Nn + (size_t)pb * n, n, gx, gy, w, e, s, nn);
             const int c = ly * R + lx;
             const T pv = se[c];
-            const T qv = (w + e + s + nn) * pv - (w * se[c - 1] + e * se[c + 1] + s * se[c - R] + nn * se[c + R]);
+            const T qv = w * (pv - se[c - 1]) + e * (pv - se[c + 1]) + s * (pv - se[c - R]) + nn * (pv - se[c + R]);
             const size_t gi = base + (size_t)gy * n + gx;
             pout[gi] = pv;
             q[gi] = qv;
@@ -578,7 +578,11 @@ enum ScalarMode { SM_START = 0, SM_INIT_RR = 1, SM_RZ_FIRST = 2, SM_RZ = 3, SM_P
 
 // One warp per particle: the tile partial sums are reduced in a fixed order
 // (lane-strided, then a shuffle tree), so results do not depend on scheduling.
-__global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, int maxit) {
+// A CG phase ends when |r|^2 <= max(tol2 |r_start|^2, floor2 |b|^2): the floor
+// keeps the last refinement phase from reducing the residual further than the
+// FP64 tolerance needs.
+__global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, double floor2,
+                         int maxit) {
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= count) return;
@@ -594,7 +598,7 @@ __global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Part
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane != 0) return;
     if (mode == SM_INIT_RR) {
-        sc.rr0[p] = s;
+        sc.rr0[p] = fmax(tol2 * s, floor2 * sc.b2[p]);   // the phase's stopping threshold on |r|^2
         sc.rr[p] = s;
         if (!(s > 0.0)) sc.act_in[p] = 0;
         else atomicAdd(&sc.count[0], 1);
@@ -610,7 +614,7 @@ __global__ void k_scalar(int mode, int count, int ntiles, SolverScalars sc, Part
     } else if (mode == SM_RR) {
         sc.rr[p] = s;
         int it = ++sc.iters[p];
-        if (s <= tol2 * sc.rr0[p]) {
+        if (s <= sc.rr0[p]) {
             sc.act_in[p] = 0;
         } else if (it >= maxit || !(s == s)) {
             sc.act_in[p] = 0;
@@ -1131,7 +1135,7 @@ static void staged_lower(Ctx& c, InnerSolver<float>& s, int nact) {
 // One preconditioned-CG solve A x = r[0] (x = 0 on entry) for the particles whose
 // refinement is still active; every launch covers only the particles still iterating.
 template <typename T>
-static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
+static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol, double floor2) {
     SolverScalars& sc = c.sc;
     Passes<T> P(c, s);
     const int n = P.n, ntiles = P.ntiles;
@@ -1140,23 +1144,23 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
     const int maxit = c.cfg.max_iter;
     int cur = 0, pc = 0;
     int hcount[3] = {0, 0, 0};
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_START, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
     check(cudaMemsetAsync(sc.count, 0, 3 * sizeof(int), c.stream), "memset count");
     int nact = compact_active(c, s, count, hcount);
     if (nact == 0) return 0;
     P.pre(nact, cur, pc, 0);                      // z0 = M r0
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_INIT_RR, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
     nact = compact_active(c, s, count, hcount);
     c.pc.inner_solves += nact;
     if (nact == 0) return 0;
     P.lower(nact);
     P.post(nact, cur);
-    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+    k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
     const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T);   // per cell: r,q,x,p,Kw,Ks in; r,x,e,rc out
     for (int it = 0; it < maxit; ++it) {
         P.apply(nact, pc, it == 0);
         pc ^= 1;
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_PQ, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
         if (c.prof) check(cudaEventRecord(c.ev0, c.stream), "event");
         P.pre(nact, cur, pc, 1);
         if (c.prof) check(cudaEventRecord(c.ev1, c.stream), "event");
@@ -1164,7 +1168,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         c.pc.cg_iterations += nact;
         const int launched = nact;
         check(cudaMemsetAsync(sc.count, 0, sizeof(int), c.stream), "memset count");
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RR, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
         nact = compact_active(c, s, count, hcount);
         if (c.prof) {
             float ms = 0.f;
@@ -1177,7 +1181,7 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol) {
         if (nact == 0) break;
         P.lower(nact);
         P.post(nact, cur);
-        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, maxit); ++c.pc.launches;
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
     }
     check(cudaGetLastError(), "inner solve launch");
     return hcount[2];
@@ -1265,8 +1269,9 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
     int itmax = 0;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
+    const double floor2 = 0.25 * tol_out2;   // no phase need reduce |r| below half the final tolerance
     for (int o = 0; o < max_outer; ++o) {
-        int it = inner_solve<T>(c, s, count, tol_in);
+        int it = inner_solve<T>(c, s, count, tol_in, floor2);
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
         k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, c.w64, s.x, sc.act_out); ++c.pc.launches;

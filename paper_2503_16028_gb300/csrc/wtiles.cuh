@@ -565,6 +565,12 @@ struct WApplyArgs {
 // touches 16 consecutive words of two rows: in global memory two 64-byte row
 // segments, in the staged p (row stride 48 = 16 mod 32) 32 distinct banks.
 // All global loads (z, p, ring, faces) are issued before any is used.
+// q is formed as the sum of the face fluxes k_f (p_c - p_nb), not as
+// diag p_c - sum k_f p_nb: for a smooth p the differences are exact and the
+// rounding error stays at the size of the fluxes, where the diagonal form
+// loses it to cancellation.  CG's recursive residual r - alpha q then tracks
+// the true residual of the FP32 iterate closely, and each refinement phase's
+// reduction holds for the FP64 residual too.
 template <typename T>
 __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     constexpr int PW = 48;                    // staged p row stride (tile + ring: 18 columns used)
@@ -637,8 +643,8 @@ __global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
     for (int k = 0; k < 8; ++k) {
         const int yy = ry + 2 * k;
         const int c = (yy + 1) * PW + cx + 1;
-        const T q = (fw[k] + fe[k] + fs[k] + fn[k]) * pv[k] -
-                    (fw[k] * sp[c - 1] + fe[k] * sp[c + 1] + fs[k] * sp[c - PW] + fn[k] * sp[c + PW]);
+        const T q = fw[k] * (pv[k] - sp[c - 1]) + fe[k] * (pv[k] - sp[c + 1]) + fs[k] * (pv[k] - sp[c - PW]) +
+                    fn[k] * (pv[k] - sp[c + PW]);
         const size_t gi = base + (size_t)(ty * WT + yy) * n + gx;
         A.pout[gi] = pv[k];
         A.q[gi] = q;
