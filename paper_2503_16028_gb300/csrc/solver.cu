@@ -677,16 +677,17 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* __restric
 }
 
 // Mixed precision: the FP64-accurate residual b - A w, with w in FP64 and the
-// faces and b as df32 pairs, evaluated as b - sum over faces of k_f (w_c - w_nb)
-// (w_nb = 0 beyond a wall).  Only the differences w_c - w_nb use the FP64
-// unit (exact for neighbouring values, by Sterbenz's lemma), and each face's
-// difference is formed once: a 32 x 32 tile puts the west and south
-// differences of its cells, plus those of the next column and row, into
-// shared memory as df32 (split by bit manipulation), and every cell takes its
-// east / north difference from its neighbour's west / south one.  Products and
-// sums run in df32 on the FP32 pipes (error ~2^-47 of the face fluxes, whose
-// sum is ~200 |b| at 256^2).  Stored in FP32 with the partial |res|^2 per
-// tile, like the FP64 residual.
+// faces and b as df32 pairs, evaluated as b - sum over faces of the fluxes
+// k_f (w_c - w_nb) (w_nb = 0 beyond a wall).  Only the differences w_c - w_nb
+// use the FP64 unit (exact for neighbouring values, by Sterbenz's lemma), and
+// each face's flux is formed once: a 32 x 32 tile puts the west and south
+// fluxes of its cells, plus those of the next column and row, into shared
+// memory as df32 (the difference split by bit manipulation, the product in
+// df32), and every cell takes its east / north flux from its neighbour's west
+// / south one.  Products and sums run in df32 on the FP32 pipes (error ~2^-47
+// of the face fluxes, whose sum is ~200 |b| at 256^2).  Stored in FP32 with the
+// partial |res|^2 per tile, summed in FP32 (a convergence test needs no more,
+// and the FP64 unit, ~1/64 of the FP32 rate here, is left to the differences).
 __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __restrict__ Kwh, const float* __restrict__ Kwl,
                                                       const float* __restrict__ Ksh, const float* __restrict__ Ksl,
                                                       const float* __restrict__ Eh, const float* __restrict__ El,
@@ -694,9 +695,9 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
                                                       const double* __restrict__ w, const float* __restrict__ bhi,
                                                       const float* __restrict__ blo, float* __restrict__ rout,
                                                       double* __restrict__ part_res, const int* __restrict__ act) {
-    __shared__ double red[32];
-    __shared__ float2 DW[TILE][TILE + 1];   // DW[j][i] = w(i) - w(i-1) (w(-1) = 0 at the west wall); column TILE: the next tile's
-    __shared__ float2 DS[TILE + 1][TILE];   // DS[j][i] = w(j) - w(j-1); row TILE likewise
+    __shared__ float red[8];
+    __shared__ float2 FW[TILE][TILE + 1];   // FW[j][i]: flux of the west face of cell (x0 + i, y0 + j); column TILE: the east edge
+    __shared__ float2 FS[TILE + 1][TILE];   // FS[j][i]: south face; row TILE: the north edge
     const int pb = blockIdx.y;
     if (!act[pb]) return;
     const int tpr = n / TILE;
@@ -704,41 +705,45 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
     const int x0 = tx * TILE, y0 = ty * TILE;
     const size_t nn = (size_t)n * n, base = (size_t)pb * nn;
     const double* wp = w + base;
+    const float *kwh = Kwh + base, *kwl = Kwl + base, *ksh = Ksh + base, *ksl = Ksl + base;
     const int li = threadIdx.x % TILE, lj0 = threadIdx.x / TILE;   // 8 rows of threads
-    auto put = [](float2& dst, double d) {
-        const df32 v = df_from_double_bits(d);
-        dst = make_float2(v.hi, v.lo);
+    auto flux = [](float kh, float kl, double d) {
+        const df32 v = df_mul(df32{kh, kl}, df_from_double_bits(d));
+        return make_float2(v.hi, v.lo);
     };
     for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
         const int i = x0 + li, j = y0 + lj;
         const int c = j * n + i;
         const double wc = wp[c];
-        put(DW[lj][li], i > 0 ? wc - wp[c - 1] : wc);
-        put(DS[lj][li], j > 0 ? wc - wp[c - n] : wc);
-        if (li == TILE - 1) put(DW[lj][TILE], i + 1 < n ? wp[c + 1] - wc : -wc);
-        if (lj == TILE - 1) put(DS[TILE][li], j + 1 < n ? wp[c + n] - wc : -wc);
+        FW[lj][li] = flux(kwh[c], kwl[c], i > 0 ? wc - wp[c - 1] : wc);
+        FS[lj][li] = flux(ksh[c], ksl[c], j > 0 ? wc - wp[c - n] : wc);
+        if (li == TILE - 1)
+            FW[lj][TILE] = i + 1 < n ? flux(kwh[c + 1], kwl[c + 1], wp[c + 1] - wc)
+                                     : flux(Eh[(size_t)pb * n + j], El[(size_t)pb * n + j], -wc);
+        if (lj == TILE - 1)
+            FS[TILE][li] = j + 1 < n ? flux(ksh[c + n], ksl[c + n], wp[c + n] - wc)
+                                     : flux(Nh[(size_t)pb * n + i], Nl[(size_t)pb * n + i], -wc);
     }
     __syncthreads();
-    float acc2 = 0.f;                       // |r|^2 of a thread's 4 cells in FP32 (a convergence test needs no more)
+    float acc2 = 0.f;                       // |r|^2 of a thread's 4 cells
     for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
-        const int i = x0 + li, j = y0 + lj;
-        const int c = j * n + i;
-        const df32 kw{Kwh[base + c], Kwl[base + c]};
-        const df32 ke = i < n - 1 ? df32{Kwh[base + c + 1], Kwl[base + c + 1]} : df32{Eh[(size_t)pb * n + j], El[(size_t)pb * n + j]};
-        const df32 ks{Ksh[base + c], Ksl[base + c]};
-        const df32 kn = j < n - 1 ? df32{Ksh[base + c + n], Ksl[base + c + n]} : df32{Nh[(size_t)pb * n + i], Nl[(size_t)pb * n + i]};
-        const float2 dw = DW[lj][li], de = DW[lj][li + 1], ds = DS[lj][li], dn = DS[lj + 1][li];
-        df32 aw = df_mul(kw, df32{dw.x, dw.y});
-        aw = df_add(aw, df_neg(df_mul(ke, df32{de.x, de.y})));
-        aw = df_add(aw, df_mul(ks, df32{ds.x, ds.y}));
-        aw = df_add(aw, df_neg(df_mul(kn, df32{dn.x, dn.y})));
+        const int c = (y0 + lj) * n + x0 + li;
+        const float2 fw = FW[lj][li], fe = FW[lj][li + 1], fs = FS[lj][li], fn = FS[lj + 1][li];
+        const df32 aw = df_add(df_add(df32{fw.x, fw.y}, df32{-fe.x, -fe.y}), df_add(df32{fs.x, fs.y}, df32{-fn.x, -fn.y}));
         const df32 res = df_sub_acc(df32{bhi[c], blo[c]}, aw);
         const float r = __fadd_rn(res.hi, res.lo);
         rout[base + c] = r;
         acc2 = fmaf(r, r, acc2);
     }
-    double tot = block_sum((double)acc2, red);
-    if (threadIdx.x == 0) part_res[(size_t)pb * gridDim.x + blockIdx.x] = tot;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_down_sync(0xffffffffu, acc2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        part_res[(size_t)pb * gridDim.x + blockIdx.x] = (double)t;
+    }
 }
 
 // r = b for every particle (the residual of w = 0), in the inner precision.

@@ -20,11 +20,12 @@ namespace smcgm {
 // The recursion is unrolled into log2 n top-down splitting levels and log2 n
 // bottom-up butterfly levels, O(n log n) FP64 operations per transform
 // instead of O(n Km).  One warp per transform (warp-synchronous); a block
-// handles 32 transforms so that its input and output rows are contiguous.
+// handles 16 transforms so that its input and output rows are contiguous
+// (128-byte rows), and three blocks fit an SM.
 // Stage 1 (along x, one transform per y-mode l) writes T^T[i][l]; stage 2
 // (along y, one transform per column i) writes U[j][i].
 // ------------------------------------------------------------------------
-constexpr int FCT_T = 32;            // transforms per block
+constexpr int FCT_T = 16;            // transforms per block (16 x 8 bytes: whole 128-byte rows)
 constexpr int FCT_WARPS = 8;
 
 // Arithmetic of the transforms: FP64, or df32 on the FP32 pipes for the
