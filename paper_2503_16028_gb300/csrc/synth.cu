@@ -74,8 +74,8 @@ template <> __device__ inline float2 sqrt2_of<DfOps>() {   // df32 split of sqrt
 }
 
 template <class O>
-__device__ inline void fct_warp(typename O::V* b0, typename O::V* b1, int N, int lgN, const typename O::W* __restrict__ tw,
-                                int lane) {
+__device__ inline typename O::V* fct_warp(typename O::V* b0, typename O::V* b1, int N, int lgN,
+                                          const typename O::W* __restrict__ tw, int lane) {
     using V = typename O::V;
     V* src = b0;
     V* dst = b1;
@@ -99,21 +99,49 @@ __device__ inline void fct_warp(typename O::V* b0, typename O::V* b1, int N, int
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
-    // bottom-up butterflies
-    for (int lm = 1; lm <= lgN; ++lm) {
+    // bottom-up butterflies: level lm maps G = src[o + i], H = src[o + h + i]
+    // (i < h = M/2) to X[o + i] = G + t_i H, X[o + M - 1 - i] = G - t_i H.  Two
+    // levels run per pass: the four values src[o2 + i], src[o2 + h + i],
+    // src[o2 + M + i], src[o2 + M + h + i] of one level give, through it, the
+    // G and H of two outputs pairs (i and M - 1 - i) of the next level, so a
+    // group of four is closed under both and shared memory is read and
+    // written once for the two.
+    int lm = 1;
+    if (lgN & 1) {
+        for (int i0 = lane; i0 < half; i0 += 32) {           // level 1 alone (M = 2, t = tw[0])
+            const V g = src[2 * i0];
+            const V hp = O::mul(src[2 * i0 + 1], tw[0]);
+            dst[2 * i0] = O::add(g, hp);
+            dst[2 * i0 + 1] = O::sub(g, hp);
+        }
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+        lm = 2;
+    }
+    for (; lm < lgN; lm += 2) {
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        const typename O::W* twm = tw + (h - 1);
-        for (int idx = lane; idx < half; idx += 32) {
-            const int o = (idx >> lh) << lm, i = idx & (h - 1);
-            const V g = src[o + i];
-            const V hp = O::mul(src[o + h + i], twm[i]);
-            dst[o + i] = O::add(g, hp);
-            dst[o + M - 1 - i] = O::sub(g, hp);
+        const typename O::W* twa = tw + (h - 1);             // level lm
+        const typename O::W* twb = tw + (M - 1);             // level lm + 1 (half size M)
+        for (int g = lane; g < (N >> 2); g += 32) {
+            const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
+            const typename O::W ta = twa[i];
+            const V a = src[o2 + i];
+            const V bt = O::mul(src[o2 + h + i], ta);
+            const V c = src[o2 + M + i];
+            const V dt = O::mul(src[o2 + M + h + i], ta);
+            const V x0 = O::add(a, bt), x1 = O::sub(a, bt);   // level lm: o2 + i, o2 + M - 1 - i
+            const V y0 = O::add(c, dt), y1 = O::sub(c, dt);   // o2 + M + i, o2 + 2M - 1 - i
+            const V p = O::mul(y0, twb[i]);
+            const V q = O::mul(y1, twb[M - 1 - i]);
+            dst[o2 + i] = O::add(x0, p);
+            dst[o2 + 2 * M - 1 - i] = O::sub(x0, p);
+            dst[o2 + M - 1 - i] = O::add(x1, q);
+            dst[o2 + M + i] = O::sub(x1, q);
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
-    // after 2 lgN swaps the result is back in b0
+    return src;
 }
 
 // stage: 0 = along x (input V[k][l], FP64, one transform per l, output T^T[i][l]),
@@ -151,8 +179,8 @@ __global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lg
     for (int t = warp; t < FCT_T; t += FCT_WARPS) {
         for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : O::zero();
         __syncwarp();
-        fct_warp<O>(b0, b1, n, lgn, tw, lane);
-        for (int k = lane; k < n; k += 32) stg[t * SP + k] = b0[k];
+        const V* res = fct_warp<O>(b0, b1, n, lgn, tw, lane);
+        for (int k = lane; k < n; k += 32) stg[t * SP + k] = res[k];
         __syncwarp();
     }
     __syncthreads();
