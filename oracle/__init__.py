@@ -30,6 +30,9 @@ Modules
            resampling and mutation of Alg. 1 / Alg. 3, posterior moments.
   gm       Gaussian-mixture fit on the leading KL modes (Sec. 2.4, the
            estimation step the paper delegates to its reference Feng2018).
+  adjoint  dPhi/dx by the adjoint of the discrete forward model (the drift of
+           the Langevin equation of App. B; Langevin kernels cited in Sec. 1
+           and Sec. 2.4).
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force or invariants; none is "parity unpinned".
