@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--particles", type=int, default=0, help="override N (default: the workload's 4096)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -194,6 +195,30 @@ def make_sampler(wl, precision, N, smcgm):
     return s
 
 
+def time_gradient(wl, N, smcgm, torch, calls=2):
+    """Phi and dPhi/dx of all N particles (a forward and an adjoint solve each, mixed precision),
+    timed with CUDA events on the library's stream after one untimed call."""
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, gradient=1))
+    X = torch.tensor(s.particles()[0], dtype=torch.float64, device="cuda")
+    Phi = torch.empty(N, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(X)
+    s.smc_gradient(X, Phi, G)
+    s.smc_profile_query(enable=1, reset=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(calls):
+        s.smc_gradient(X, Phi, G)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / calls
+    prof = s.smc_profile_query(reset=True)
+    s.close()
+    return dict(value=N / (ms / 1000.0), unit="gradients/s", ms_per_call=ms, particles=N,
+                solves_per_gradient=prof["solves"] / (N * calls), cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
+
+
 def time_moves(s, steps, warmup, torch, barrier):
     for _ in range(warmup):
         s.smc_move(1, allow_noconv=True)
@@ -326,6 +351,9 @@ def run_native(args, rank, world, local):
                     cg_per_solve=prof64["cg_iterations"] / max(1, prof64["solves"]),
                     dominant_kernel_gbs=prof64["dom_bytes"] / (prof64["dom_ms"] / 1000.0) / 1e9 if prof64["dom_ms"] else None)
         s64.close()
+    grad = None
+    if not args.no_gradient:
+        grad = time_gradient(wl, N, smcgm, torch)
     if rank != 0:
         return
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -339,7 +367,7 @@ def run_native(args, rank, world, local):
                                                       frac=step_hbm / hbm_peak, peak=hbm_peak),
                 iterations=iters, fp64=fp64,
                 speedup_vs_fp64=(value / fp64["value"]) if fp64 else None,
-                e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu)
+                e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu, adjoint_gradient=grad)
     print(json.dumps(line), flush=True)
 
 

@@ -92,6 +92,8 @@ typedef struct smc_config {
     double coarse_scale;/* multigrid coarse-correction factor */
     int solve_batch;    /* particles per forward-solve batch (0: all N) */
     unsigned long long seed;
+    int gradient;       /* 1: also lay out the arrays of smc_gradient (2D only; two more
+                           solution-sized FP64 arrays per batch particle); 0: no gradients */
 } smc_config;
 
 /* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */
@@ -147,6 +149,18 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl,
  * d_Phi (count) and d_w (count x grid, FP64, may be NULL) are device
  * outputs; iters (host, may be NULL) gets the largest CG iteration count. */
 smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_w, int* iters);
+
+/* Potential and its gradient for `count` coefficient vectors on the device
+ * (d_X: count x d, FP64): d_Phi (count) and d_grad (count x d, FP64), device
+ * outputs, get Phi(x) and dPhi/dx.  The gradient is that of the discrete
+ * model by its adjoint: w solves A(u) w = b; lam solves A lam = O^T (O w - d)
+ * / sigma^2 (A is symmetric, so the same multigrid-preconditioned solver and
+ * precision serve both); dPhi/du_c = -sum over the faces f of cell c of
+ * (dK_f/du_c)(lam_c - lam_nb)(w_c - w_nb) with dK_f/du_c = K_f^2 e^{-u_c} / 2
+ * for a harmonic face and K_f for a wall face; dPhi/dx is the transpose of the
+ * synthesis applied to it.  The drift of the Langevin equation of App. B.
+ * Needs cfg.gradient = 1 and dim = 2 (else SMC_ESTATE / SMC_EINVAL). */
+smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_grad);
 
 /* Device views of the particle state (borrowed; valid until the next call). */
 smc_status smc_get_particles(smc_ctx* ctx, const double** d_X, const double** d_Phi);

@@ -61,6 +61,8 @@ static const char* validate(const smc_config& c) {
     if (c.fine_sweeps != 1 && c.fine_sweeps != 2) return "fine_sweeps must be 1 or 2";
     if (!(c.coarse_scale > 0 && c.coarse_scale <= 2.5)) return "coarse_scale must be in (0, 2.5]";
     if (c.solve_batch < 0) return "solve_batch must be >= 0";
+    if (c.gradient != 0 && c.gradient != 1) return "gradient must be 0 or 1";
+    if (c.gradient && c.dim != 2) return "gradients are built for dim = 2 only";
     for (int i = 0; i < c.n_obs * c.dim; ++i)
         if (!(c.obs[i] > 0.0 && c.obs[i] < 1.0)) return "observation points must lie inside the domain";
     return nullptr;
@@ -135,13 +137,18 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
             C.Kwlo = P.take<float>(bn); C.Kslo = P.take<float>(bn);
             C.Elo = P.take<float>((size_t)B * n); C.Nlo = P.take<float>((size_t)B * n);
             C.w64 = P.take<double>(bn);
-            C.bhi = P.take<float>(cells); C.blo = P.take<float>(cells);
+            C.bdf = P.take<float2>(cells);
             C.exptab = P.take<float>(128);
             C.fct_tw_df = P.take<float>(2 * (size_t)n);
         } else {
             C.Kw64 = P.take<double>(bn); C.Ks64 = P.take<double>(bn);
             C.E64 = P.take<double>((size_t)B * n); C.N64 = P.take<double>((size_t)B * n);
             C.w64 = P.take<double>(bn);
+        }
+        if (cfg.gradient) {
+            C.lam64 = P.take<double>(bn);
+            C.rhs = P.take<double>(bn);
+            C.rhs_b2 = P.take<double>(B);
         }
         const int ntiles = (n / 16) * (n / 16);   // the finest tiled level's tiles (16 x 16 warp tiles or fewer)
         C.part.ntiles = ntiles;
@@ -352,16 +359,14 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     check(cudaMemcpyAsync(c.sqrtlam, sq.data(), sq.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.basis, basis.data(), basis.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemcpyAsync(c.b64, b.data(), b.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
-    std::vector<float> bhi, blo;
-    if (c.bhi) {   // df32 split of the right-hand side: hi = round(b), lo = round(b - hi)
-        bhi.resize(b.size());
-        blo.resize(b.size());
+    std::vector<float2> bdf;
+    if (c.bdf) {   // df32 split of the right-hand side: hi = round(b), lo = round(b - hi)
+        bdf.resize(b.size());
         for (size_t i = 0; i < b.size(); ++i) {
-            bhi[i] = (float)b[i];
-            blo[i] = (float)(b[i] - (double)bhi[i]);
+            const float h = (float)b[i];
+            bdf[i] = float2{h, (float)(b[i] - (double)h)};
         }
-        check(cudaMemcpyAsync(c.bhi, bhi.data(), bhi.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
-        check(cudaMemcpyAsync(c.blo, blo.data(), blo.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
+        check(cudaMemcpyAsync(c.bdf, bdf.data(), bdf.size() * 8, cudaMemcpyHostToDevice, c.stream), "h2d");
     }
     // df32 Box-Muller: logarithm table and constants (df32 pairs hi = round(v), lo = round(v - hi))
     auto split = [](double v) { const float h = (float)v; return float2{h, (float)(v - (double)h)}; };
@@ -583,6 +588,20 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl, 
         if (var_grid) check(cudaMemcpyAsync(var_grid, c.gridtmp + cells, cells * 8, cudaMemcpyDeviceToHost, c.stream), "d2h");
     }
     check(cudaStreamSynchronize(c.stream), "sync");
+    return SMC_OK;
+    API_END(ctx)
+}
+
+smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_grad) {
+    if (!ctx || !d_X || !d_Phi || !d_grad || count < 1) return SMC_EINVAL;
+    Ctx& c = ctx->c;
+    if (c.stage < 1) return fail(ctx, SMC_ESTATE, "smc_gradient: context not initialised");
+    if (!c.lam64) return fail(ctx, SMC_ESTATE, "smc_gradient: the context was set up without cfg.gradient = 1");
+    API_BEGIN
+    const long long nc0 = c.nonconv;
+    gradient_batch(c, d_X, count, d_Phi, d_grad);
+    check(cudaStreamSynchronize(c.stream), "sync");
+    if ((c.nonconv - nc0) * 100 > 2LL * count) return fail(ctx, SMC_ENOCONV, "more than 1% of forward or adjoint solves missed the tolerance");
     return SMC_OK;
     API_END(ctx)
 }

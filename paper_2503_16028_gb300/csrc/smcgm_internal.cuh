@@ -96,10 +96,23 @@ struct Ctx;
 void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t purpose);
 void launch_synth2d(Ctx& c, const double* X, int count, double* U);
 void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U);
+void launch_analysis2d(Ctx& c, const double* g, int count, double* G);
 void launch_setup_coeffs(Ctx& c, int count);
 template <typename T> void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count);
 template <typename T> void build_tma_maps(Ctx& c, InnerSolver<T>& s);
 int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w_out);
+// Right-hand side of a batch of solves: one shared by every particle (stride 0)
+// or one per particle (stride n*n); FP64 (b64) and, for the mixed-precision
+// solver, as df32 pairs (bdf); |b|^2 per particle (b2pp) or common (b2const).
+struct Rhs {
+    const double* b64;
+    const float2* bdf;
+    size_t stride;
+    const double* b2pp;
+    double b2const;
+};
+Rhs shared_rhs(const Ctx& c);
+int solve_batch(Ctx& c, int count, const Rhs& R, double* W);   // W: the FP64 solutions (count x n x n)
 void launch_observe(Ctx& c, const double* w, int count, double* Phi);
 void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w_out);
 void launch_move_tables(Ctx& c);
@@ -110,6 +123,7 @@ void launch_resample(Ctx& c);
 double gm_fit_device(Ctx& c);
 void launch_moments(Ctx& c, double* mean, double* var);
 void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
+void gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out);
 
 struct Ctx {
     smc_config cfg;
@@ -137,7 +151,10 @@ struct Ctx {
     // mixed precision: FP64-accurate faces and right-hand side as df32 pairs (the
     // high parts of the faces are the inner solver's FP32 faces); the solution stays FP64
     float *Kwlo = nullptr, *Kslo = nullptr, *Elo = nullptr, *Nlo = nullptr;
-    float *bhi = nullptr, *blo = nullptr;
+    float2* bdf = nullptr;     // the shared right-hand side h^2 f as df32 pairs
+    // gradient (cfg.gradient): the adjoint solution and a per-particle right-hand
+    // side (FP64, or df32 pairs in the same storage), reused for dPhi/du
+    double *lam64 = nullptr, *rhs = nullptr, *rhs_b2 = nullptr;
     float* exptab = nullptr;   // 2^(j/64), j < 64, as df32 pairs (the df32 exponential)
     ExpConsts expc{};
     float* normtab = nullptr;  // logarithm table of the df32 Box-Muller normals (NORMAL_TAB pairs)

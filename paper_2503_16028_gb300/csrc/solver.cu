@@ -646,8 +646,8 @@ __global__ void __launch_bounds__(256) k_update_w(int nn, double* __restrict__ w
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(int n, const double* __restrict__ Kw, const double* __restrict__ Ks,
                                                   const double* __restrict__ E, const double* __restrict__ Nn,
-                                                  const double* __restrict__ w, const double* __restrict__ b, T* __restrict__ rout,
-                                                  double* __restrict__ part_res, const int* __restrict__ act) {
+                                                  const double* __restrict__ w, const double* __restrict__ b, size_t bstride,
+                                                  T* __restrict__ rout, double* __restrict__ part_res, const int* __restrict__ act) {
     __shared__ double red[32];
     const int pb = blockIdx.y;
     if (!act[pb]) return;
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* __restric
         if (i < n - 1) aw -= kE * wp[c + 1];
         if (j > 0) aw -= ks[c] * wp[c - n];
         if (j < n - 1) aw -= kN * wp[c + n];
-        const double res = b[c] - aw;
+        const double res = b[(size_t)pb * bstride + c] - aw;
         rout[base + c] = (T)res;
         acc += res * res;
     }
@@ -692,8 +692,8 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
                                                       const float* __restrict__ Ksh, const float* __restrict__ Ksl,
                                                       const float* __restrict__ Eh, const float* __restrict__ El,
                                                       const float* __restrict__ Nh, const float* __restrict__ Nl,
-                                                      const double* __restrict__ w, const float* __restrict__ bhi,
-                                                      const float* __restrict__ blo, float* __restrict__ rout,
+                                                      const double* __restrict__ w, const float2* __restrict__ bdf,
+                                                      size_t bstride, float* __restrict__ rout,
                                                       double* __restrict__ part_res, const int* __restrict__ act) {
     __shared__ float red[8];
     __shared__ float2 FW[TILE][TILE + 1];   // FW[j][i]: flux of the west face of cell (x0 + i, y0 + j); column TILE: the east edge
@@ -730,7 +730,8 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
         const int c = (y0 + lj) * n + x0 + li;
         const float2 fw = FW[lj][li], fe = FW[lj][li + 1], fs = FS[lj][li], fn = FS[lj + 1][li];
         const df32 aw = df_add(df_add(df32{fw.x, fw.y}, df32{-fe.x, -fe.y}), df_add(df32{fs.x, fs.y}, df32{-fn.x, -fn.y}));
-        const df32 res = df_sub_acc(df32{bhi[c], blo[c]}, aw);
+        const float2 bb = bdf[(size_t)pb * bstride + c];
+        const df32 res = df_sub_acc(df32{bb.x, bb.y}, aw);
         const float r = __fadd_rn(res.hi, res.lo);
         rout[base + c] = r;
         acc2 = fmaf(r, r, acc2);
@@ -746,20 +747,26 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
     }
 }
 
-// r = b for every particle (the residual of w = 0), in the inner precision.
+// r = b for every particle (the residual of w = 0), in the inner precision:
+// from the df32 pairs when given (mixed precision), else from FP64.
 template <typename T>
-__global__ void k_fill_rhs(size_t nn, int count, const double* __restrict__ b, T* __restrict__ r) {
+__global__ void k_fill_rhs(size_t nn, int count, const double* __restrict__ b, const float2* __restrict__ bdf, size_t stride,
+                           T* __restrict__ r) {
     const size_t total = nn * count;
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (; t < total; t += stride) r[t] = (T)b[t % nn];
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (; t < total; t += step) {
+        const size_t p = t / nn, i = p * stride + (t - p * nn);
+        r[t] = bdf ? (T)__fadd_rn(bdf[i].x, bdf[i].y) : (T)b[i];
+    }
 }
 
-__global__ void k_outer(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, double b2const) {
+__global__ void k_outer(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, double b2const,
+                        const double* __restrict__ b2pp) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= count) return;
-    if (mode == 0) {  // initial residual = b, |b|^2 known
-        const double s = b2const;
+    if (mode == 0) {  // initial residual = b, |b|^2 known (per particle, or common)
+        const double s = b2pp ? b2pp[p] : b2const;
         sc.b2[p] = s;
         sc.res2[p] = s;
         sc.act_out[p] = s > 0.0 ? 1 : 0;
@@ -1247,7 +1254,7 @@ void launch_setup_coeffs(Ctx& c, int count) {
 }
 
 template <typename T>
-static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
+static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, double* W) {
     const int n = c.n;
     const int ntiles = (n / TILE) * (n / TILE);
     dim3 tgrid(ntiles, count);
@@ -1256,7 +1263,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
     SolverScalars& sc = c.sc;
     const bool mixed = sizeof(T) == 4;
     const double tol_out2 = c.cfg.tol_outer * c.cfg.tol_outer;
-    check(cudaMemsetAsync(c.w64, 0, total * sizeof(double), c.stream), "memset w");
+    check(cudaMemsetAsync(W, 0, total * sizeof(double), c.stream), "memset w");
     check(cudaMemsetAsync(s.x, 0, total * sizeof(T), c.stream), "memset x");
     // act_out = 1 for the residual of w = 0
     {
@@ -1264,13 +1271,14 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         check(cudaMemcpyAsync(sc.act_out, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, c.stream), "act init");
         check(cudaStreamSynchronize(c.stream), "sync");
     }
-    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, c.b64, s.r[0]); ++c.pc.launches;
+    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, R.b64, mixed ? R.bdf : nullptr, R.stride,
+                                                        s.r[0]); ++c.pc.launches;
     c.pc.solves += count;
     c.pc.cells = n * n;
     c.pc.word_bytes = (int)sizeof(T);
     int outer_active = count;
     const int sgrid = (count + 127) / 128;
-    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, c.b2); ++c.pc.launches;
+    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp); ++c.pc.launches;
     int itmax = 0;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
@@ -1279,16 +1287,17 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         int it = inner_solve<T>(c, s, count, tol_in, floor2);
         itmax = std::max(itmax, it);
         c.pc.residuals += outer_active;
-        k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, c.w64, s.x, sc.act_out); ++c.pc.launches;
+        k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, W, s.x, sc.act_out); ++c.pc.launches;
         if constexpr (sizeof(T) == 4) {
             LevelArrays<float>& f0 = s.lv[0];
-            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, c.w64, c.bhi, c.blo,
+            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
                                                        s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
         } else {
-            k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.b64, s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
+            k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, W, R.b64, R.stride, s.r[0], c.part.res,
+                                                       sc.act_out); ++c.pc.launches;
         }
         check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
-        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, c.b2); ++c.pc.launches;
+        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp); ++c.pc.launches;
         int h = 0;
         check(cudaMemcpyAsync(&h, sc.count + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
         check(cudaStreamSynchronize(c.stream), "sync");
@@ -1297,6 +1306,13 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count) {
         if (o == max_outer - 1) c.nonconv += h;
     }
     return itmax;
+}
+
+Rhs shared_rhs(const Ctx& c) { return Rhs{c.b64, c.bdf, 0, nullptr, c.b2}; }
+
+int solve_batch(Ctx& c, int count, const Rhs& R, double* W) {
+    return c.cfg.precision == SMC_P_FP32_REFINE ? solve_batch_t<float>(c, c.s32, count, R, W)
+                                                 : solve_batch_t<double>(c, c.s64, count, R, W);
 }
 
 int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w_out) {
@@ -1314,7 +1330,7 @@ int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w
         else
             launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
         launch_setup_coeffs(c, cnt);
-        int it = c.cfg.precision == SMC_P_FP32_REFINE ? solve_batch_t<float>(c, c.s32, cnt) : solve_batch_t<double>(c, c.s64, cnt);
+        int it = solve_batch(c, cnt, shared_rhs(c), c.w64);
         itmax = std::max(itmax, it);
         launch_observe(c, c.w64, cnt, Phi_out + off);
         if (w_out) check(cudaMemcpyAsync(w_out + off * nn, c.w64, cnt * nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "w copy");

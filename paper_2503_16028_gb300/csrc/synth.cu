@@ -39,6 +39,7 @@ struct F64Ops {
     static __device__ V sub(V a, V b) { return a - b; }
     static __device__ V mul(V a, W t) { return a * t; }
     static __device__ V from_input(double x) { return x; }
+    static __device__ double to_double(V v) { return v; }
     // the pair (v[0], v[1]) of a 16-byte aligned address, in one load
     static __device__ void load_pair(const V* v, V& a, V& b) {
         const double2 t = *reinterpret_cast<const double2*>(v);
@@ -56,6 +57,7 @@ struct DfOps {
     static __device__ V sub(V a, V b) { return df_add(a, df_neg(b)); }
     static __device__ V mul(V a, W t) { return df_mul(a, df32{t.x, t.y}); }
     static __device__ V from_input(double x) { return df_from_double_bits(x); }
+    static __device__ double to_double(V v) { return (double)v.hi + (double)v.lo; }
     static __device__ void load_pair(const V* v, V& a, V& b) {
         const float4 t = *reinterpret_cast<const float4*>(v);
         a = df32{t.x, t.y};
@@ -218,6 +220,125 @@ void launch_synth2d(Ctx& c, const double* X, int count, double* U) {
 void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U) {
     launch_fct<DfOps>(c, X, count, reinterpret_cast<df32*>(c.fct_tmp), reinterpret_cast<df32*>(U),
                       reinterpret_cast<const float2*>(c.fct_tw_df));
+}
+
+// ------------------------------------------------------------------------
+// Analysis G = S^T g, the transpose of the synthesis (the last step of the
+// potential gradient): G[k][l] = c_k c_l sum_{i,j} g[j][i] cos(k pi x_i)
+// cos(l pi y_j), a DCT-II along each axis keeping the Km lowest outputs.  The
+// network is the transpose of fct_warp's: the butterfly levels first, in
+// reverse order, each mapping the pair (X[o + i], X[o + M - 1 - i]) to
+// G = X[o + i] + X[o + M - 1 - i], H = t_i (X[o + i] - X[o + M - 1 - i]); then
+// the splitting levels, in reverse order, x[2m] = e[m], x[2m + 1] =
+// y[m] + y[m + 1] (y[h] = 0).
+// ------------------------------------------------------------------------
+template <class O>
+__device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1, int N, int lgN,
+                                            const typename O::W* __restrict__ tw, int lane) {
+    using V = typename O::V;
+    V* src = b0;
+    V* dst = b1;
+    const int half = N >> 1;
+    for (int lm = lgN; lm >= 1; --lm) {
+        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+        const typename O::W* twm = tw + (h - 1);
+        for (int idx = lane; idx < half; idx += 32) {
+            const int o = (idx >> lh) << lm, i = idx & (h - 1);
+            const V a = src[o + i], b = src[o + M - 1 - i];
+            dst[o + i] = O::add(a, b);
+            dst[o + h + i] = O::mul(O::sub(a, b), twm[i]);
+        }
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+    }
+    for (int lm = 1; lm <= lgN; ++lm) {
+        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+        for (int idx = lane; idx < half; idx += 32) {
+            const int o = (idx >> lh) << lm, m = idx & (h - 1);
+            dst[o + 2 * m] = src[o + m];
+            dst[o + 2 * m + 1] = m + 1 < h ? O::add(src[o + h + m], src[o + h + m + 1]) : src[o + h + m];
+        }
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
+// stage: 0 = along y (input g[j][i], FP64, one transform per column i, output
+//            T^T[i][l] = c_l (DCT-II over j)[l] for l < Km),
+//        1 = along x (input T^T[i][l], one transform per l, output G[k][l] =
+//            c_k (DCT-II over i)[k] for k < Km, FP64).
+template <class O>
+__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct_t(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
+                                                        const typename O::V* __restrict__ in, typename O::V* __restrict__ out,
+                                                        double* __restrict__ out64, const typename O::W* __restrict__ tw) {
+    using V = typename O::V;
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    V* fsm = reinterpret_cast<V*>(fsm_raw);
+    const int SP = n + 1;
+    V* stg = fsm;                                       // FCT_T x SP
+    V* work = fsm + FCT_T * SP;                         // FCT_WARPS x 2n
+    const int p = blockIdx.y;
+    const int t0 = blockIdx.x * FCT_T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntr = stage == 0 ? n : Km;                // transforms of this stage
+    // load: stage 0 rows g[j][t0 .. t0+15]; stage 1 rows T^T[i][t0 .. t0+15]
+    for (int idx = threadIdx.x; idx < FCT_T * n; idx += blockDim.x) {
+        const int j = idx / FCT_T, t = idx % FCT_T;
+        V v = O::zero();
+        if (t0 + t < ntr)
+            v = stage == 0 ? O::from_input(in64[(size_t)p * n * n + (size_t)j * n + t0 + t])
+                           : in[(size_t)p * n * Km + (size_t)j * Km + t0 + t];
+        stg[t * SP + j] = v;
+    }
+    __syncthreads();
+    V* b0 = work + warp * 2 * n;
+    V* b1 = b0 + n;
+    for (int t = warp; t < FCT_T; t += FCT_WARPS) {
+        for (int k = lane; k < n; k += 32) b0[k] = stg[t * SP + k];
+        __syncwarp();
+        const V* res = fct_warp_t<O>(b0, b1, n, lgn, tw, lane);
+        for (int k = lane; k < Km; k += 32) stg[t * SP + k] = k == 0 ? res[k] : O::mul(res[k], sqrt2_of<O>());
+        __syncwarp();
+    }
+    __syncthreads();
+    if (stage == 0) {   // T^T[t0 + t][l], l < Km: one contiguous row per transform
+        for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
+            const int t = idx / Km, l = idx % Km;
+            out[(size_t)p * n * Km + (size_t)(t0 + t) * Km + l] = stg[t * SP + l];
+        }
+    } else {            // G[k][t0 + t] in FP64
+        for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
+            const int k = idx / FCT_T, t = idx % FCT_T;
+            if (t0 + t < Km) out64[(size_t)p * Km * Km + (size_t)k * Km + t0 + t] = O::to_double(stg[t * SP + k]);
+        }
+    }
+}
+
+template <class O>
+static void launch_fct_t(Ctx& c, const double* g, int count, typename O::V* tmp, double* G, const typename O::W* tw) {
+    const int n = c.n, Km = c.Km;
+    int lgn = 0;
+    while ((1 << lgn) < n) ++lgn;
+    const size_t smem = 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
+    static size_t attr = 0;
+    if (attr < smem) {
+        check(cudaFuncSetAttribute(k_fct_t<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
+        attr = smem;
+    }
+    k_fct_t<O><<<dim3(n / FCT_T, count), 32 * FCT_WARPS, smem, c.stream>>>(0, n, lgn, Km, g, nullptr, tmp, nullptr, tw); ++c.pc.launches;
+    k_fct_t<O><<<dim3((Km + FCT_T - 1) / FCT_T, count), 32 * FCT_WARPS, smem, c.stream>>>(1, n, lgn, Km, nullptr, tmp, nullptr, G,
+                                                                                        tw); ++c.pc.launches;
+    check(cudaGetLastError(), "analysis2d");
+}
+
+// G = S^T g for `count` grids (FP64 in and out), in df32 for the mixed-precision
+// context (inputs and outputs FP64, ~1e-13 relative) and FP64 otherwise.
+void launch_analysis2d(Ctx& c, const double* g, int count, double* G) {
+    if (c.cfg.precision == SMC_P_FP32_REFINE)
+        launch_fct_t<DfOps>(c, g, count, reinterpret_cast<df32*>(c.fct_tmp), G, reinterpret_cast<const float2*>(c.fct_tw_df));
+    else
+        launch_fct_t<F64Ops>(c, g, count, c.fct_tmp, G, c.fct_tw);
 }
 
 // ------------------------------------------------------------------------

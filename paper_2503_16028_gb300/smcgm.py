@@ -33,6 +33,7 @@ class smc_config(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("tol_inner", ctypes.c_double), ("tol_outer", ctypes.c_double),
         ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int), ("fine_sweeps", ctypes.c_int),
         ("coarse_scale", ctypes.c_double), ("solve_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+        ("gradient", ctypes.c_int),
     ]
 
 
@@ -54,6 +55,7 @@ EXPORTS = {
     "smc_move_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _dp]),
     "smc_posterior_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "smc_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _ip]),
+    "smc_gradient": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
     "smc_get_particles": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "smc_set_particles": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "smc_set_schedule": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint]),
@@ -125,7 +127,7 @@ def make_config(preset, **overrides):
     cfg.n_particles = p["n_particles"]; cfg.n_components = p["n_components"]; cfg.gm_rank = p["gm_rank"]
     cfg.beta0 = p["beta0"]; cfg.ess_frac = p["ess_frac"]; cfg.seed = p["seed"]
     for key in ("em_iters", "var_floor", "kernel", "precision", "tol_inner", "tol_outer", "max_iter", "max_refine",
-                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch"):
+                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch", "gradient"):
         if key in p:
             setattr(cfg, key, p[key])
     cfg._keep = (obs, data)
@@ -214,6 +216,10 @@ class Sampler:
         self._check(self.lib.smc_forward(self.ctx, _ptr(X_dev), int(X_dev.shape[0]), _ptr(Phi_dev), _ptr(w_dev),
                                          ctypes.byref(it)), self.ctx)
         return it.value
+
+    def smc_gradient(self, X_dev, Phi_dev, G_dev):
+        """Phi(x) and dPhi/dx of the rows of X_dev (device tensors, FP64) into Phi_dev and G_dev."""
+        self._check(self.lib.smc_gradient(self.ctx, _ptr(X_dev), int(X_dev.shape[0]), _ptr(Phi_dev), _ptr(G_dev)), self.ctx)
 
     # --- state access ----------------------------------------------------
     def particles(self):

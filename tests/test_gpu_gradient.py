@@ -1,0 +1,139 @@
+"""The adjoint gradient of the potential (smc_gradient) against the oracle's
+adjoint (oracle/adjoint.py, itself pinned by finite differences), against
+finite differences of the library's own forward map, through
+torch.autograd, and across ragged batches."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2503_16028_gb300 import inputs, smcgm  # noqa: E402
+from oracle import adjoint as oadjoint, problem as oproblem  # noqa: E402
+
+PHI_RTOL = 1e-10
+GRAD_RTOL = 1e-9        # relative L2 of dPhi/dx (both paths solve to 1e-10 relative residual; measured ~1e-11)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_16028_gb300 import build
+    build.build()
+    smcgm.load_library()
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def _sampler(wl, N, precision, **kw):
+    return smcgm.Sampler(smcgm.make_config(wl, n_particles=N, n_components=1, precision=precision, gradient=1, **kw))
+
+
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+def test_gradient_matches_oracle_adjoint_64(precision):
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 6
+    s = _sampler(wl, N, precision)
+    prob = oproblem.from_workload(wl)
+    X, _ = s.particles()
+    X = X.copy()
+    X[3] *= 1.7                                   # rougher fields than the prior draws
+    X[4] += 0.3 * np.sqrt(prob.lam) * np.random.default_rng(4).standard_normal(prob.d)
+    Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+    Phi = torch.empty(N, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(Xd)
+    s.smc_gradient(Xd, Phi, G)
+    torch.cuda.synchronize()
+    Phi, G = Phi.cpu().numpy(), G.cpu().numpy()
+    worst = 0.0
+    for n in range(N):
+        phi, grad, _, _ = oadjoint.potential_and_gradient_2d(prob, X[n])
+        assert abs(Phi[n] - phi) <= PHI_RTOL * abs(phi), (n, Phi[n], phi)
+        e = _rel(G[n], grad)
+        worst = max(worst, e)
+        assert e < GRAD_RTOL, (n, e)
+    print("worst relative L2 gradient error", worst)
+    s.close()
+
+
+def test_gradient_matches_finite_differences_of_forward_map():
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 4
+    s = _sampler(wl, N, smcgm.SMC_P_FP32_REFINE)
+    X, _ = s.particles()
+    rng = np.random.default_rng(11)
+    Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+    Phi = torch.empty(N, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(Xd)
+    s.smc_gradient(Xd, Phi, G)
+    E = rng.standard_normal(X.shape)
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    eps = 1e-5
+    Fp = torch.empty(N, dtype=torch.float64, device="cuda")
+    Fm = torch.empty_like(Fp)
+    s.smc_forward(torch.tensor(X + eps * E, device="cuda"), Fp)
+    s.smc_forward(torch.tensor(X - eps * E, device="cuda"), Fm)
+    torch.cuda.synchronize()
+    fd = (Fp - Fm).cpu().numpy() / (2 * eps)
+    dd = np.sum(G.cpu().numpy() * E, axis=1)
+    gn = np.linalg.norm(G.cpu().numpy(), axis=1)
+    assert np.all(np.abs(fd - dd) <= 1e-6 * gn), (fd, dd)
+    s.close()
+
+
+def test_autograd_function_and_ragged_batches():
+    from paper_2503_16028_gb300.autograd import potential
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 13
+    s1 = _sampler(wl, N, smcgm.SMC_P_FP32_REFINE)
+    s2 = _sampler(wl, N, smcgm.SMC_P_FP32_REFINE, solve_batch=5)
+    X, _ = s1.particles()
+    Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+    Phi1 = torch.empty(N, dtype=torch.float64, device="cuda")
+    G1 = torch.empty_like(Xd)
+    s1.smc_gradient(Xd, Phi1, G1)
+    Phi2 = torch.empty_like(Phi1)
+    G2 = torch.empty_like(G1)
+    s2.smc_gradient(Xd, Phi2, G2)
+    torch.cuda.synchronize()
+    assert torch.equal(Phi1, Phi2) and torch.equal(G1, G2)      # 5 + 5 + 3 batches: bit-identical
+    Xa = Xd.clone().requires_grad_(True)
+    w = torch.linspace(0.5, 2.0, N, dtype=torch.float64, device="cuda")
+    (w * potential(Xa, s1)).sum().backward()
+    torch.cuda.synchronize()
+    assert torch.allclose(Xa.grad, w[:, None] * G1, rtol=0, atol=0)
+    s1.close()
+    s2.close()
+
+
+def test_gradient_needs_the_config_flag():
+    wl = inputs.load_workload("darcy64_bimodal")
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=2, n_components=1))
+    Xd = torch.zeros((2, s.d), dtype=torch.float64, device="cuda")
+    Phi = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(smcgm.SMCError) as ei:
+        s.smc_gradient(Xd, Phi, torch.empty_like(Xd))
+    assert "gradient" in str(ei.value)
+    s.close()
+
+
+def test_gradient_full_size_sampled():
+    """The metric workload (256^2, 128^2 modes, 4096 particles, mixed precision):
+    two particles against the oracle's adjoint."""
+    wl = inputs.load_workload("darcy256_precision")
+    s = smcgm.Sampler(smcgm.make_config(wl, gradient=1))
+    prob = oproblem.from_workload(wl)
+    X, _ = s.particles()
+    Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+    Phi = torch.empty(X.shape[0], dtype=torch.float64, device="cuda")
+    G = torch.empty_like(Xd)
+    s.smc_gradient(Xd, Phi, G)
+    torch.cuda.synchronize()
+    for n in (0, 4095):
+        phi, grad, _, _ = oadjoint.potential_and_gradient_2d(prob, X[n])
+        assert abs(Phi[n].item() - phi) <= PHI_RTOL * abs(phi)
+        assert _rel(G[n].cpu().numpy(), grad) < GRAD_RTOL
+    s.close()
