@@ -33,6 +33,8 @@ Modules
   adjoint  dPhi/dx by the adjoint of the discrete forward model (the drift of
            the Langevin equation of App. B; Langevin kernels cited in Sec. 1
            and Sec. 2.4).
+  langevin pCN-Langevin mutation: App. B's Langevin equation with the drift
+           kept, Crank-Nicolson in the linear part, explicit drift.
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force or invariants; none is "parity unpinned".

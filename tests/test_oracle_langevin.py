@@ -1,0 +1,73 @@
+"""Pins of the oracle's pCN-Langevin kernel (oracle/langevin.py).
+
+* Detailed balance written out with full Gaussian densities: for a quadratic
+  potential with a closed-form gradient, log alpha(u, v) must equal
+  [log pi_t(v) + log q(v, u)] - [log pi_t(u) + log q(u, v)] with
+  pi_t = exp(-t Phi) N(0, C) and q(u, .) = N(gamma u - (1-gamma) t C DPhi(u),
+  beta^2 C) evaluated directly (not through the prior-relative form).
+* No drift (t = 0, or a zero gradient): the pCN proposal and acceptance.
+* The Crank-Nicolson step: beta = sqrt(8 delta)/(2 + delta) gives
+  gamma = (2 - delta)/(2 + delta) and a drift factor 2 delta/(2 + delta).
+"""
+import numpy as np
+import pytest
+
+from oracle import langevin, pcngm
+
+
+def _quadratic(d, seed):
+    rng = np.random.default_rng(seed)
+    H = rng.standard_normal((d + 2, d))
+    y = rng.standard_normal(d + 2)
+    phi = lambda x: 0.5 * float(np.sum((H @ x - y) ** 2))
+    grad = lambda x: H.T @ (H @ x - y)
+    return phi, grad
+
+
+def _log_gauss(x, m, var):
+    return float(-0.5 * np.sum((x - m) ** 2 / var) - 0.5 * np.sum(np.log(2 * np.pi * var)))
+
+
+@pytest.mark.parametrize("t,beta", [(0.3, 0.2), (1.0, 0.5), (0.05, 0.9)])
+def test_detailed_balance_direct_densities(t, beta):
+    d = 6
+    lam = (1.0 + 0.3 * np.arange(d)) ** -2.0
+    phi, grad = _quadratic(d, 3)
+    rng = np.random.default_rng(5)
+    gm = np.sqrt(1 - beta ** 2)
+    for _ in range(5):
+        u = np.sqrt(lam) * rng.standard_normal(d)
+        v = np.sqrt(lam) * rng.standard_normal(d)
+        la = langevin.log_alpha(u, v, phi(u), phi(v), grad(u), grad(v), lam, beta, t)
+
+        def log_pi(x):
+            return -t * phi(x) + _log_gauss(x, 0.0, lam)
+
+        def log_q(a, b):
+            return _log_gauss(b, gm * a - (1 - gm) * t * lam * grad(a), beta ** 2 * lam)
+
+        direct = (log_pi(v) + log_q(v, u)) - (log_pi(u) + log_q(u, v))
+        assert abs(la - direct) <= 1e-10 * max(1.0, abs(direct)), (la, direct)
+
+
+def test_no_drift_is_pcn():
+    d = 5
+    lam = np.linspace(1.0, 0.1, d)
+    rng = np.random.default_rng(8)
+    u, z = rng.standard_normal(d), rng.standard_normal(d)
+    g = rng.standard_normal(d)
+    beta = 0.3
+    v0 = langevin.propose(u, g, lam, beta, 0.0, z)
+    assert np.allclose(v0, np.sqrt(1 - beta ** 2) * u + beta * np.sqrt(lam) * z, rtol=0, atol=1e-15)
+    v = langevin.propose(u, np.zeros(d), lam, beta, 0.7, z)
+    assert np.array_equal(v, v0)
+    la = langevin.log_alpha(u, v, 2.0, 1.5, np.zeros(d), np.zeros(d), lam, beta, 0.7)
+    assert la == pytest.approx(0.7 * 0.5, abs=1e-15)
+
+
+def test_crank_nicolson_step():
+    for delta in (0.01, 0.2, 1.0, 1.9):          # delta <= 2: beta <= 1 and gamma >= 0
+        beta = np.sqrt(8 * delta) / (2 + delta)
+        gm = langevin.gamma_of(beta)
+        assert gm == pytest.approx((2 - delta) / (2 + delta), rel=1e-13)
+        assert 1 - gm == pytest.approx(2 * delta / (2 + delta), rel=1e-12)
