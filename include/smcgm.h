@@ -49,8 +49,17 @@ typedef enum {
 
 /* Mutation kernels (App. A).  SMC_K_PCN: pCN (eq. pCNproposal, a_pCN);
  * SMC_K_PCN_GM: pCN-GM (Alg. 2); SMC_K_GM_INDEP: the mixture independence
- * sampler with every proposal accepted (Alg. 3, SMC-GM). */
-typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2 } smc_kernel;
+ * sampler with every proposal accepted (Alg. 3, SMC-GM); SMC_K_PCNL:
+ * pCN-Langevin, the Langevin equation of App. B with its drift kept
+ * (Crank-Nicolson in the linear part, explicit drift, tempered target
+ * exp(-t Phi) mu0): v = gamma u - (1 - gamma) t C DPhi(u) + beta C^{1/2} z,
+ * log alpha = t (Phi(u) - Phi(v)) + rho(v, u) - rho(u, v) with
+ * rho(a, b) = -(1-gamma) t <DPhi(a), b - gamma a>/beta^2
+ *             - (1-gamma)^2 t^2 <DPhi(a), C DPhi(a)>/(2 beta^2);
+ * each step evaluates Phi and DPhi at the proposal (smc_gradient's forward
+ * and adjoint solves), and smc_move starts from DPhi of the current
+ * particles (one extra gradient per call).  Needs cfg.gradient = 1. */
+typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2, SMC_K_PCNL = 3 } smc_kernel;
 
 /* Arithmetic of the forward solve.  SMC_P_FP64: FP64 multigrid-preconditioned
  * CG to tol_outer.  SMC_P_FP32_REFINE: FP32 multigrid-preconditioned CG inner

@@ -152,17 +152,18 @@ __global__ void __launch_bounds__(256) k_grad_u(int n, GradSrc<MIXED> S, const d
     }
 }
 
-void gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out) {
+int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out) {
     const int n = c.n;
     const size_t nn = (size_t)n * n;
     const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
+    int itmax = 0;
     for (int off = 0; off < count; off += c.B) {
         const int cnt = std::min(c.B, count - off);
         // 1. forward: field, coefficients, w, Phi
         if (mixed) launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
         else launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
         launch_setup_coeffs(c, cnt);
-        solve_batch(c, cnt, shared_rhs(c), c.w64);
+        itmax = std::max(itmax, solve_batch(c, cnt, shared_rhs(c), c.w64));
         launch_observe(c, c.w64, cnt, Phi_out + off);
         // 2. adjoint right-hand side
         check(cudaMemsetAsync(c.rhs, 0, (size_t)cnt * nn * sizeof(double), c.stream), "memset rhs");
@@ -171,7 +172,7 @@ void gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double*
         k_rhs_finish<<<cnt, 256, 0, c.stream>>>((int)nn, mixed ? 1 : 0, c.rhs, c.rhs_b2); ++c.pc.launches;
         // 3. adjoint solve
         const Rhs R{mixed ? nullptr : c.rhs, mixed ? reinterpret_cast<const float2*>(c.rhs) : nullptr, nn, c.rhs_b2, 0.0};
-        solve_batch(c, cnt, R, c.lam64);
+        itmax = std::max(itmax, solve_batch(c, cnt, R, c.lam64));
         // 4. dPhi/du into the right-hand side's storage (no longer needed)
         const dim3 grid((n / TILE) * (n / TILE), cnt);
         if (mixed) {
@@ -187,6 +188,7 @@ void gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double*
         launch_analysis2d(c, c.rhs, cnt, grad_out + (size_t)off * c.d);
     }
     check(cudaGetLastError(), "gradient");
+    return itmax;
 }
 
 }  // namespace smcgm

@@ -53,7 +53,8 @@ static const char* validate(const smc_config& c) {
     if (c.em_iters < 0) return "em_iters must be >= 0";
     if (!(c.beta0 > 0 && c.beta0 <= 1)) return "beta0 must be in (0, 1]";
     if (!(c.ess_frac > 0 && c.ess_frac <= 1)) return "ess_frac must be in (0, 1]";
-    if (c.kernel < 0 || c.kernel > 2) return "unknown kernel";
+    if (c.kernel < 0 || c.kernel > 3) return "unknown kernel";
+    if (c.kernel == SMC_K_PCNL && (!c.gradient || c.dim != 2)) return "the pCN-Langevin kernel needs gradient = 1 and dim = 2";
     if (c.precision < 0 || c.precision > 1) return "unknown precision";
     if (!(c.tol_inner > 0 && c.tol_inner < 1) || !(c.tol_outer > 0 && c.tol_outer < 1)) return "tolerances must be in (0, 1)";
     if (c.max_iter < 1 || c.max_refine < 1) return "max_iter and max_refine must be >= 1";
@@ -106,7 +107,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     const int dim = cfg.dim, n = cfg.n, Km = cfg.kl_modes;
     const int d = dim == 2 ? Km * Km : Km;
     const int N = cfg.n_particles;
-    const int K = cfg.kernel == SMC_K_PCN ? 1 : cfg.n_components;
+    const int K = (cfg.kernel == SMC_K_PCN || cfg.kernel == SMC_K_PCNL) ? 1 : cfg.n_components;
     const int r = std::min(cfg.gm_rank, d);
     const int B = cfg.solve_batch > 0 ? std::min(cfg.solve_batch, N) : N;
     const size_t cells = dim == 2 ? (size_t)n * n : (size_t)n;
@@ -149,6 +150,10 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
             C.lam64 = P.take<double>(bn);
             C.rhs = P.take<double>(bn);
             C.rhs_b2 = P.take<double>(B);
+        }
+        if (cfg.kernel == SMC_K_PCNL) {
+            C.G = P.take<double>((size_t)N * d);
+            C.GV = P.take<double>((size_t)N * d);
         }
         const int ntiles = (n / 16) * (n / 16);   // the finest tiled level's tiles (16 x 16 warp tiles or fewer)
         C.part.ntiles = ntiles;
@@ -440,7 +445,7 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
         else build_tma_maps<double>(c, c.s64);
     }
     set_prior_mixture(c);
-    c.fitted = (c.cfg.kernel == SMC_K_PCN);
+    c.fitted = (c.cfg.kernel == SMC_K_PCN || c.cfg.kernel == SMC_K_PCNL);
     c.t = 0.0;
     c.beta = c.cfg.kernel == SMC_K_GM_INDEP ? 1.0 : c.cfg.beta0;
     c.layer = 0;
@@ -510,7 +515,7 @@ smc_status gm_fit(smc_ctx* ctx, double* loglik) {
     if (!ctx) return SMC_EINVAL;
     Ctx& c = ctx->c;
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "gm_fit: context not initialised");
-    if (c.cfg.kernel == SMC_K_PCN) { if (loglik) *loglik = 0.0; return SMC_OK; }
+    if (c.cfg.kernel == SMC_K_PCN || c.cfg.kernel == SMC_K_PCNL) { if (loglik) *loglik = 0.0; return SMC_OK; }
     API_BEGIN
     const double ll = gm_fit_device(c);
     if (loglik) *loglik = ll;
@@ -527,14 +532,26 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
     API_BEGIN
     int* accn = c.icount;
     check(cudaMemsetAsync(accn, 0, sizeof(int), c.stream), "memset");
-    launch_move_tables(c);
     const long long nc0 = c.nonconv;
     int itmax = 0;
-    for (int s = 0; s < steps; ++s) {
-        launch_propose(c);
-        itmax = std::max(itmax, forward_solve(c, c.V, c.N, c.PhiV, nullptr));
-        launch_accept(c, accn);
-        ++c.step;
+    long long solves = (long long)c.N * steps;
+    if (c.cfg.kernel == SMC_K_PCNL) {
+        itmax = gradient_batch(c, c.X, c.N, c.Phi2, c.G);   // DPhi of the current particles (Phi2: scratch)
+        for (int s = 0; s < steps; ++s) {
+            launch_propose_pcnl(c);
+            itmax = std::max(itmax, gradient_batch(c, c.V, c.N, c.PhiV, c.GV));
+            launch_accept_pcnl(c, accn);
+            ++c.step;
+        }
+        solves = 2LL * c.N * (steps + 1);
+    } else {
+        launch_move_tables(c);
+        for (int s = 0; s < steps; ++s) {
+            launch_propose(c);
+            itmax = std::max(itmax, forward_solve(c, c.V, c.N, c.PhiV, nullptr));
+            launch_accept(c, accn);
+            ++c.step;
+        }
     }
     int hacc = 0;
     check(cudaMemcpyAsync(&hacc, accn, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
@@ -550,7 +567,7 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
     }
     ++c.layer;
     c.stage = 1;
-    if ((c.nonconv - nc0) * 100 > (long long)c.N * steps)
+    if ((c.nonconv - nc0) * 100 > solves)
         return fail(ctx, SMC_ENOCONV, "more than 1% of forward solves missed the tolerance");
     return SMC_OK;
     API_END(ctx)

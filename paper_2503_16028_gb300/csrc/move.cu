@@ -232,4 +232,103 @@ void launch_accept(Ctx& c, int* acc_count) {
     check(cudaGetLastError(), "accept");
 }
 
+// ------------------------------------------------------------------------
+// pCN-Langevin mutation (App. B's Langevin equation with its drift kept for
+// the tempered target exp(-t Phi) mu0; Crank-Nicolson in the linear part,
+// explicit drift):
+//   v = gamma u - (1 - gamma) t C g_u + beta C^{1/2} z,   g = DPhi, C = diag(lambda),
+//   log alpha = t (Phi(u) - Phi(v)) + rho(v, u) - rho(u, v),
+//   rho(a, b) = -(1 - gamma) t <g_a, b - gamma a> / beta^2
+//               - (1 - gamma)^2 t^2 <g_a, C g_a> / (2 beta^2).
+// The normals and the accept uniform are those of the pCN-GM move.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_propose_pcnl(int d, const double* __restrict__ X, const double* __restrict__ G,
+                                                      double* __restrict__ V, const double* __restrict__ lam,
+                                                      const double* __restrict__ sqrtlam, double beta, double gamma, double kt,
+                                                      uint32_t step, Key key, const float2* __restrict__ ntab, NormalConsts nc) {
+    __shared__ float2 tab_s[NORMAL_TAB];
+    for (int i = threadIdx.x; i < NORMAL_TAB; i += blockDim.x) tab_s[i] = ntab[i];
+    __syncthreads();
+    const int p = blockIdx.x;
+    const double* u = X + (size_t)p * d;
+    const double* g = G + (size_t)p * d;
+    double* v = V + (size_t)p * d;
+    for (int m = threadIdx.x; m < (d + 1) / 2; m += blockDim.x) {
+        double z[2];
+        normal_pair_df((uint32_t)m, (uint32_t)p, step, P_NORMAL, key, tab_s, nc, z[0], z[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = 2 * m + h;
+            if (i >= d) break;
+            v[i] = (gamma * u[i] - kt * lam[i] * g[i]) + (beta * sqrtlam[i]) * z[h];
+        }
+    }
+}
+
+// Accept/reject of the pCN-Langevin step, one block per particle: the four
+// inner products of rho by a block reduction in a fixed order, then the same
+// accept rule as k_accept and the copies v -> u, g_v -> g_u, Phi_v -> Phi.
+__global__ void __launch_bounds__(256) k_accept_pcnl(int d, const double* __restrict__ lam, double t, double beta, double gamma,
+                                                     uint32_t step, Key key, double* __restrict__ X, const double* __restrict__ V,
+                                                     double* __restrict__ G, const double* __restrict__ GV,
+                                                     double* __restrict__ Phi, const double* __restrict__ PhiV,
+                                                     double* __restrict__ logalpha, unsigned char* __restrict__ acc,
+                                                     int* __restrict__ count) {
+    __shared__ double red[32];
+    __shared__ int s_acc;
+    const int p = blockIdx.x;
+    const double* u = X + (size_t)p * d;
+    const double* v = V + (size_t)p * d;
+    const double* gu = G + (size_t)p * d;
+    const double* gv = GV + (size_t)p * d;
+    double a = 0.0, b = 0.0, c = 0.0, e = 0.0;   // <g_u, v - gamma u>, <g_u, C g_u>, <g_v, u - gamma v>, <g_v, C g_v>
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        a += gu[i] * (v[i] - gamma * u[i]);
+        b += gu[i] * lam[i] * gu[i];
+        c += gv[i] * (u[i] - gamma * v[i]);
+        e += gv[i] * lam[i] * gv[i];
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    c = block_sum(c, red);
+    e = block_sum(e, red);
+    if (threadIdx.x == 0) {
+        const double k = (1.0 - gamma) * t, ib2 = 1.0 / (beta * beta);
+        const double rho_uv = -k * a * ib2 - 0.5 * k * k * b * ib2;
+        const double rho_vu = -k * c * ib2 - 0.5 * k * k * e * ib2;
+        const double la = t * (Phi[p] - PhiV[p]) + rho_vu - rho_uv;
+        U4 wa = philox(0u, (uint32_t)p, step, P_ACCEPT, key.k0, key.k1);
+        const double U = open53(wa.x, wa.y);
+        const int ok = (la >= 0.0 || log(U) < la) ? 1 : 0;
+        logalpha[p] = la;
+        acc[p] = (unsigned char)ok;
+        if (ok) {
+            Phi[p] = PhiV[p];
+            atomicAdd(count, 1);
+        }
+        s_acc = ok;
+    }
+    __syncthreads();
+    if (s_acc) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            X[(size_t)p * d + i] = v[i];
+            G[(size_t)p * d + i] = gv[i];
+        }
+    }
+}
+
+void launch_propose_pcnl(Ctx& c) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_propose_pcnl<<<c.N, 256, 0, c.stream>>>(c.d, c.X, c.G, c.V, c.lam, c.sqrtlam, c.beta, gamma, (1.0 - gamma) * c.t, c.step,
+                                              c.key, reinterpret_cast<const float2*>(c.normtab), c.normc); ++c.pc.launches;
+    check(cudaGetLastError(), "propose pcnl");
+}
+
+void launch_accept_pcnl(Ctx& c, int* acc_count) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_accept_pcnl<<<c.N, 256, 0, c.stream>>>(c.d, c.lam, c.t, c.beta, gamma, c.step, c.key, c.X, c.V, c.G, c.GV, c.Phi, c.PhiV,
+                                             c.logalpha, c.acc, acc_count); ++c.pc.launches;
+    check(cudaGetLastError(), "accept pcnl");
+}
+
 }  // namespace smcgm

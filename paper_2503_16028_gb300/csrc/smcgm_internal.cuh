@@ -118,12 +118,14 @@ void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w
 void launch_move_tables(Ctx& c);
 void launch_propose(Ctx& c);
 void launch_accept(Ctx& c, int* acc_count);
+void launch_propose_pcnl(Ctx& c);
+void launch_accept_pcnl(Ctx& c, int* acc_count);
 void launch_temper(Ctx& c, double* out5);
 void launch_resample(Ctx& c);
 double gm_fit_device(Ctx& c);
 void launch_moments(Ctx& c, double* mean, double* var);
 void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
-void gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out);
+int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out);   // largest CG iteration count
 
 struct Ctx {
     smc_config cfg;
@@ -155,6 +157,7 @@ struct Ctx {
     // gradient (cfg.gradient): the adjoint solution and a per-particle right-hand
     // side (FP64, or df32 pairs in the same storage), reused for dPhi/du
     double *lam64 = nullptr, *rhs = nullptr, *rhs_b2 = nullptr;
+    double *G = nullptr, *GV = nullptr;   // pCN-Langevin: DPhi of the particles and of the proposals (N x d)
     float* exptab = nullptr;   // 2^(j/64), j < 64, as df32 pairs (the df32 exponential)
     ExpConsts expc{};
     float* normtab = nullptr;  // logarithm table of the df32 Box-Muller normals (NORMAL_TAB pairs)

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libsmcgm.so")
 
 SMC_STATIC_RESAMPLE_MAX = 32768
 SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ENOCONV, SMC_EDEGENERATE, SMC_ESTATE = range(7)
-SMC_K_PCN, SMC_K_PCN_GM, SMC_K_GM_INDEP = range(3)
+SMC_K_PCN, SMC_K_PCN_GM, SMC_K_GM_INDEP, SMC_K_PCNL = range(4)
 SMC_P_FP64, SMC_P_FP32_REFINE = range(2)
 STATUS_NAMES = ["SMC_OK", "SMC_EINVAL", "SMC_ENOMEM", "SMC_ECUDA", "SMC_ENOCONV", "SMC_EDEGENERATE", "SMC_ESTATE"]
 
@@ -155,7 +155,7 @@ class Sampler:
         self.ctx = ctx
         self.d = cfg.kl_modes ** 2 if cfg.dim == 2 else cfg.kl_modes
         self.N = cfg.n_particles
-        self.K = 1 if cfg.kernel == SMC_K_PCN else cfg.n_components
+        self.K = 1 if cfg.kernel in (SMC_K_PCN, SMC_K_PCNL) else cfg.n_components
         self.r = min(cfg.gm_rank, self.d)
 
     def _check(self, st, ctx, allow=()):
