@@ -27,6 +27,21 @@ with g_a = DPhi(a) in KL coordinates, C = diag(lambda).  With g = 0 (or
 t = 0) this is the pCN kernel and its acceptance t (Phi(u) - Phi(v)).
 Random numbers: the normals and the accept uniform of the pCN-GM move
 (Philox purposes NORMAL and ACCEPT with the same counters).
+
+GMpCN-Langevin (a definition: the paper gives neither Langevin kernel).  The
+pCN-GM proposal of Sec. 2.3 with the same drift, preconditioned by the
+drawn component's covariance:
+
+  v = gamma u + (1 - gamma) m_j - (1 - gamma) t C_j DPhi(u) + beta C_j^{1/2} z,
+
+C_j = diag(lambda_j) on the mixture modes S and C elsewhere.  Against the
+mu0-reversible pCN kernel the acceptance is
+
+  log alpha = t (Phi(u) - Phi(v)) + log sum_j w_j R_j(v, u) - log sum_j w_j R_j(u, v),
+  R_j(a, b) = N(b; gamma a + (1-gamma) m_j - (1-gamma) t C_j DPhi(a), beta^2 C_j)
+              / N(b; gamma a, beta^2 C)      (over all d modes).
+
+With DPhi = 0 it is the pCN-GM kernel; with one prior component, pCN-Langevin.
 """
 import numpy as np
 
@@ -62,6 +77,55 @@ def move_particle(x, phi_x, g_x, lam, beta, t, seed, n, step, potential_and_grad
     v = propose(x, g_x, lam, beta, t, z)
     phi_v, g_v = potential_and_gradient(v)
     la = log_alpha(x, v, phi_x, phi_v, g_x, g_v, lam, beta, t)
+    Ua = float(philox.uniforms(seed, 0, n, step, philox.ACCEPT))
+    if pcngm.accept(la, Ua):
+        return v, phi_v, g_v, True, la, phi_v
+    return x, phi_x, g_x, False, la, phi_v
+
+
+def _component_lams(mix, j):
+    """(mean shift (1-gamma) m_j and variance factors lambda_j) as full d-vectors."""
+    lamj = mix.lam0.copy()
+    lamj[mix.S] = mix.lam[j]
+    mj = np.zeros_like(mix.lam0)
+    mj[mix.S] = mix.m[j]
+    return mj, lamj
+
+
+def gm_propose(x, g, j, z, mix, beta, t):
+    """v = gamma u + (1 - gamma) m_j - (1 - gamma) t C_j g + beta C_j^{1/2} z."""
+    gm = gamma_of(beta)
+    mj, lamj = _component_lams(mix, j)
+    return gm * x + (1.0 - gm) * mj - (1.0 - gm) * t * lamj * g + beta * np.sqrt(lamj) * z
+
+
+def gm_log_R(b, a, g_a, mix, beta, t):
+    """(K,) log R_j(a, b), every mode written out."""
+    gm = gamma_of(beta)
+    out = np.empty(mix.K)
+    base = gm * a
+    q0 = -0.5 * np.sum((b - base) ** 2 / (beta ** 2 * mix.lam0) + np.log(beta ** 2 * mix.lam0))
+    for j in range(mix.K):
+        mj, lamj = _component_lams(mix, j)
+        mean = base + (1.0 - gm) * mj - (1.0 - gm) * t * lamj * g_a
+        out[j] = -0.5 * np.sum((b - mean) ** 2 / (beta ** 2 * lamj) + np.log(beta ** 2 * lamj)) - q0
+    return out
+
+
+def gm_log_alpha(x, v, phi_x, phi_v, g_x, g_v, mix, beta, t):
+    lw = np.log(mix.w)
+    return (t * (phi_x - phi_v) + pcngm.logsumexp(lw + gm_log_R(x, v, g_v, mix, beta, t))
+            - pcngm.logsumexp(lw + gm_log_R(v, x, g_x, mix, beta, t)))
+
+
+def gm_move_particle(x, phi_x, g_x, mix, beta, t, seed, n, step, potential_and_gradient):
+    """One GMpCN-Langevin step (component draw, normals and accept uniform as in the pCN-GM move)."""
+    Uc = float(philox.uniforms(seed, 0, n, step, philox.COMP))
+    j = pcngm.choose_component(mix.w, Uc)
+    z = philox.normals(seed, x.shape[0], n, step, philox.NORMAL)
+    v = gm_propose(x, g_x, j, z, mix, beta, t)
+    phi_v, g_v = potential_and_gradient(v)
+    la = gm_log_alpha(x, v, phi_x, phi_v, g_x, g_v, mix, beta, t)
     Ua = float(philox.uniforms(seed, 0, n, step, philox.ACCEPT))
     if pcngm.accept(la, Ua):
         return v, phi_v, g_v, True, la, phi_v

@@ -71,3 +71,58 @@ def test_crank_nicolson_step():
         gm = langevin.gamma_of(beta)
         assert gm == pytest.approx((2 - delta) / (2 + delta), rel=1e-13)
         assert 1 - gm == pytest.approx(2 * delta / (2 + delta), rel=1e-12)
+
+
+def _mixture(d, r, K, seed):
+    rng = np.random.default_rng(seed)
+    lam0 = (1.0 + 0.3 * np.arange(d)) ** -2.0
+    S = np.arange(r)
+    w = rng.dirichlet(np.ones(K) * 2)
+    m = rng.standard_normal((K, r)) * np.sqrt(lam0[S]) * 0.7
+    lam = lam0[S] * rng.uniform(0.3, 1.5, size=(K, r))
+    return pcngm.Mixture(S, w, m, lam, lam0)
+
+
+@pytest.mark.parametrize("t,beta", [(0.3, 0.2), (1.0, 0.6)])
+def test_gm_detailed_balance_direct_densities(t, beta):
+    """GMpCN-Langevin: log alpha against the mixture proposal densities and the
+    tempered posterior written out in full."""
+    d, r, K = 7, 4, 3
+    mix = _mixture(d, r, K, 9)
+    lam = mix.lam0
+    phi, grad = _quadratic(d, 4)
+    gm = np.sqrt(1 - beta ** 2)
+    rng = np.random.default_rng(12)
+
+    def log_q(a, b):
+        terms = []
+        for j in range(K):
+            lamj = lam.copy(); lamj[mix.S] = mix.lam[j]
+            mj = np.zeros(d); mj[mix.S] = mix.m[j]
+            mean = gm * a + (1 - gm) * mj - (1 - gm) * t * lamj * grad(a)
+            terms.append(np.log(mix.w[j]) + _log_gauss(b, mean, beta ** 2 * lamj))
+        return pcngm.logsumexp(np.array(terms))
+
+    for _ in range(5):
+        u = np.sqrt(lam) * rng.standard_normal(d)
+        v = np.sqrt(lam) * rng.standard_normal(d)
+        la = langevin.gm_log_alpha(u, v, phi(u), phi(v), grad(u), grad(v), mix, beta, t)
+        direct = (-t * phi(v) + _log_gauss(v, 0.0, lam) + log_q(v, u)) - (-t * phi(u) + _log_gauss(u, 0.0, lam) + log_q(u, v))
+        assert abs(la - direct) <= 1e-10 * max(1.0, abs(direct)), (la, direct)
+
+
+def test_gm_special_cases():
+    d, r = 6, 3
+    lam0 = (1.0 + 0.3 * np.arange(d)) ** -2.0
+    rng = np.random.default_rng(2)
+    u, v, g_u, g_v = (rng.standard_normal(d) for _ in range(4))
+    # one prior component: the pCN-Langevin kernel
+    prior_mix = pcngm.Mixture.prior(lam0, np.arange(r), K=1)
+    a = langevin.gm_log_alpha(u, v, 1.0, 0.5, g_u, g_v, prior_mix, 0.3, 0.4)
+    b = langevin.log_alpha(u, v, 1.0, 0.5, g_u, g_v, lam0, 0.3, 0.4)
+    assert a == pytest.approx(b, rel=1e-12, abs=1e-12)
+    # zero drift: the pCN-GM kernel
+    mix = _mixture(d, r, 2, 5)
+    a = langevin.gm_log_alpha(u, v, 1.0, 0.5, g_u, g_v, mix, 0.3, 0.0)
+    b = pcngm.log_alpha(0.0, 1.0, 0.5, pcngm.log_mixture_ratio(u, v, mix, 0.3))
+    assert a == pytest.approx(b, rel=1e-12, abs=1e-12)
