@@ -58,8 +58,15 @@ typedef enum {
  *             - (1-gamma)^2 t^2 <DPhi(a), C DPhi(a)>/(2 beta^2);
  * each step evaluates Phi and DPhi at the proposal (smc_gradient's forward
  * and adjoint solves), and smc_move starts from DPhi of the current
- * particles (one extra gradient per call).  Needs cfg.gradient = 1. */
-typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2, SMC_K_PCNL = 3 } smc_kernel;
+ * particles (one extra gradient per call).  Needs cfg.gradient = 1.
+ * SMC_K_GMPCNL: GMpCN-Langevin (a definition; the paper gives no Langevin
+ * kernel): the pCN-GM proposal with the drift preconditioned by the drawn
+ * component, v = gamma u + (1-gamma) m_j - (1-gamma) t C_j DPhi(u) +
+ * beta C_j^{1/2} z, and log alpha = t (Phi(u) - Phi(v)) + log sum_j w_j
+ * R_j(v, u) - log sum_j w_j R_j(u, v), R_j(a, b) the ratio of the drawn
+ * component's proposal density to the pCN one; needs cfg.gradient = 1 and a
+ * mixture (gm_fit or smc_set_mixture). */
+typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2, SMC_K_PCNL = 3, SMC_K_GMPCNL = 4 } smc_kernel;
 
 /* Arithmetic of the forward solve.  SMC_P_FP64: FP64 multigrid-preconditioned
  * CG to tol_outer.  SMC_P_FP32_REFINE: FP32 multigrid-preconditioned CG inner

@@ -53,8 +53,9 @@ static const char* validate(const smc_config& c) {
     if (c.em_iters < 0) return "em_iters must be >= 0";
     if (!(c.beta0 > 0 && c.beta0 <= 1)) return "beta0 must be in (0, 1]";
     if (!(c.ess_frac > 0 && c.ess_frac <= 1)) return "ess_frac must be in (0, 1]";
-    if (c.kernel < 0 || c.kernel > 3) return "unknown kernel";
-    if (c.kernel == SMC_K_PCNL && (!c.gradient || c.dim != 2)) return "the pCN-Langevin kernel needs gradient = 1 and dim = 2";
+    if (c.kernel < 0 || c.kernel > 4) return "unknown kernel";
+    if ((c.kernel == SMC_K_PCNL || c.kernel == SMC_K_GMPCNL) && (!c.gradient || c.dim != 2))
+        return "the Langevin kernels need gradient = 1 and dim = 2";
     if (c.precision < 0 || c.precision > 1) return "unknown precision";
     if (!(c.tol_inner > 0 && c.tol_inner < 1) || !(c.tol_outer > 0 && c.tol_outer < 1)) return "tolerances must be in (0, 1)";
     if (c.max_iter < 1 || c.max_refine < 1) return "max_iter and max_refine must be >= 1";
@@ -151,7 +152,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
             C.rhs = P.take<double>(bn);
             C.rhs_b2 = P.take<double>(B);
         }
-        if (cfg.kernel == SMC_K_PCNL) {
+        if (cfg.kernel == SMC_K_PCNL || cfg.kernel == SMC_K_GMPCNL) {
             C.G = P.take<double>((size_t)N * d);
             C.GV = P.take<double>((size_t)N * d);
         }
@@ -541,6 +542,18 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
             launch_propose_pcnl(c);
             itmax = std::max(itmax, gradient_batch(c, c.V, c.N, c.PhiV, c.GV));
             launch_accept_pcnl(c, accn);
+            ++c.step;
+        }
+        solves = 2LL * c.N * (steps + 1);
+    } else if (c.cfg.kernel == SMC_K_GMPCNL) {
+        launch_move_tables(c);
+        itmax = gradient_batch(c, c.X, c.N, c.Phi2, c.G);
+        for (int s = 0; s < steps; ++s) {
+            launch_propose(c);                               // with the drift; the terms wait for DPhi(v)
+            itmax = std::max(itmax, gradient_batch(c, c.V, c.N, c.PhiV, c.GV));
+            launch_gmpcnl_terms(c);
+            launch_accept(c, accn);
+            launch_copy_accepted_gradients(c);
             ++c.step;
         }
         solves = 2LL * c.N * (steps + 1);

@@ -104,12 +104,15 @@ void launch_move_tables(Ctx& c) {
     check(cudaGetLastError(), "move tables");
 }
 
-// One block per particle: v, then the 2K log-ratio terms.
+// One block per particle: v, then the 2K log-ratio terms.  With a gradient
+// G (GMpCN-Langevin) v also takes the drift -(1 - gamma) t C_j G (kt =
+// (1 - gamma) t) and the terms are left to k_gmpcnl_terms, which needs DPhi(v).
 __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const double* __restrict__ X, double* __restrict__ V,
                                                  const double* __restrict__ sqrtlam, const int* __restrict__ slot,
                                                  const int* __restrict__ S, const double* __restrict__ tab, double beta, double gamma,
                                                  uint32_t step, Key key, double* __restrict__ lfwd, double* __restrict__ lrev,
-                                                 const float2* __restrict__ ntab, NormalConsts nc) {
+                                                 const float2* __restrict__ ntab, NormalConsts nc, const double* __restrict__ G,
+                                                 const double* __restrict__ lam, const double* __restrict__ glam, double kt) {
     __shared__ int s_j;
     __shared__ float2 tab_s[NORMAL_TAB];
     for (int i = threadIdx.x; i < NORMAL_TAB; i += blockDim.x) tab_s[i] = ntab[i];
@@ -139,9 +142,12 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
             if (cidx >= d) break;
             const int sl = slot[cidx];
             const double gu = gamma * u[cidx];
-            v[cidx] = sl < 0 ? gu + (beta * sqrtlam[cidx]) * z[h] : (gu + mu[sl]) + sq[sl] * z[h];
+            double vv = sl < 0 ? gu + (beta * sqrtlam[cidx]) * z[h] : (gu + mu[sl]) + sq[sl] * z[h];
+            if (G) vv -= kt * (sl < 0 ? lam[cidx] : glam[(size_t)j * r + sl]) * G[(size_t)p * d + cidx];
+            v[cidx] = vv;
         }
     }
+    if (G) return;
     __syncthreads();
     // log-ratio terms: warp w handles components j = w, w + nwarps, ...
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -174,8 +180,10 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
 
 void launch_propose(Ctx& c) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
+    const bool drift = c.cfg.kernel == SMC_K_GMPCNL;
     k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma, c.step, c.key,
-                                         c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab), c.normc); ++c.pc.launches;
+                                         c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab), c.normc,
+                                         drift ? c.G : nullptr, c.lam, c.glam, (1.0 - gamma) * c.t); ++c.pc.launches;
     check(cudaGetLastError(), "propose");
 }
 
@@ -315,6 +323,92 @@ __global__ void __launch_bounds__(256) k_accept_pcnl(int d, const double* __rest
             G[(size_t)p * d + i] = gv[i];
         }
     }
+}
+
+// GMpCN-Langevin acceptance terms, one block per particle, after DPhi(v):
+//   lfwd_j = log R_j(u, v), lrev_j = log R_j(v, u),
+//   log R_j(a, b) = sum_{s in S} [ 1/2 log(lambda_s / lambda_js)
+//                                  - (e_s - (1-gamma) m_js + kt lambda_js g_a,s)^2 / (2 beta^2 lambda_js)
+//                                  + e_s^2 / (2 beta^2 lambda_s) ]
+//                 + sum_{i not in S} [ -kt e_i g_a,i - kt^2 lambda_i g_a,i^2 / 2 ] / beta^2,
+// e = b - gamma a, kt = (1 - gamma) t; the sum outside S is the same for every
+// component (there C_j = C and m_j = 0) and is added to each term.
+__global__ void __launch_bounds__(256) k_gmpcnl_terms(int d, int K, int r, const double* __restrict__ X,
+                                                      const double* __restrict__ V, const double* __restrict__ G,
+                                                      const double* __restrict__ GV, const double* __restrict__ lam,
+                                                      const double* __restrict__ glam, const int* __restrict__ slot,
+                                                      const int* __restrict__ S, const double* __restrict__ tab, double beta,
+                                                      double gamma, double kt, double* __restrict__ lfwd, double* __restrict__ lrev) {
+    __shared__ double red[32];
+    __shared__ double s_tail[2];
+    const int p = blockIdx.x;
+    const int Kr = K * r;
+    const double* u = X + (size_t)p * d;
+    const double* v = V + (size_t)p * d;
+    const double* gu = G + (size_t)p * d;
+    const double* gv = GV + (size_t)p * d;
+    const double ib2 = 1.0 / (beta * beta);
+    double tf = 0.0, tr = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        if (slot[i] >= 0) continue;
+        const double ef = v[i] - gamma * u[i], er = u[i] - gamma * v[i];
+        tf += -kt * ef * gu[i] - 0.5 * kt * kt * lam[i] * gu[i] * gu[i];
+        tr += -kt * er * gv[i] - 0.5 * kt * kt * lam[i] * gv[i] * gv[i];
+    }
+    tf = block_sum(tf, red);
+    tr = block_sum(tr, red);
+    if (threadIdx.x == 0) {
+        s_tail[0] = tf * ib2;
+        s_tail[1] = tr * ib2;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const double* c0 = tab;
+    const double* aa = tab + Kr;
+    const double* mm = tab + 2 * Kr;
+    const double* bb = tab + 4 * Kr;
+    for (int jj = warp; jj < K; jj += nw) {
+        double f = 0.0, rv = 0.0;
+        for (int s2 = lane; s2 < r; s2 += 32) {
+            const int cidx = S[s2];
+            const int ti = jj * r + s2;
+            const double lj = glam[ti];
+            const double ef = v[cidx] - gamma * u[cidx];
+            const double er = u[cidx] - gamma * v[cidx];
+            const double df = ef - mm[ti] + kt * lj * gu[cidx], dr = er - mm[ti] + kt * lj * gv[cidx];
+            f += c0[ti] - df * df * aa[ti] + ef * ef * bb[s2];
+            rv += c0[ti] - dr * dr * aa[ti] + er * er * bb[s2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f += __shfl_down_sync(0xffffffffu, f, o);
+            rv += __shfl_down_sync(0xffffffffu, rv, o);
+        }
+        if (lane == 0) {
+            lfwd[(size_t)p * K + jj] = f + s_tail[0];
+            lrev[(size_t)p * K + jj] = rv + s_tail[1];
+        }
+    }
+}
+
+// G_u <- G_v for the accepted particles (after k_accept).
+__global__ void __launch_bounds__(256) k_copy_accepted(int d, const unsigned char* __restrict__ acc, const double* __restrict__ GV,
+                                                       double* __restrict__ G) {
+    const int p = blockIdx.x;
+    if (!acc[p]) return;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) G[(size_t)p * d + i] = GV[(size_t)p * d + i];
+}
+
+void launch_gmpcnl_terms(Ctx& c) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_gmpcnl_terms<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.G, c.GV, c.lam, c.glam, c.slot, c.S, c.tab, c.beta, gamma,
+                                              (1.0 - gamma) * c.t, c.lfwd, c.lrev); ++c.pc.launches;
+    check(cudaGetLastError(), "gmpcnl terms");
+}
+
+void launch_copy_accepted_gradients(Ctx& c) {
+    k_copy_accepted<<<c.N, 256, 0, c.stream>>>(c.d, c.acc, c.GV, c.G); ++c.pc.launches;
+    check(cudaGetLastError(), "copy gradients");
 }
 
 void launch_propose_pcnl(Ctx& c) {

@@ -119,6 +119,8 @@ void launch_move_tables(Ctx& c);
 void launch_propose(Ctx& c);
 void launch_accept(Ctx& c, int* acc_count);
 void launch_propose_pcnl(Ctx& c);
+void launch_gmpcnl_terms(Ctx& c);
+void launch_copy_accepted_gradients(Ctx& c);
 void launch_accept_pcnl(Ctx& c, int* acc_count);
 void launch_temper(Ctx& c, double* out5);
 void launch_resample(Ctx& c);
