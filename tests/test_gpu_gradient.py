@@ -137,3 +137,36 @@ def test_gradient_full_size_sampled():
         assert abs(Phi[n].item() - phi) <= PHI_RTOL * abs(phi)
         assert _rel(G[n].cpu().numpy(), grad) < GRAD_RTOL
     s.close()
+
+
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+def test_gradient_32_directions_128(precision):
+    """The differentiation workload's check: 128^2 grid, 64^2 modes, N = 2048,
+    central differences with eps = 1e-6 along 32 random unit KL directions agree
+    with the adjoint gradient to 1e-6 of |dPhi/dx|."""
+    wl = inputs.load_workload("darcy256_precision")
+    s = smcgm.Sampler(smcgm.make_config(wl, n=128, kl_modes=64, n_particles=2048, n_components=1,
+                                        precision=precision, gradient=1))
+    X, _ = s.particles()
+    x = X[7]
+    d = x.shape[0]
+    rng = np.random.default_rng(128)
+    E = rng.standard_normal((32, d))
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    eps = 1e-6
+    Xd = torch.tensor(x[None, :], dtype=torch.float64, device="cuda")
+    Phi = torch.empty(1, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(Xd)
+    s.smc_gradient(Xd, Phi, G)
+    P = torch.tensor(np.concatenate([x + eps * E, x - eps * E]), dtype=torch.float64, device="cuda")
+    F = torch.empty(64, dtype=torch.float64, device="cuda")
+    s.smc_forward(P, F)
+    torch.cuda.synchronize()
+    F = F.cpu().numpy()
+    fd = (F[:32] - F[32:]) / (2 * eps)
+    g = G.cpu().numpy()[0]
+    dd = E @ g
+    err = np.max(np.abs(fd - dd)) / np.linalg.norm(g)
+    print("max |FD - <grad, e>| / |grad| over 32 directions:", err)
+    assert err < 1e-6, err
+    s.close()
