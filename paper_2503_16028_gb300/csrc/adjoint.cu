@@ -165,6 +165,7 @@ int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* 
         launch_setup_coeffs(c, cnt);
         itmax = std::max(itmax, solve_batch(c, cnt, shared_rhs(c), c.w64));
         launch_observe(c, c.w64, cnt, Phi_out + off);
+        launch_mark_out_of_range(c, cnt, Phi_out + off);
         // 2. adjoint right-hand side
         check(cudaMemsetAsync(c.rhs, 0, (size_t)cnt * nn * sizeof(double), c.stream), "memset rhs");
         k_adjoint_scatter<<<(cnt + 127) / 128, 128, 0, c.stream>>>(n, cnt, c.nobs, c.w64, c.obs, c.data,

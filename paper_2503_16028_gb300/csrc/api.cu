@@ -140,6 +140,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
             C.Elo = P.take<float>((size_t)B * n); C.Nlo = P.take<float>((size_t)B * n);
             C.w64 = P.take<double>(bn);
             C.bdf = P.take<float2>(cells);
+            C.badp = P.take<int>(B);
             C.exptab = P.take<float>(128);
             C.fct_tw_df = P.take<float>(2 * (size_t)n);
         } else {
@@ -531,6 +532,11 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "smc_move: context not initialised");
     if (!c.fitted) return fail(ctx, SMC_ESTATE, "smc_move: the pCN-GM kernels need gm_fit or smc_set_mixture first");
     API_BEGIN
+    struct Lenient {   // proposals outside the mixed-precision field range are rejected, not fatal
+        Ctx& c;
+        explicit Lenient(Ctx& cc) : c(cc) { c.lenient = true; }
+        ~Lenient() { c.lenient = false; }
+    } lenient_guard(c);
     int* accn = c.icount;
     check(cudaMemsetAsync(accn, 0, sizeof(int), c.stream), "memset");
     const long long nc0 = c.nonconv;

@@ -113,6 +113,7 @@ struct Rhs {
 };
 Rhs shared_rhs(const Ctx& c);
 int solve_batch(Ctx& c, int count, const Rhs& R, double* W);   // W: the FP64 solutions (count x n x n)
+void launch_mark_out_of_range(Ctx& c, int count, double* Phi);
 void launch_observe(Ctx& c, const double* w, int count, double* Phi);
 void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w_out);
 void launch_move_tables(Ctx& c);
@@ -187,6 +188,8 @@ struct Ctx {
     smc_profile pc{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int* dev_err = nullptr;    // device flag set by kernels whose bounded waits time out
+    int* badp = nullptr;       // per batch particle: field outside the mixed-precision range
+    bool lenient = false;      // in a move: such proposals are rejected instead of failing the call
     int sm_count = 0;
     std::string err;
 };

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __res
                                                       ExpConsts ec, float* __restrict__ Kwh, float* __restrict__ Kwl,
                                                       float* __restrict__ Ksh, float* __restrict__ Ksl, float* __restrict__ Eh,
                                                       float* __restrict__ El, float* __restrict__ Nh, float* __restrict__ Nl,
-                                                      int* __restrict__ err) {
+                                                      int* __restrict__ err, int* __restrict__ badp) {
     __shared__ float2 tab[64];
     __shared__ float2 S[FY + 1][FX + 1];
     const int p = blockIdx.y;
@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __res
         }
         S[ly][lx] = v;
     }
-    if (bad) atomicExch(&err[1], 1);
+    if (bad) {
+        atomicExch(&err[1], 1);
+        badp[p] = 1;                          // the particle (batch index) whose field is out of range
+    }
     __syncthreads();
     const int lx = threadIdx.x % FX, ly = threadIdx.x / FX;
     const int i = tx * FX + lx, j = ty * FY + ly;
@@ -762,14 +765,14 @@ __global__ void k_fill_rhs(size_t nn, int count, const double* __restrict__ b, c
 }
 
 __global__ void k_outer(int mode, int count, int ntiles, SolverScalars sc, Partials part, double tol2, double b2const,
-                        const double* __restrict__ b2pp) {
+                        const double* __restrict__ b2pp, const int* __restrict__ badp) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= count) return;
-    if (mode == 0) {  // initial residual = b, |b|^2 known (per particle, or common)
+    if (mode == 0) {  // initial residual = b, |b|^2 known (per particle, or common); out-of-range fields are not solved
         const double s = b2pp ? b2pp[p] : b2const;
         sc.b2[p] = s;
         sc.res2[p] = s;
-        sc.act_out[p] = s > 0.0 ? 1 : 0;
+        sc.act_out[p] = (s > 0.0 && !(badp && badp[p])) ? 1 : 0;
         sc.iters[p] = 0;
         sc.flags[p] = 0;
         return;
@@ -970,7 +973,8 @@ static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
     check(cudaMemcpy(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
     if (err[0] || err[1]) check(cudaMemset(c.dev_err, 0, 2 * sizeof(int)), "err reset");   // the context stays usable
     if (err[0]) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
-    if (err[1]) throw InputError{"log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};
+    if (err[1] && !c.lenient)
+        throw InputError{"log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};
     return h[0];
 }
 
@@ -1233,9 +1237,10 @@ void launch_setup_coeffs(Ctx& c, int count) {
     const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
     if (mixed && n % FX == 0 && n % FY == 0) {
         LevelArrays<float>& f0 = c.s32.lv[0];
+        check(cudaMemsetAsync(c.badp, 0, count * sizeof(int), c.stream), "memset badp");
         k_faces_df<<<dim3((n / FX) * (n / FY), count), FX * FY, 0, c.stream>>>(
             n, reinterpret_cast<const float2*>(c.u64), reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
-            c.dev_err); ++c.pc.launches;
+            c.dev_err, c.badp); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
         return;
     }
@@ -1278,7 +1283,8 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
     c.pc.word_bytes = (int)sizeof(T);
     int outer_active = count;
     const int sgrid = (count + 127) / 128;
-    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp); ++c.pc.launches;
+    const int* badp = (mixed && c.lenient) ? c.badp : nullptr;
+    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp, badp); ++c.pc.launches;
     int itmax = 0;
     const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
     const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
@@ -1297,7 +1303,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
                                                        sc.act_out); ++c.pc.launches;
         }
         check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
-        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp); ++c.pc.launches;
+        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp, badp); ++c.pc.launches;
         int h = 0;
         check(cudaMemcpyAsync(&h, sc.count + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
         check(cudaStreamSynchronize(c.stream), "sync");
@@ -1309,6 +1315,18 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
 }
 
 Rhs shared_rhs(const Ctx& c) { return Rhs{c.b64, c.bdf, 0, nullptr, c.b2}; }
+
+// In a move (c.lenient) a proposal whose field is outside the mixed-precision
+// range is not solved; Phi = +inf makes the accept step reject it.
+__global__ void k_mark_out_of_range(int count, const int* __restrict__ badp, double* __restrict__ Phi) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < count && badp[p]) Phi[p] = 1.0 / 0.0;
+}
+
+void launch_mark_out_of_range(Ctx& c, int count, double* Phi) {
+    if (!c.lenient || !c.badp || c.cfg.precision != SMC_P_FP32_REFINE) return;
+    k_mark_out_of_range<<<(count + 127) / 128, 128, 0, c.stream>>>(count, c.badp, Phi); ++c.pc.launches;
+}
 
 int solve_batch(Ctx& c, int count, const Rhs& R, double* W) {
     return c.cfg.precision == SMC_P_FP32_REFINE ? solve_batch_t<float>(c, c.s32, count, R, W)
@@ -1333,6 +1351,7 @@ int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w
         int it = solve_batch(c, cnt, shared_rhs(c), c.w64);
         itmax = std::max(itmax, it);
         launch_observe(c, c.w64, cnt, Phi_out + off);
+        launch_mark_out_of_range(c, cnt, Phi_out + off);
         if (w_out) check(cudaMemcpyAsync(w_out + off * nn, c.w64, cnt * nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "w copy");
     }
     check(cudaGetLastError(), "forward");

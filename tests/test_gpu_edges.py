@@ -141,3 +141,36 @@ def test_out_of_range_field_fails_cleanly():
     ref = prob.potential(X[1])
     assert abs(F[1].item() - ref) <= 1e-10 * abs(ref)
     s.close()
+
+
+def test_move_rejects_out_of_range_proposal():
+    """In a move, a proposal whose field leaves the mixed-precision range is
+    rejected (Phi_v = +inf) instead of failing the call; the other particles
+    move exactly as the oracle's kernel."""
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 6
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, n_components=2, precision=smcgm.SMC_P_FP32_REFINE))
+    prob = oproblem.from_workload(wl)
+    X, Phi = s.particles()
+    X = X.copy()
+    Phi = Phi.copy()
+    X[2, 0] = 80.0                                    # constant mode: gamma * 80 + noise stays above 64
+    Phi[2] = 1e3                                      # any finite value (the field cannot be solved in FP32 + df32)
+    s.smc_set_particles(X, Phi)
+    mix = _random_mixture(s, np.random.default_rng(9), prob.lam)
+    t, beta, step = 0.05, 0.2, 3
+    s.smc_set_schedule(t, beta, 0, step)
+    s.smc_move(1)
+    X2, Phi2 = s.particles()
+    dg = s.diagnostics()
+    assert not dg["accepted"][2] and np.isinf(dg["phi_proposed"][2])
+    assert np.array_equal(X2[2], X[2]) and Phi2[2] == Phi[2]
+    for n in (0, 1, 3, 4, 5):
+        x, ph, acc, la, pv = osmc.move_particle(X[n], Phi[n], mix, beta, t, wl["seed"], n, step, prob.potential)
+        assert abs(dg["phi_proposed"][n] - pv) <= 1e-10 * abs(pv)
+        U = float(osmc.philox.uniforms(wl["seed"], 0, n, step, osmc.philox.ACCEPT))
+        if abs(np.log(U) - la) < NEAR_TIE:
+            continue
+        assert bool(dg["accepted"][n]) == bool(acc)
+        assert _rel(X2[n], x) < 1e-13
+    s.close()
