@@ -5,7 +5,7 @@
 //   2. adjoint right-hand side O^T (O w - d) / sigma^2, one thread per particle
 //      scattering its observation stencils in a fixed order (deterministic);
 //   3. adjoint solve A lam = that right-hand side with the same solver;
-//   4. dPhi/du per cell from w, lam, the faces and e^{-u} (k_grad_u);
+//   4. dPhi/du per cell from w, lam, the faces and e^{-u} (k_grad_u_df, k_grad_u64);
 //   5. dPhi/dx = S^T dPhi/du (launch_analysis2d, the transposed cosine transform).
 #include <algorithm>
 #include "smcgm_internal.cuh"
@@ -71,56 +71,16 @@ __global__ void __launch_bounds__(256) k_rhs_finish(int nn, int as_df32, double*
     if (threadIdx.x == 0) b2[p] = acc;
 }
 
-// Face coefficient and its derivative with respect to the cell's own log
-// permeability: harmonic face K^2 e^{-u} / 2, wall face K.
-struct FaceD {
-    double K, dK;
-};
-
-template <bool MIXED>
-struct GradSrc;
-
-template <>
-struct GradSrc<true> {   // df32 field and faces of the mixed-precision set-up
-    const float2* u;
-    const float *kwh, *kwl, *ksh, *ksl, *eh, *el, *nh, *nl;
-    const float2* tab;
-    ExpConsts ec;
-    __device__ df32 emu(size_t c) const {
-        const float2 v = u[c];
-        return df_exp(df32{-v.x, -v.y}, tab, ec);
-    }
-    __device__ static FaceD face(float kh, float kl, df32 e, bool wall) {
-        const df32 K{kh, kl};
-        if (wall) return FaceD{(double)kh + (double)kl, (double)kh + (double)kl};
-        const df32 d = df_mul(df_mul(K, K), e);
-        return FaceD{(double)kh + (double)kl, 0.5 * ((double)d.hi + (double)d.lo)};
-    }
-    __device__ FaceD west(size_t c, df32 e, bool wall) const { return face(kwh[c], kwl[c], e, wall); }
-    __device__ FaceD south(size_t c, df32 e, bool wall) const { return face(ksh[c], ksl[c], e, wall); }
-    __device__ FaceD east_wall(size_t r) const { return face(eh[r], el[r], df32{0.f, 0.f}, true); }
-    __device__ FaceD north_wall(size_t r) const { return face(nh[r], nl[r], df32{0.f, 0.f}, true); }
-};
-
-template <>
-struct GradSrc<false> {  // FP64 faces; the FP64 set-up leaves e^{-u} in the field's array (k_exp_neg)
-    const double* s;
-    const double *kw, *ks, *E, *N;
-    __device__ double emu(size_t c) const { return s[c]; }
-    __device__ static FaceD face(double K, double e, bool wall) { return FaceD{K, wall ? K : 0.5 * K * K * e}; }
-    __device__ FaceD west(size_t c, double e, bool wall) const { return face(kw[c], e, wall); }
-    __device__ FaceD south(size_t c, double e, bool wall) const { return face(ks[c], e, wall); }
-    __device__ FaceD east_wall(size_t r) const { return face(E[r], 0.0, true); }
-    __device__ FaceD north_wall(size_t r) const { return face(N[r], 0.0, true); }
-};
-
-// dPhi/du_c = -sum over the faces of cell c of (dK_f/du_c)(lam_c - lam_nb)(w_c - w_nb),
-// lam_nb = w_nb = 0 across a wall.  A 32 x 32 tile per block, 4 cells a thread;
-// the east / north face of a cell is its neighbour's west / south face, whose
-// derivative with respect to this cell takes this cell's e^{-u}.
-template <bool MIXED>
-__global__ void __launch_bounds__(256) k_grad_u(int n, GradSrc<MIXED> S, const double* __restrict__ w,
-                                                const double* __restrict__ lam, double* __restrict__ g) {
+// FP64 context: dPhi/du_c = -sum over the faces of cell c of
+// (dK_f/du_c)(lam_c - lam_nb)(w_c - w_nb), lam_nb = w_nb = 0 across a wall, with
+// dK_f/du_c = K_f^2 e^{-u_c} / 2 for a harmonic face and K_f for a wall face.
+// The FP64 set-up leaves e^{-u} in the field's array (k_exp_neg).  A 32 x 32
+// tile per block, 4 cells a thread; the east / north face of a cell is its
+// neighbour's west / south face.
+__global__ void __launch_bounds__(256) k_grad_u64(int n, const double* __restrict__ s, const double* __restrict__ kw,
+                                                  const double* __restrict__ ks, const double* __restrict__ E,
+                                                  const double* __restrict__ N, const double* __restrict__ w,
+                                                  const double* __restrict__ lam, double* __restrict__ g) {
     const int p = blockIdx.y;
     const int tpr = n / TILE;
     const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
@@ -129,26 +89,71 @@ __global__ void __launch_bounds__(256) k_grad_u(int n, GradSrc<MIXED> S, const d
     for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
         const int i = tx * TILE + li, j = ty * TILE + lj;
         const size_t c = base + (size_t)j * n + i;
-        const auto e = S.emu(c);
-        const double wc = w[c], lc = lam[c];
+        const double e = s[c], wc = w[c], lc = lam[c];
+        auto dk = [e](double K) { return 0.5 * K * K * e; };
         double acc = 0.0;
-        {   // west
-            const FaceD f = S.west(c, e, i == 0);
-            acc += f.dK * (i > 0 ? (lc - lam[c - 1]) * (wc - w[c - 1]) : lc * wc);
-        }
-        {   // east
-            const FaceD f = i + 1 < n ? S.west(c + 1, e, false) : S.east_wall((size_t)p * n + j);
-            acc += f.dK * (i + 1 < n ? (lc - lam[c + 1]) * (wc - w[c + 1]) : lc * wc);
-        }
-        {   // south
-            const FaceD f = S.south(c, e, j == 0);
-            acc += f.dK * (j > 0 ? (lc - lam[c - n]) * (wc - w[c - n]) : lc * wc);
-        }
-        {   // north
-            const FaceD f = j + 1 < n ? S.south(c + n, e, false) : S.north_wall((size_t)p * n + i);
-            acc += f.dK * (j + 1 < n ? (lc - lam[c + n]) * (wc - w[c + n]) : lc * wc);
-        }
+        acc += i > 0 ? dk(kw[c]) * (lc - lam[c - 1]) * (wc - w[c - 1]) : kw[c] * lc * wc;
+        acc += i + 1 < n ? dk(kw[c + 1]) * (lc - lam[c + 1]) * (wc - w[c + 1]) : E[(size_t)p * n + j] * lc * wc;
+        acc += j > 0 ? dk(ks[c]) * (lc - lam[c - n]) * (wc - w[c - n]) : ks[c] * lc * wc;
+        acc += j + 1 < n ? dk(ks[c + n]) * (lc - lam[c + n]) * (wc - w[c + n]) : N[(size_t)p * n + i] * lc * wc;
         g[c] = -acc;
+    }
+}
+
+// Mixed precision: the same gradient with the face terms formed once per face
+// and in df32.  For a harmonic face dK_f/du_c = K_f^2 e^{-u_c} / 2, and for a
+// wall face K_f = 2 k_c gives K_f = K_f^2 e^{-u_c} / 2 as well, so
+//   dPhi/du_c = -e^{-u_c} sum over the faces of c of P_f,
+//   P_f = K_f^2 (lam_a - lam_b)(w_a - w_b) / 2   (lam_b = w_b = 0 across a wall),
+// symmetric in the face's two cells.  A 32 x 32 tile puts the west and south
+// P of its cells (and those of the next column and row) in shared memory; the
+// differences use the FP64 unit once per face (exact for neighbours), the rest
+// runs in df32 on the FP32 pipes.
+__global__ void __launch_bounds__(256) k_grad_u_df(int n, const float2* __restrict__ u, const float* __restrict__ Kwh,
+                                                   const float* __restrict__ Kwl, const float* __restrict__ Ksh,
+                                                   const float* __restrict__ Ksl, const float* __restrict__ Eh,
+                                                   const float* __restrict__ El, const float* __restrict__ Nh,
+                                                   const float* __restrict__ Nl, const float2* __restrict__ exptab, ExpConsts ec,
+                                                   const double* __restrict__ w, const double* __restrict__ lam, double* __restrict__ g) {
+    __shared__ float2 tab[64];
+    __shared__ float2 PW[TILE][TILE + 1];
+    __shared__ float2 PS[TILE + 1][TILE];
+    const int p = blockIdx.y;
+    const int tpr = n / TILE;
+    const int tx = blockIdx.x % tpr, ty = blockIdx.x / tpr;
+    const int x0 = tx * TILE, y0 = ty * TILE;
+    const size_t nn = (size_t)n * n, base = (size_t)p * nn;
+    const double* wp = w + base;
+    const double* lp = lam + base;
+    const int li = threadIdx.x % TILE, lj0 = threadIdx.x / TILE;
+    if (threadIdx.x < 64) tab[threadIdx.x] = exptab[threadIdx.x];
+    auto P = [](float kh, float kl, double dl, double dw) {
+        const df32 K{kh, kl};
+        const df32 r = df_mul(df_mul(K, K), df_mul(df_from_double_bits(dl), df_from_double_bits(dw)));
+        return make_float2(0.5f * r.hi, 0.5f * r.lo);
+    };
+    for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
+        const int i = x0 + li, j = y0 + lj;
+        const size_t c = base + (size_t)j * n + i;
+        const size_t cl = c - base;
+        const double wc = wp[cl], lc = lp[cl];
+        PW[lj][li] = i > 0 ? P(Kwh[c], Kwl[c], lc - lp[cl - 1], wc - wp[cl - 1]) : P(Kwh[c], Kwl[c], lc, wc);
+        PS[lj][li] = j > 0 ? P(Ksh[c], Ksl[c], lc - lp[cl - n], wc - wp[cl - n]) : P(Ksh[c], Ksl[c], lc, wc);
+        if (li == TILE - 1)
+            PW[lj][TILE] = i + 1 < n ? P(Kwh[c + 1], Kwl[c + 1], lp[cl + 1] - lc, wp[cl + 1] - wc)
+                                     : P(Eh[(size_t)p * n + j], El[(size_t)p * n + j], lc, wc);
+        if (lj == TILE - 1)
+            PS[TILE][li] = j + 1 < n ? P(Ksh[c + n], Ksl[c + n], lp[cl + n] - lc, wp[cl + n] - wc)
+                                     : P(Nh[(size_t)p * n + i], Nl[(size_t)p * n + i], lc, wc);
+    }
+    __syncthreads();
+    for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
+        const size_t c = base + (size_t)(y0 + lj) * n + x0 + li;
+        const float2 a = PW[lj][li], b = PW[lj][li + 1], d = PS[lj][li], e = PS[lj + 1][li];
+        const df32 sum = df_add(df_add(df32{a.x, a.y}, df32{b.x, b.y}), df_add(df32{d.x, d.y}, df32{e.x, e.y}));
+        const float2 uv = u[c];
+        const df32 r = df_mul(df_exp(df32{-uv.x, -uv.y}, tab, ec), sum);
+        g[c] = -((double)r.hi + (double)r.lo);
     }
 }
 
@@ -178,12 +183,11 @@ int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* 
         const dim3 grid((n / TILE) * (n / TILE), cnt);
         if (mixed) {
             LevelArrays<float>& f0 = c.s32.lv[0];
-            GradSrc<true> S{reinterpret_cast<const float2*>(c.u64), f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
-                            reinterpret_cast<const float2*>(c.exptab), c.expc};
-            k_grad_u<true><<<grid, 256, 0, c.stream>>>(n, S, c.w64, c.lam64, c.rhs); ++c.pc.launches;
+            k_grad_u_df<<<grid, 256, 0, c.stream>>>(n, reinterpret_cast<const float2*>(c.u64), f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E,
+                                                    c.Elo, f0.Nn, c.Nlo, reinterpret_cast<const float2*>(c.exptab), c.expc, c.w64,
+                                                    c.lam64, c.rhs); ++c.pc.launches;
         } else {
-            GradSrc<false> S{c.u64, c.Kw64, c.Ks64, c.E64, c.N64};
-            k_grad_u<false><<<grid, 256, 0, c.stream>>>(n, S, c.w64, c.lam64, c.rhs); ++c.pc.launches;
+            k_grad_u64<<<grid, 256, 0, c.stream>>>(n, c.u64, c.Kw64, c.Ks64, c.E64, c.N64, c.w64, c.lam64, c.rhs); ++c.pc.launches;
         }
         // 5. dPhi/dx
         launch_analysis2d(c, c.rhs, cnt, grad_out + (size_t)off * c.d);
