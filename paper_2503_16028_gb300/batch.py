@@ -1,0 +1,106 @@
+"""Many independent inverse problems on one GPU, and a solver-setting autotuner.
+
+Batching: one context and one CUDA stream per problem, each driven by its own
+host thread.  The library's calls release the GIL (ctypes) and synchronise
+only their own stream, so while one problem's host thread waits on its
+convergence checks the other problems' kernels run; small problems (64^2,
+a few hundred particles) that cannot fill 152 SMs alone overlap on the GPU.
+A problem's result does not depend on the others (its kernels touch only its
+own workspace, and its random numbers are its own Philox streams).
+
+Autotuning: the multigrid smoothing counts, the coarse-correction factor and
+the inner tolerance are run-time settings (`smc_config`); `autotune` times
+`smc_move` for each candidate on the problem itself and keeps the fastest.
+Every candidate meets the same FP64 tolerance, so the choice changes speed,
+not the answer beyond that tolerance.
+"""
+import concurrent.futures as cf
+import time
+
+import numpy as np
+
+from . import smcgm
+
+
+def run_smc(sampler, mcmc_steps, max_layers=200):
+    """Alg. 1 on one context until t = 1: reweight (ESS bisection), resample,
+    fit the mixture, move.  Returns the per-layer (h, ess, log Z increment,
+    acceptance) and the final particles."""
+    layers = []
+    for _ in range(max_layers):
+        h, ess, lz, done = sampler.smc_temper_step()
+        sampler.smc_resample()
+        sampler.gm_fit()
+        acc, _ = sampler.smc_move(mcmc_steps, allow_noconv=True)
+        layers.append(dict(h=h, ess=ess, logz=lz, acc=acc))
+        if done:
+            break
+    X, Phi = sampler.particles()
+    return dict(layers=layers, X=X, Phi=Phi)
+
+
+def make_samplers(configs, device="cuda:0"):
+    """One Sampler per smc_config, each on a new CUDA stream of its own."""
+    import torch
+    out = []
+    for cfg in configs:
+        stream = torch.cuda.Stream(device=device)
+        out.append(smcgm.Sampler(cfg, device=device, stream=stream))
+    return out
+
+
+def run_batch(samplers, mcmc_steps, max_layers=200, concurrent=True):
+    """run_smc on every sampler, concurrently (a thread per problem) or one by
+    one.  Returns (results, seconds)."""
+    steps = mcmc_steps if isinstance(mcmc_steps, (list, tuple)) else [mcmc_steps] * len(samplers)
+    t0 = time.perf_counter()
+    if concurrent:
+        with cf.ThreadPoolExecutor(max_workers=len(samplers)) as ex:
+            futs = [ex.submit(run_smc, s, k, max_layers) for s, k in zip(samplers, steps)]
+            results = [f.result() for f in futs]
+    else:
+        results = [run_smc(s, k, max_layers) for s, k in zip(samplers, steps)]
+    return results, time.perf_counter() - t0
+
+
+DEFAULT_CANDIDATES = (
+    dict(),                                            # the library defaults
+    dict(smooth_sweeps=1),
+    dict(fine_sweeps=2),
+    dict(tol_inner=2e-4),
+    dict(tol_inner=1e-3),
+    dict(coarse_scale=1.8),
+)
+
+
+def pick_fastest(timings):
+    """The candidate with the smallest time (ties: the earlier candidate)."""
+    best = min(range(len(timings)), key=lambda i: (timings[i][1], i))
+    return timings[best][0]
+
+
+def autotune(preset, candidates=DEFAULT_CANDIDATES, n_particles=None, steps=2, reps=2, **overrides):
+    """Time `steps` moves for each candidate solver setting on `preset`
+    (a workload dict) and return (best overrides, [(candidate, ms per move)])."""
+    import torch
+    timings = []
+    for cand in candidates:
+        kw = dict(overrides)
+        kw.update(cand)
+        if n_particles:
+            kw["n_particles"] = n_particles
+        s = smcgm.Sampler(smcgm.make_config(preset, **kw))
+        s.smc_temper_step()
+        s.smc_resample()
+        s.gm_fit()
+        s.smc_move(1, allow_noconv=True)                     # warm-up
+        best = np.inf
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.smc_move(steps, allow_noconv=True)
+            torch.cuda.synchronize()
+            best = min(best, (time.perf_counter() - t0) * 1e3 / steps)
+        s.close()
+        timings.append((cand, best))
+    return pick_fastest(timings), timings
