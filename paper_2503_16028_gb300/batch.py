@@ -104,3 +104,22 @@ def autotune(preset, candidates=DEFAULT_CANDIDATES, n_particles=None, steps=2, r
         s.close()
         timings.append((cand, best))
     return pick_fastest(timings), timings
+
+
+def mesh_sweep(preset, grids, n_particles, kl_modes, mcmc_steps, max_layers=200, concurrent=True, **overrides):
+    """The same prior (kl_modes^2 cosine modes), data and random streams solved on
+    each grid of `grids`; returns {n: cumulative temperatures per layer} (the mesh
+    independence of the tempering schedule, Sec. 3.2).  The grids run as a batch."""
+    configs = [smcgm.make_config(preset, n=n, kl_modes=kl_modes, n_particles=n_particles, **overrides) for n in grids]
+    samplers = make_samplers(configs)
+    results, seconds = run_batch(samplers, mcmc_steps, max_layers, concurrent=concurrent)
+    out = {}
+    for n, res in zip(grids, results):
+        t, ts = 0.0, []
+        for lay in res["layers"]:
+            t = min(1.0, t + lay["h"])
+            ts.append(t)
+        out[n] = ts
+    for s in samplers:
+        s.close()
+    return out, seconds

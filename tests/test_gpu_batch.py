@@ -43,3 +43,17 @@ def test_autotune_returns_a_candidate():
     best, timings = batch.autotune(wl, candidates=cands, n_particles=64, steps=1, reps=1, n_components=2, em_iters=5)
     assert best in cands
     assert len(timings) == 2 and all(t > 0 for _, t in timings)
+
+
+def test_mesh_independence_of_the_tempering_schedule():
+    """Sec. 3.2 (mesh independence): the same prior, data and random streams on
+    64^2 and 128^2 grids give the same number of layers and nearly the same
+    temperatures (they differ only through the discretisation of Phi)."""
+    wl = inputs.load_workload("darcy256_precision")
+    temps, _ = batch.mesh_sweep(wl, [64, 128], n_particles=1024, kl_modes=32, mcmc_steps=10, max_layers=60,
+                                n_components=8, em_iters=30)
+    a, b = temps[64], temps[128]
+    assert a[-1] == 1.0 and b[-1] == 1.0
+    assert abs(len(a) - len(b)) <= 2, (len(a), len(b))
+    for ta, tb in zip(a[:-3], b[:-3]):
+        assert abs(ta - tb) <= 0.25 * max(ta, tb) + 1e-3, (a, b)
