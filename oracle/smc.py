@@ -104,14 +104,19 @@ def prior_draw(seed, lam, n):
     return np.sqrt(lam) * philox.normals(seed, lam.shape[0], n, 0, philox.INIT)
 
 
-def move_particle(x, phi_x, mix, beta, t, seed, n, step, forward):
-    """One pCN-GM step (Alg. 2) for particle n; returns (x', phi', accepted, log_alpha, phi_v)."""
+def move_particle(x, phi_x, mix, beta, t, seed, n, step, forward, always_accept=False):
+    """One pCN-GM step (Alg. 2) for particle n; returns (x', phi', accepted, log_alpha, phi_v).
+
+    always_accept: the SMC-GM mutation of Alg. 3 (beta = 1, a = 1): the
+    mixture proposal is taken as the new state."""
     d = x.shape[0]
     Uc = float(philox.uniforms(seed, 0, n, step, philox.COMP))
     j = pcngm.choose_component(mix.w, Uc)
     z = philox.normals(seed, d, n, step, philox.NORMAL)
     v = pcngm.propose(x, j, z, mix, beta)
     phi_v = forward(v)
+    if always_accept:
+        return v, phi_v, True, 0.0, phi_v
     lr = pcngm.log_mixture_ratio(x, v, mix, beta)
     la = pcngm.log_alpha(t, phi_x, phi_v, lr)
     Ua = float(philox.uniforms(seed, 0, n, step, philox.ACCEPT))
@@ -120,7 +125,7 @@ def move_particle(x, phi_x, mix, beta, t, seed, n, step, forward):
     return x, phi_x, False, la, phi_v
 
 
-def move(X, Phi, mix, beta, t, seed, step0, steps, forward, particles=None):
+def move(X, Phi, mix, beta, t, seed, step0, steps, forward, particles=None, always_accept=False):
     """`steps` pCN-GM steps for every particle (or the listed subset).
 
     Step s uses the Philox step counter step0 + s.  Returns new (X, Phi),
@@ -135,7 +140,7 @@ def move(X, Phi, mix, beta, t, seed, step0, steps, forward, particles=None):
     for s in range(steps):
         for n in ids:
             X[n], Phi[n], acc[s, n], la[s, n], pv[s, n] = move_particle(
-                X[n], Phi[n], mix, beta, t, seed, n, step0 + s, forward)
+                X[n], Phi[n], mix, beta, t, seed, n, step0 + s, forward, always_accept)
     return X, Phi, acc, la, pv
 
 
@@ -147,7 +152,8 @@ def posterior_moments(X):
 
 def run(problem, N, K, r, L, beta0, ess_frac, seed, em_iters=50, kernel="pcn_gm",
         max_layers=1000, record=None):
-    """Whole SMC-pCN-GM run (Alg. 1 with Alg. 2 as mutation).  kernel: 'pcn_gm' or 'pcn'.
+    """Whole SMC-pCN-GM run (Alg. 1 with Alg. 2 as mutation).  kernel: 'pcn_gm', 'pcn', or
+    'gm_indep' (SMC-GM, Alg. 3: beta = 1 and every mixture proposal accepted).
 
     Returns a dict with the final particles, potentials, temperatures and per-layer records.
     """
@@ -156,7 +162,8 @@ def run(problem, N, K, r, L, beta0, ess_frac, seed, em_iters=50, kernel="pcn_gm"
     S = problem.gm_modes(r)
     X = np.stack([prior_draw(seed, lam, n) for n in range(N)])
     Phi = np.array([problem.potential(x) for x in X])
-    t, beta, layer, step, logZ = 0.0, float(beta0), 0, 0, 0.0
+    indep = kernel == "gm_indep"
+    t, beta, layer, step, logZ = 0.0, 1.0 if indep else float(beta0), 0, 0, 0.0
     layers = []
     while t < 1.0 and layer < max_layers:
         h = bisect_h(Phi, t, ess_frac * N)
@@ -169,11 +176,12 @@ def run(problem, N, K, r, L, beta0, ess_frac, seed, em_iters=50, kernel="pcn_gm"
             mix = pcngm.Mixture.prior(lam, S, 1)
         else:
             mix, _ = gm.fit(X, S, lam, K, em_iters, seed, layer)
-        X, Phi, acc, _, _ = move(X, Phi, mix, beta, t, seed, step, L, problem.potential)
+        X, Phi, acc, _, _ = move(X, Phi, mix, beta, t, seed, step, L, problem.potential, always_accept=indep)
         step += L
         rate = float(np.mean(acc))
         layers.append(dict(h=h, t=t, beta=beta, acc=rate, logZ=logZ))
-        beta = beta_rule(beta, rate)
+        if not indep:
+            beta = beta_rule(beta, rate)
         layer += 1
         if record is not None:
             record(layer, X, Phi, mix)

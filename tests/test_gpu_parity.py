@@ -195,6 +195,31 @@ def test_elliptic_1d_full_run_matches_oracle():
     s.close()
 
 
+def test_elliptic_1d_smc_gm_full_run_matches_oracle():
+    """SMC-GM (Alg. 3, SMC_K_GM_INDEP: beta = 1, every mixture draw accepted) end
+    to end on the config-1 workload against the oracle's SMC-GM run."""
+    wl = inputs.load_workload("elliptic1d_n128")
+    N = 64
+    cfg = smcgm.make_config(wl, n_particles=N, em_iters=20, kernel=smcgm.SMC_K_GM_INDEP)
+    s = smcgm.Sampler(cfg)
+    prob = oproblem.from_workload(wl)
+    ref = osmc.run(prob, N=N, K=cfg.n_components, r=cfg.gm_rank, L=wl["mcmc_steps"], beta0=wl["beta0"],
+                   ess_frac=wl["ess_frac"], seed=wl["seed"], em_iters=20, max_layers=8, kernel="gm_indep")
+    for lay in ref["layers"]:
+        h, ess, lz, done = s.smc_temper_step()
+        assert abs(h - lay["h"]) <= 1e-9 * lay["h"]
+        s.smc_resample()
+        s.gm_fit()
+        acc, _ = s.smc_move(wl["mcmc_steps"])
+        assert acc == 1.0 and lay["acc"] == 1.0
+        if done:
+            break
+    X, Phi = s.particles()
+    assert _rel(X, ref["X"]) < 1e-10
+    assert _rel(Phi, ref["Phi"]) < 1e-10
+    s.close()
+
+
 def test_checkpoint_roundtrip():
     wl, cfg, s = _sampler("darcy64_bimodal", n_particles=16)
     s.smc_set_schedule(0.2, 0.4, 2, 30)

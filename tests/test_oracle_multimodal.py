@@ -73,3 +73,21 @@ def test_smc_pcn_gm_recovers_the_four_modes():
     for i in range(4):
         mi = X[lab == i].mean(axis=0)
         assert np.max(np.abs(mi - means[i])) < 0.03, (i, mi[:4], means[i][:4])   # measured <= 0.01
+
+
+def test_smc_gm_finds_the_four_modes():
+    """SMC-GM (Alg. 3: every particle redrawn from the fitted mixture), the method
+    the paper runs on this example.  Alg. 3 does not preserve the layer targets
+    (Thm 4 bounds the extra error instead), so the modal weights are not
+    reproduced (measured: 0.17 / 0.38 / 0.39 / 0.05 against 0.31 / 0.31 / 0.24 / 0.15),
+    nor the means of the small modes; every mode must still carry mass."""
+    prob = Ex1()
+    w, means = prob.posterior()
+    N = 2000
+    out = smc.run(prob, N=N, K=8, r=KM, L=1, beta0=1.0, ess_frac=0.5, seed=32, em_iters=50, kernel="gm_indep")
+    assert out["t"] == 1.0
+    assert all(lay["acc"] == 1.0 and lay["beta"] == 1.0 for lay in out["layers"])
+    X = out["X"]
+    lab = np.argmin(np.stack([np.sum((X - m) ** 2, axis=1) for m in means], axis=1), axis=1)
+    frac = np.bincount(lab, minlength=4) / N
+    assert np.all(frac > 0.02), frac
