@@ -81,3 +81,57 @@ def fit(X, S, lam0, K, iters, seed, layer, var_floor=1e-3):
     g, ll = e_step(xs, w, m, lam)
     hist.append(ll)
     return Mixture(S, w, m, lam, lam0), hist
+
+
+def e_step_full(xs, w, m, cov):
+    """E-step with full covariances: log p_nj = log w_j + log N(x_n; m_j, C_j)."""
+    N, r = xs.shape
+    K = w.shape[0]
+    logp = np.empty((N, K))
+    for j in range(K):
+        _, logdet = np.linalg.slogdet(cov[j])
+        dev = xs - m[j]
+        q = np.sum(dev * np.linalg.solve(cov[j], dev.T).T, axis=1)
+        logp[:, j] = np.log(w[j]) - 0.5 * (r * np.log(2.0 * np.pi) + logdet) - 0.5 * q
+    mx = np.max(logp, axis=1, keepdims=True)
+    lse = mx[:, 0] + np.log(np.sum(np.exp(logp - mx), axis=1))
+    return np.exp(logp - lse[:, None]), float(np.sum(lse))
+
+
+def fit_full(X, S, lam0, K, iters, seed, layer, var_floor=1e-3):
+    """EM with full covariances on X[:, S] (a reading beyond the paper, whose C_j
+    are diagonal in the KL basis): the steps of ``fit`` with
+    C_j = sum_n g_nj (x_n - m_j)(x_n - m_j)^T / N_j + floor * diag(lambda_S)
+    (a ridge keeps C_j positive definite), initial and re-seeded covariances
+    diag(pooled variances).  Returns (Mixture with cov, loglik history)."""
+    X = np.asarray(X, dtype=np.float64)
+    N = X.shape[0]
+    xs = X[:, S]
+    lamS = np.asarray(lam0)[S]
+    pooled_mean = np.mean(xs, axis=0)
+    pooled = np.maximum(np.mean((xs - pooled_mean) ** 2, axis=0), var_floor * lamS)
+    idx = init_indices(seed, layer, N, K)
+    w = np.full(K, 1.0 / K)
+    m = xs[idx].copy()
+    cov = np.stack([np.diag(pooled) for _ in range(K)])
+    hist = []
+    for _ in range(iters):
+        g, ll = e_step_full(xs, w, m, cov)
+        hist.append(ll)
+        Nj = np.sum(g, axis=0)
+        for j in range(K):
+            if Nj[j] < 2.0:
+                n_star = int(np.argmin(np.max(g, axis=1)))
+                m[j] = xs[n_star]
+                cov[j] = np.diag(pooled)
+                w[j] = 1.0 / N
+                continue
+            w[j] = Nj[j] / N
+            m[j] = np.sum(g[:, j:j + 1] * xs, axis=0) / Nj[j]
+            dev = xs - m[j]
+            cov[j] = (g[:, j:j + 1] * dev).T @ dev / Nj[j] + np.diag(var_floor * lamS)
+        w = w / np.sum(w)
+    g, ll = e_step_full(xs, w, m, cov)
+    hist.append(ll)
+    lam = np.stack([np.diag(c) for c in cov])
+    return Mixture(S, w, m, lam, lam0, cov=cov), hist

@@ -52,12 +52,14 @@ class Mixture:
     lam0   : (d,) prior eigenvalues lambda_i
     """
 
-    def __init__(self, S, w, m, lam, lam0):
+    def __init__(self, S, w, m, lam, lam0, cov=None):
         self.S = np.asarray(S, dtype=np.int64)
         self.w = np.asarray(w, dtype=np.float64)
         self.m = np.asarray(m, dtype=np.float64)
         self.lam = np.asarray(lam, dtype=np.float64)
         self.lam0 = np.asarray(lam0, dtype=np.float64)
+        # full covariances (K, r, r) on S, or None for the diagonal lambda_j of Sec. 2.3
+        self.cov = None if cov is None else np.asarray(cov, dtype=np.float64)
 
     @property
     def K(self):
@@ -71,7 +73,8 @@ class Mixture:
                        np.tile(np.asarray(lam0)[S], (K, 1)), lam0)
 
     def copy(self):
-        return Mixture(self.S.copy(), self.w.copy(), self.m.copy(), self.lam.copy(), self.lam0.copy())
+        return Mixture(self.S.copy(), self.w.copy(), self.m.copy(), self.lam.copy(), self.lam0.copy(),
+                       None if self.cov is None else self.cov.copy())
 
 
 def choose_component(w, U):
@@ -85,10 +88,15 @@ def choose_component(w, U):
 
 
 def propose(u, j, z, mix, beta):
-    """v = gamma u + (1 - gamma) m_j + beta sqrt(lambda_j) z  (eq. pCN-GM proposal)."""
+    """v = gamma u + (1 - gamma) m_j + beta sqrt(lambda_j) z  (eq. pCN-GM proposal);
+    with full covariances, beta L_j z_S on S, C_j = L_j L_j^T (Cholesky)."""
     g = gamma_of(beta)
     v = g * u + beta * np.sqrt(mix.lam0) * z
     S = mix.S
+    if mix.cov is not None:
+        L = np.linalg.cholesky(mix.cov[j])
+        v[S] = g * u[S] + (1.0 - g) * mix.m[j] + beta * (L @ z[S])
+        return v
     v[S] = g * u[S] + (1.0 - g) * mix.m[j] + beta * np.sqrt(mix.lam[j]) * z[S]
     return v
 
@@ -100,6 +108,15 @@ def log_r(b, a, mix, beta):
     e = b[S] - g * a[S]
     l0 = mix.lam0[S]
     out = np.empty(mix.K)
+    if mix.cov is not None:
+        # log N(e; (1-gamma) m_j, beta^2 C_j) - log N(e; 0, beta^2 diag(lambda_S)), written out
+        for j in range(mix.K):
+            C = beta * beta * mix.cov[j]
+            dev = e - (1.0 - g) * mix.m[j]
+            _, logdet = np.linalg.slogdet(C)
+            out[j] = (-0.5 * logdet - 0.5 * dev @ np.linalg.solve(C, dev)
+                      + 0.5 * np.sum(np.log(beta * beta * l0)) + np.sum(e * e / (2.0 * beta * beta * l0)))
+        return out
     for j in range(mix.K):
         lj = mix.lam[j]
         out[j] = np.sum(0.5 * np.log(l0 / lj)
