@@ -110,6 +110,9 @@ typedef struct smc_config {
     unsigned long long seed;
     int gradient;       /* 1: also lay out the arrays of smc_gradient (2D only; two more
                            solution-sized FP64 arrays per batch particle); 0: no gradients */
+    int full_cov;       /* 1: mixture components with full r x r covariances on the mixture
+                           modes (EM with the ridge var_floor * diag(lambda_S)); 0: diagonal
+                           lambda_j as in Sec. 2.3.  pCN-GM and independence kernels only */
 } smc_config;
 
 /* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */
@@ -177,6 +180,18 @@ smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi
  * synthesis applied to it.  The drift of the Langevin equation of App. B.
  * Needs cfg.gradient = 1 and dim = 2 (else SMC_ESTATE / SMC_EINVAL). */
 smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_grad);
+
+/* Full-covariance mixtures (cfg.full_cov = 1): set or read the components'
+ * r x r covariances C_j on the mixture modes (host, K x r x r, row-major,
+ * symmetric positive definite; w and m as in smc_set_mixture).  The library
+ * keeps C_j = L_j L_j^T, L_j^{-1} and log det L_j; the pCN-GM proposal draws
+ * beta L_j z on the mixture modes and the acceptance ratio uses
+ * N(e; (1-gamma) m_j, beta^2 C_j) / N(e; 0, beta^2 diag(lambda)).  gm_fit
+ * then fits full covariances (EM, ridge var_floor * diag(lambda)).
+ * SMC_ESTATE without cfg.full_cov; SMC_EINVAL for a C_j that is not positive
+ * definite. */
+smc_status smc_set_mixture_cov(smc_ctx* ctx, const double* w, const double* m, const double* cov);
+smc_status smc_get_mixture_cov(smc_ctx* ctx, double* cov);
 
 /* Device views of the particle state (borrowed; valid until the next call). */
 smc_status smc_get_particles(smc_ctx* ctx, const double** d_X, const double** d_Phi);

@@ -64,6 +64,10 @@ static const char* validate(const smc_config& c) {
     if (!(c.coarse_scale > 0 && c.coarse_scale <= 2.5)) return "coarse_scale must be in (0, 2.5]";
     if (c.solve_batch < 0) return "solve_batch must be >= 0";
     if (c.gradient != 0 && c.gradient != 1) return "gradient must be 0 or 1";
+    if (c.full_cov != 0 && c.full_cov != 1) return "full_cov must be 0 or 1";
+    if (c.full_cov && c.kernel != SMC_K_PCN_GM && c.kernel != SMC_K_GM_INDEP)
+        return "full_cov needs the pCN-GM or the mixture independence kernel";
+    if (c.full_cov && !(c.var_floor > 0)) return "full_cov needs var_floor > 0 (the covariance ridge)";
     if (c.gradient && c.dim != 2) return "gradients are built for dim = 2 only";
     for (int i = 0; i < c.n_obs * c.dim; ++i)
         if (!(c.obs[i] > 0.0 && c.obs[i] < 1.0)) return "observation points must lie inside the domain";
@@ -126,6 +130,10 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     C.icount = P.take<int>(64); C.dscal = P.take<double>(64); C.dev_err = P.take<int>(4);
     C.normtab = P.take<float>(2 * NORMAL_TAB);
     C.gw = P.take<double>(K); C.gmu = P.take<double>((size_t)K * r); C.glam = P.take<double>((size_t)K * r);
+    if (cfg.full_cov) {
+        C.gcov = P.take<double>((size_t)K * r * r); C.gL = P.take<double>((size_t)K * r * r);
+        C.gLi = P.take<double>((size_t)K * r * r); C.glogdet = P.take<double>(K);
+    }
     C.tab = P.take<double>(4 * (size_t)K * r + r + 2 * K);
     C.xsT = P.take<double>((size_t)r * N); C.resp = P.take<double>((size_t)K * N); C.nj = P.take<double>(K);
     C.pooled = P.take<double>(2 * (size_t)r); C.lse = P.take<double>(N); C.gmax = P.take<double>(N);
@@ -566,7 +574,8 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
     } else {
         launch_move_tables(c);
         for (int s = 0; s < steps; ++s) {
-            launch_propose(c);
+            if (c.cfg.full_cov) launch_propose_full(c);
+            else launch_propose(c);
             itmax = std::max(itmax, forward_solve(c, c.V, c.N, c.PhiV, nullptr));
             launch_accept(c, accn);
             ++c.step;
@@ -704,8 +713,44 @@ smc_status smc_set_mixture(smc_ctx* ctx, const double* w, const double* m, const
     check(cudaMemcpyAsync(c.gw, w, c.K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "w");
     check(cudaMemcpyAsync(c.gmu, m, (size_t)c.K * c.r * sizeof(double), cudaMemcpyHostToDevice, c.stream), "m");
     check(cudaMemcpyAsync(c.glam, lam, (size_t)c.K * c.r * sizeof(double), cudaMemcpyHostToDevice, c.stream), "lam");
+    if (c.cfg.full_cov) {                                  // diagonal covariances in the full form
+        std::vector<double> cov((size_t)c.K * c.r * c.r, 0.0);
+        for (int j = 0; j < c.K; ++j)
+            for (int a = 0; a < c.r; ++a) cov[((size_t)j * c.r + a) * c.r + a] = lam[(size_t)j * c.r + a];
+        factor_mixture(c, cov.data());
+    }
     check(cudaStreamSynchronize(c.stream), "sync");
     c.fitted = true;
+    return SMC_OK;
+    API_END(ctx)
+}
+
+smc_status smc_set_mixture_cov(smc_ctx* ctx, const double* w, const double* m, const double* cov) {
+    if (!ctx || !w || !m || !cov) return SMC_EINVAL;
+    Ctx& c = ctx->c;
+    if (!c.cfg.full_cov) return fail(ctx, SMC_ESTATE, "smc_set_mixture_cov: the context was set up without cfg.full_cov = 1");
+    for (int j = 0; j < c.K; ++j) if (!(w[j] > 0.0)) return fail(ctx, SMC_EINVAL, "mixture weights must be > 0");
+    API_BEGIN
+    const size_t Kr = (size_t)c.K * c.r;
+    std::vector<double> lam(Kr);
+    for (size_t t = 0; t < Kr; ++t) lam[t] = cov[(t / c.r * c.r + t % c.r) * c.r + t % c.r];
+    factor_mixture(c, cov);                                // fails for a covariance that is not positive definite
+    check(cudaMemcpyAsync(c.gw, w, c.K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "w");
+    check(cudaMemcpyAsync(c.gmu, m, Kr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "m");
+    check(cudaMemcpyAsync(c.glam, lam.data(), Kr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "lam");
+    check(cudaStreamSynchronize(c.stream), "sync");
+    c.fitted = true;
+    return SMC_OK;
+    API_END(ctx)
+}
+
+smc_status smc_get_mixture_cov(smc_ctx* ctx, double* cov) {
+    if (!ctx || !cov) return SMC_EINVAL;
+    Ctx& c = ctx->c;
+    if (!c.cfg.full_cov) return fail(ctx, SMC_ESTATE, "smc_get_mixture_cov: the context was set up without cfg.full_cov = 1");
+    API_BEGIN
+    check(cudaMemcpyAsync(cov, c.gcov, (size_t)c.K * c.r * c.r * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "cov");
+    check(cudaStreamSynchronize(c.stream), "sync");
     return SMC_OK;
     API_END(ctx)
 }
@@ -745,7 +790,8 @@ struct SaveHeader {
 smc_status smc_save(smc_ctx* ctx, void* host_buf, size_t* bytes) {
     if (!ctx || !bytes) return SMC_EINVAL;
     Ctx& c = ctx->c;
-    const size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)c.N * c.d + c.N + c.K + 2 * (size_t)c.K * c.r);
+    const size_t covn = c.cfg.full_cov ? (size_t)c.K * c.r * c.r : 0;
+    const size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)c.N * c.d + c.N + c.K + 2 * (size_t)c.K * c.r + covn);
     if (!host_buf) { *bytes = need; return SMC_OK; }
     if (*bytes < need) return fail(ctx, SMC_EINVAL, "smc_save: buffer too small");
     API_BEGIN
@@ -765,6 +811,8 @@ smc_status smc_save(smc_ctx* ctx, void* host_buf, size_t* bytes) {
     check(cudaMemcpyAsync(q, c.gmu, (size_t)c.K * c.r * 8, cudaMemcpyDeviceToHost, c.stream), "save");
     q += (size_t)c.K * c.r;
     check(cudaMemcpyAsync(q, c.glam, (size_t)c.K * c.r * 8, cudaMemcpyDeviceToHost, c.stream), "save");
+    q += (size_t)c.K * c.r;
+    if (covn) check(cudaMemcpyAsync(q, c.gcov, covn * 8, cudaMemcpyDeviceToHost, c.stream), "save");
     check(cudaStreamSynchronize(c.stream), "sync");
     *bytes = need;
     return SMC_OK;
@@ -778,7 +826,8 @@ smc_status smc_load(smc_ctx* ctx, const void* host_buf, size_t bytes) {
     std::memcpy(&h, host_buf, sizeof(h));
     if (std::memcmp(h.magic, "SMCGMv1", 8) != 0 || h.N != c.N || h.d != c.d || h.K != c.K || h.r != c.r)
         return fail(ctx, SMC_EINVAL, "smc_load: checkpoint does not match this configuration");
-    const size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)c.N * c.d + c.N + c.K + 2 * (size_t)c.K * c.r);
+    const size_t covn = c.cfg.full_cov ? (size_t)c.K * c.r * c.r : 0;
+    const size_t need = sizeof(SaveHeader) + sizeof(double) * ((size_t)c.N * c.d + c.N + c.K + 2 * (size_t)c.K * c.r + covn);
     if (bytes < need) return fail(ctx, SMC_EINVAL, "smc_load: truncated checkpoint");
     API_BEGIN
     const double* q = reinterpret_cast<const double*>(reinterpret_cast<const char*>(host_buf) + sizeof(h));
@@ -791,6 +840,8 @@ smc_status smc_load(smc_ctx* ctx, const void* host_buf, size_t bytes) {
     check(cudaMemcpyAsync(c.gmu, q, (size_t)c.K * c.r * 8, cudaMemcpyHostToDevice, c.stream), "load");
     q += (size_t)c.K * c.r;
     check(cudaMemcpyAsync(c.glam, q, (size_t)c.K * c.r * 8, cudaMemcpyHostToDevice, c.stream), "load");
+    q += (size_t)c.K * c.r;
+    if (covn && h.fitted) factor_mixture(c, q);            // uploads C_j and its factors
     check(cudaStreamSynchronize(c.stream), "sync");
     c.layer = h.layer; c.stage = h.stage; c.fitted = h.fitted != 0; c.step = h.step; c.t = h.t; c.beta = h.beta;
     return SMC_OK;

@@ -10,6 +10,7 @@
 //   max_j g_nj (pooled variances, w_j = 1/N); weights are renormalised.
 // Initial means: K distinct particles from Philox (purpose EMINIT), variances
 // the pooled population variance, w_j = 1/K.  A fixed number of iterations.
+#include <cmath>
 #include <vector>
 #include "smcgm_internal.cuh"
 #include "common.cuh"
@@ -182,6 +183,137 @@ __global__ void k_lamS(int r, const double* __restrict__ lam, const int* __restr
     if (s < r) out[s] = lam[S[s]];
 }
 
+// ------------------------------------------------------------------------
+// Full covariances on the mixture modes (cfg.full_cov; a reading beyond the
+// paper, whose C_j are diagonal in the KL basis):
+//   E-step: log p_nj = log w_j - r/2 log(2 pi) - log det L_j - |L_j^{-1}(x_n - m_j)|^2 / 2,
+//   M-step: C_j = sum_n g_nj (x_n - m_j)(x_n - m_j)^T / N_j + floor diag(lambda_S),
+//   initial and re-seeded covariances diag(pooled variances).
+// L_j (Cholesky), L_j^{-1} and log det L_j are formed on the host in FP64
+// (factor_mixture) after every M-step: K r x r matrices, a few hundred KB.
+// ------------------------------------------------------------------------
+
+// E-step, one block per particle: for each j, y = L_j^{-1}(x_n - m_j) (a row per thread).
+__global__ void __launch_bounds__(128) k_estep_full(int N, int K, int r, const double* __restrict__ xsT, const double* __restrict__ w,
+                                                    const double* __restrict__ m, const double* __restrict__ Li,
+                                                    const double* __restrict__ logdet, double* __restrict__ resp,
+                                                    double* __restrict__ lse, double* __restrict__ gmax) {
+    __shared__ double red[32];
+    __shared__ double dev[MAXR];
+    __shared__ double lp[MAXK];
+    const int n = blockIdx.x;
+    for (int j = 0; j < K; ++j) {
+        for (int s = threadIdx.x; s < r; s += blockDim.x) dev[s] = xsT[(size_t)s * N + n] - m[(size_t)j * r + s];
+        __syncthreads();
+        double q = 0.0;
+        const double* Lj = Li + (size_t)j * r * r;
+        for (int i = threadIdx.x; i < r; i += blockDim.x) {
+            double y = 0.0;
+            for (int k = 0; k <= i; ++k) y += Lj[(size_t)i * r + k] * dev[k];
+            q += y * y;
+        }
+        q = block_sum(q, red);
+        if (threadIdx.x == 0) lp[j] = log(w[j]) - 0.5 * r * log(2.0 * M_PI) - logdet[j] - 0.5 * q;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double mx = -1.0 / 0.0;
+        for (int j = 0; j < K; ++j) mx = fmax(mx, lp[j]);
+        double sum = 0.0;
+        for (int j = 0; j < K; ++j) sum += exp(lp[j] - mx);
+        const double l = mx + log(sum);
+        double gm = 0.0;
+        for (int j = 0; j < K; ++j) {
+            const double g = exp(lp[j] - l);
+            resp[(size_t)j * N + n] = g;
+            gm = fmax(gm, g);
+        }
+        lse[n] = l;
+        gmax[n] = gm;
+    }
+}
+
+// M-step covariances, one block per (j, a, b <= a); both triangles written.
+__global__ void k_mstep_cov(int N, int r, const double* __restrict__ xsT, const double* __restrict__ resp,
+                            const double* __restrict__ nj, const double* __restrict__ m, const double* __restrict__ lamS,
+                            double floor_frac, double* __restrict__ cov) {
+    __shared__ double red[32];
+    const int tri = r * (r + 1) / 2;
+    const int j = blockIdx.x / tri;
+    int t = blockIdx.x % tri, a = 0;
+    while (t > a) { t -= a + 1; ++a; }
+    const int b = t;                                   // b <= a
+    const double* g = resp + (size_t)j * N;
+    const double* xa = xsT + (size_t)a * N;
+    const double* xb = xsT + (size_t)b * N;
+    const double ma = m[(size_t)j * r + a], mb = m[(size_t)j * r + b];
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (xa[n] - ma) * (xb[n] - mb);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        const double v = acc / nj[j] + (a == b ? floor_frac * lamS[a] : 0.0);
+        cov[((size_t)j * r + a) * r + b] = v;
+        cov[((size_t)j * r + b) * r + a] = v;
+    }
+}
+
+// cov_j = diag(lam_j) for the components that are new (all) or re-seeded (N_j < 2).
+__global__ void k_cov_diag(int K, int r, const double* __restrict__ nj, const double* __restrict__ lam, double* __restrict__ cov) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K * r * r) return;
+    const int j = t / (r * r), a = (t / r) % r, b = t % r;
+    if (nj && !(nj[j] < 2.0)) return;
+    cov[t] = a == b ? lam[(size_t)j * r + a] : 0.0;
+}
+
+// lam_j = diag(C_j) (what smc_get_mixture reports in the full-covariance form).
+__global__ void k_diag_of_cov(int K, int r, const double* __restrict__ cov, double* __restrict__ lam) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < K * r) lam[t] = cov[((size_t)(t / r) * r + t % r) * r + t % r];
+}
+
+void factor_mixture(Ctx& c, const double* cov_host) {
+    const int K = c.K, r = c.r;
+    const size_t rr = (size_t)r * r;
+    std::vector<double> cov(K * rr), L(K * rr, 0.0), Li(K * rr, 0.0), logdet(K, 0.0);
+    if (cov_host) {
+        std::copy(cov_host, cov_host + K * rr, cov.begin());
+    } else {
+        check(cudaMemcpyAsync(cov.data(), c.gcov, K * rr * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "cov d2h");
+        check(cudaStreamSynchronize(c.stream), "sync");
+    }
+    for (int j = 0; j < K; ++j) {
+        const double* A = cov.data() + j * rr;
+        double* Lj = L.data() + j * rr;
+        double* Ij = Li.data() + j * rr;
+        for (int i = 0; i < r; ++i) {                  // Cholesky-Banachiewicz, A = L L^T
+            for (int k = 0; k <= i; ++k) {
+                double sum = A[(size_t)i * r + k];
+                for (int q = 0; q < k; ++q) sum -= Lj[(size_t)i * r + q] * Lj[(size_t)k * r + q];
+                if (i == k) {
+                    if (!(sum > 0.0)) throw InputError{"a mixture covariance is not positive definite"};
+                    Lj[(size_t)i * r + i] = std::sqrt(sum);
+                } else {
+                    Lj[(size_t)i * r + k] = sum / Lj[(size_t)k * r + k];
+                }
+            }
+            logdet[j] += std::log(Lj[(size_t)i * r + i]);
+        }
+        for (int col = 0; col < r; ++col) {            // L^{-1} by forward substitution on the unit vectors
+            for (int i = col; i < r; ++i) {
+                double sum = i == col ? 1.0 : 0.0;
+                for (int q = col; q < i; ++q) sum -= Lj[(size_t)i * r + q] * Ij[(size_t)q * r + col];
+                Ij[(size_t)i * r + col] = sum / Lj[(size_t)i * r + i];
+            }
+        }
+    }
+    if (cov_host) check(cudaMemcpyAsync(c.gcov, cov.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "cov");
+    check(cudaMemcpyAsync(c.gL, L.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "L");
+    check(cudaMemcpyAsync(c.gLi, Li.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "Li");
+    check(cudaMemcpyAsync(c.glogdet, logdet.data(), K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "logdet");
+    check(cudaStreamSynchronize(c.stream), "sync");    // the host vectors go out of scope
+}
+
 double gm_fit_device(Ctx& c) {
     const int N = c.N, K = c.K, r = c.r;
     const double fl = c.cfg.var_floor;
@@ -208,6 +340,26 @@ double gm_fit_device(Ctx& c) {
     const size_t esm = sizeof(double) * (2 * (size_t)K * r + K);
     if (esm > 48 * 1024) check(cudaFuncSetAttribute(k_estep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm), "attr");
     const int eg = (N + 255) / 256;
+    if (c.cfg.full_cov) {
+        const int kr2 = K * r * r;
+        k_cov_diag<<<(kr2 + 255) / 256, 256, 0, c.stream>>>(K, r, nullptr, c.glam, c.gcov); ++c.pc.launches;
+        for (int it = 0; it < c.cfg.em_iters; ++it) {
+            factor_mixture(c, nullptr);
+            k_estep_full<<<N, 128, 0, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.gLi, c.glogdet, c.resp, c.lse, c.gmax); ++c.pc.launches;
+            k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu); ++c.pc.launches;
+            k_mstep_cov<<<K * r * (r + 1) / 2, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu, lamS, fl, c.gcov); ++c.pc.launches;
+            k_diag_of_cov<<<(K * r + 255) / 256, 256, 0, c.stream>>>(K, r, c.gcov, c.glam); ++c.pc.launches;
+            k_mstep_fix<<<1, 1024, 0, c.stream>>>(N, K, r, c.nj, c.gmax, c.xsT, c.pooled, c.gw, c.gmu, c.glam); ++c.pc.launches;
+            k_cov_diag<<<(kr2 + 255) / 256, 256, 0, c.stream>>>(K, r, c.nj, c.glam, c.gcov); ++c.pc.launches;   // re-seeded ones
+        }
+        factor_mixture(c, nullptr);
+        k_estep_full<<<N, 128, 0, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.gLi, c.glogdet, c.resp, c.lse, c.gmax); ++c.pc.launches;
+        k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8); ++c.pc.launches;
+        double ll = 0.0;
+        check(cudaMemcpyAsync(&ll, c.dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "ll");
+        check(cudaStreamSynchronize(c.stream), "sync");
+        return ll;
+    }
     for (int it = 0; it < c.cfg.em_iters; ++it) {
         k_estep<<<eg, 256, esm, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.glam, c.resp, c.lse, c.gmax); ++c.pc.launches;
         k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu); ++c.pc.launches;

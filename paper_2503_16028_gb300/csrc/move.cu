@@ -187,6 +187,110 @@ void launch_propose(Ctx& c) {
     check(cudaGetLastError(), "propose");
 }
 
+// Full covariances on the mixture modes: one block per particle.  The drawn
+// component j gives v_S = gamma u_S + (1-gamma) m_j + beta L_j z_S (z_S the
+// same normals the diagonal proposal uses on S), the other modes the pCN move;
+// then for every component
+//   log r_j(b|a) = 1/2 sum_s log lambda_s - log det L_j - |L_j^{-1}(e - (1-gamma) m_j)|^2 / (2 beta^2)
+//                  + sum_s e_s^2 / (2 beta^2 lambda_s),   e = b_S - gamma a_S.
+__global__ void __launch_bounds__(256) k_propose_full(int d, int K, int r, const double* __restrict__ X, double* __restrict__ V,
+                                                      const double* __restrict__ sqrtlam, const double* __restrict__ lam,
+                                                      const int* __restrict__ slot, const int* __restrict__ S,
+                                                      const double* __restrict__ tab, const double* __restrict__ L,
+                                                      const double* __restrict__ Li, const double* __restrict__ logdet,
+                                                      double beta, double gamma, uint32_t step, Key key, double* __restrict__ lfwd,
+                                                      double* __restrict__ lrev, const float2* __restrict__ ntab, NormalConsts nc) {
+    __shared__ int s_j;
+    __shared__ float2 tab_s[NORMAL_TAB];
+    __shared__ double zS[MAXR], ef[MAXR], er[MAXR];
+    __shared__ double red[32];
+    __shared__ double s_c;
+    for (int i = threadIdx.x; i < NORMAL_TAB; i += blockDim.x) tab_s[i] = ntab[i];
+    const int p = blockIdx.x;
+    const int Kr = K * r;
+    const double* cumw = tab + 4 * Kr + r + K;
+    if (threadIdx.x == 0) {
+        U4 wc = philox(0u, (uint32_t)p, step, P_COMP, key.k0, key.k1);
+        const double U = open53(wc.x, wc.y);
+        int j = K - 1;
+        for (int q = 0; q < K; ++q)
+            if (U < cumw[q]) { j = q; break; }
+        s_j = j;
+    }
+    __syncthreads();
+    const int j = s_j;
+    const double* u = X + (size_t)p * d;
+    double* v = V + (size_t)p * d;
+    const double* mu = tab + 2 * Kr;                  // (1 - gamma) m
+    for (int m = threadIdx.x; m < (d + 1) / 2; m += blockDim.x) {
+        double z[2];
+        normal_pair_df((uint32_t)m, (uint32_t)p, step, P_NORMAL, key, tab_s, nc, z[0], z[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cidx = 2 * m + h;
+            if (cidx >= d) break;
+            const int sl = slot[cidx];
+            if (sl < 0) v[cidx] = gamma * u[cidx] + (beta * sqrtlam[cidx]) * z[h];
+            else zS[sl] = z[h];
+        }
+    }
+    __syncthreads();
+    const double* Lj = L + (size_t)j * r * r;
+    for (int s = threadIdx.x; s < r; s += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k <= s; ++k) acc += Lj[(size_t)s * r + k] * zS[k];
+        const int cidx = S[s];
+        v[cidx] = (gamma * u[cidx] + mu[(size_t)j * r + s]) + beta * acc;
+    }
+    __syncthreads();
+    double c0 = 0.0;
+    for (int s = threadIdx.x; s < r; s += blockDim.x) {
+        const int cidx = S[s];
+        ef[s] = v[cidx] - gamma * u[cidx];
+        er[s] = u[cidx] - gamma * v[cidx];
+        const double l = lam[cidx];
+        c0 += 0.5 * log(l);
+    }
+    c0 = block_sum(c0, red);
+    if (threadIdx.x == 0) s_c = c0;
+    __syncthreads();
+    const double ib2 = 1.0 / (beta * beta);
+    for (int jj = 0; jj < K; ++jj) {
+        const double* Lij = Li + (size_t)jj * r * r;
+        const double* muj = mu + (size_t)jj * r;
+        double qf = 0.0, qr = 0.0, pf = 0.0, pr = 0.0;
+        for (int i = threadIdx.x; i < r; i += blockDim.x) {
+            double yf = 0.0, yr = 0.0;
+            for (int k = 0; k <= i; ++k) {
+                const double lik = Lij[(size_t)i * r + k];
+                yf += lik * (ef[k] - muj[k]);
+                yr += lik * (er[k] - muj[k]);
+            }
+            qf += yf * yf;
+            qr += yr * yr;
+            const double l = lam[S[i]];
+            pf += ef[i] * ef[i] / l;
+            pr += er[i] * er[i] / l;
+        }
+        qf = block_sum(qf, red);
+        qr = block_sum(qr, red);
+        pf = block_sum(pf, red);
+        pr = block_sum(pr, red);
+        if (threadIdx.x == 0) {
+            lfwd[(size_t)p * K + jj] = s_c - logdet[jj] - 0.5 * qf * ib2 + 0.5 * pf * ib2;
+            lrev[(size_t)p * K + jj] = s_c - logdet[jj] - 0.5 * qr * ib2 + 0.5 * pr * ib2;
+        }
+    }
+}
+
+void launch_propose_full(Ctx& c) {
+    const double gamma = sqrt(1.0 - c.beta * c.beta);
+    k_propose_full<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.lam, c.slot, c.S, c.tab, c.gL, c.gLi, c.glogdet,
+                                              c.beta, gamma, c.step, c.key, c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab),
+                                              c.normc); ++c.pc.launches;
+    check(cudaGetLastError(), "propose full");
+}
+
 __device__ inline double lse_terms(const double* lw, const double* l, int K) {
     double mx = -1.0 / 0.0;
     for (int j = 0; j < K; ++j) mx = fmax(mx, lw[j] + l[j]);

@@ -126,6 +126,8 @@ void launch_accept_pcnl(Ctx& c, int* acc_count);
 void launch_temper(Ctx& c, double* out5);
 void launch_resample(Ctx& c);
 double gm_fit_device(Ctx& c);
+void factor_mixture(Ctx& c, const double* cov_host);   // Cholesky, inverse and log det of every C_j (host), uploaded
+void launch_propose_full(Ctx& c);
 void launch_moments(Ctx& c, double* mean, double* var);
 void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
 int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out);   // largest CG iteration count
@@ -148,6 +150,9 @@ struct Ctx {
     double* dscal = nullptr;   // small device double scratch (temper outputs etc.)
     // mixture and proposal tables
     double *gw = nullptr, *gmu = nullptr, *glam = nullptr;
+    // full covariances on the mixture modes (cfg.full_cov): C_j, its Cholesky
+    // factor L_j (lower), L_j^{-1} and log det L_j; glam holds diag(C_j)
+    double *gcov = nullptr, *gL = nullptr, *gLi = nullptr, *glogdet = nullptr;
     double *tab = nullptr;     // per (j, s): c0, a, mu, sq; then per s: b; then per j: log w, cumulative w
     // EM scratch
     double *xsT = nullptr, *resp = nullptr, *nj = nullptr, *pooled = nullptr, *lse = nullptr, *gmax = nullptr;

@@ -33,7 +33,7 @@ class smc_config(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("tol_inner", ctypes.c_double), ("tol_outer", ctypes.c_double),
         ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int), ("fine_sweeps", ctypes.c_int),
         ("coarse_scale", ctypes.c_double), ("solve_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-        ("gradient", ctypes.c_int),
+        ("gradient", ctypes.c_int), ("full_cov", ctypes.c_int),
     ]
 
 
@@ -62,6 +62,8 @@ EXPORTS = {
     "smc_get_schedule": (ctypes.c_int, [_vp, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_uint)]),
     "smc_set_mixture": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "smc_get_mixture": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "smc_set_mixture_cov": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "smc_get_mixture_cov": (ctypes.c_int, [_vp, _vp]),
     "smc_get_diagnostics": (ctypes.c_int, [_vp] + [ctypes.POINTER(_vp)] * 5),
     "smc_save": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "smc_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
@@ -127,7 +129,7 @@ def make_config(preset, **overrides):
     cfg.n_particles = p["n_particles"]; cfg.n_components = p["n_components"]; cfg.gm_rank = p["gm_rank"]
     cfg.beta0 = p["beta0"]; cfg.ess_frac = p["ess_frac"]; cfg.seed = p["seed"]
     for key in ("em_iters", "var_floor", "kernel", "precision", "tol_inner", "tol_outer", "max_iter", "max_refine",
-                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch", "gradient"):
+                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch", "gradient", "full_cov"):
         if key in p:
             setattr(cfg, key, p[key])
     cfg._keep = (obs, data)
@@ -245,6 +247,16 @@ class Sampler:
         w = np.ascontiguousarray(w, dtype=np.float64); m = np.ascontiguousarray(m, dtype=np.float64)
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         self._check(self.lib.smc_set_mixture(self.ctx, _ptr(w), _ptr(m), _ptr(lam)), self.ctx)
+
+    def smc_set_mixture_cov(self, w, m, cov):
+        w = np.ascontiguousarray(w, dtype=np.float64); m = np.ascontiguousarray(m, dtype=np.float64)
+        cov = np.ascontiguousarray(cov, dtype=np.float64)
+        self._check(self.lib.smc_set_mixture_cov(self.ctx, _ptr(w), _ptr(m), _ptr(cov)), self.ctx)
+
+    def smc_get_mixture_cov(self):
+        cov = np.empty((self.K, self.r, self.r))
+        self._check(self.lib.smc_get_mixture_cov(self.ctx, _ptr(cov)), self.ctx)
+        return cov
 
     def smc_get_mixture(self):
         w = np.empty(self.K); m = np.empty((self.K, self.r)); lam = np.empty((self.K, self.r))
