@@ -138,14 +138,18 @@ smc_status smc_temper_step(smc_ctx* ctx, double* h, double* ess, double* logZ_in
  * on a 2^48 fixed-point CDF (order-independent, bit-exact), then a particle gather. */
 smc_status smc_resample(smc_ctx* ctx);
 
-/* Mixture estimation of Alg. 3 / Sec. 2.4: EM for K diagonal Gaussians on
- * the gm_rank leading KL coordinates of the particles; prior elsewhere.
- * loglik (host, may be NULL) receives the final log-likelihood. */
+/* Mixture estimation of Alg. 3 / Sec. 2.4: EM for K diagonal Gaussians (or,
+ * with cfg.full_cov, Gaussians with full covariances) on the gm_rank leading
+ * KL coordinates of the particles; prior elsewhere.  loglik (host, may be
+ * NULL) receives the final log-likelihood. */
 smc_status gm_fit(smc_ctx* ctx, double* loglik);
 
-/* Mutation step: `steps` pCN-GM steps (Alg. 2; proposal eq. pCN-GM proposal,
- * acceptance eqs. auv of pCN-GMM..GMM4) for all particles at the current t,
- * each step solving N forward problems; then the beta rule of App. C.
+/* Mutation step: `steps` steps of cfg.kernel (pCN-GM: Alg. 2, proposal eq.
+ * pCN-GM proposal, acceptance eqs. auv of pCN-GMM..GMM4; the other kernels
+ * as described at smc_kernel) for all particles at the current t, each step
+ * solving N forward problems (2N with the Langevin kernels); then the beta
+ * rule of App. C (not for SMC_K_GM_INDEP).  A proposal whose field leaves
+ * the mixed-precision range (|u| >= 64) is not solved and is rejected.
  * accept_rate: mean acceptance over the steps; iters_max: the largest
  * number of CG iterations any solve used (both host, may be NULL). */
 smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max);
