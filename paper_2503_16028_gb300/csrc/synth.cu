@@ -227,8 +227,9 @@ void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U) {
 // potential gradient): G[k][l] = c_k c_l sum_{i,j} g[j][i] cos(k pi x_i)
 // cos(l pi y_j), a DCT-II along each axis keeping the Km lowest outputs.  The
 // network is the transpose of fct_warp's: the butterfly levels first, in
-// reverse order, each mapping the pair (X[o + i], X[o + M - 1 - i]) to
-// G = X[o + i] + X[o + M - 1 - i], H = t_i (X[o + i] - X[o + M - 1 - i]); then
+// reverse order (two per shared-memory pass), each mapping the pair
+// (X[o + i], X[o + M - 1 - i]) to G = X[o + i] + X[o + M - 1 - i],
+// H = t_i (X[o + i] - X[o + M - 1 - i]); then
 // the splitting levels, in reverse order, x[2m] = e[m], x[2m + 1] =
 // y[m] + y[m + 1] (y[h] = 0).
 // ------------------------------------------------------------------------
@@ -239,14 +240,34 @@ __device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1
     V* src = b0;
     V* dst = b1;
     const int half = N >> 1;
-    for (int lm = lgN; lm >= 1; --lm) {
+    // transposed butterflies, two levels per pass (levels lm + 1 and lm, the
+    // transpose of fct_warp's paired pass): the four values at o2 + i,
+    // o2 + 2M - 1 - i, o2 + M - 1 - i, o2 + M + i map to o2 + i, o2 + h + i,
+    // o2 + M + i, o2 + M + h + i
+    for (int lm = lgN - 1; lm >= 1; lm -= 2) {
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        const typename O::W* twm = tw + (h - 1);
-        for (int idx = lane; idx < half; idx += 32) {
-            const int o = (idx >> lh) << lm, i = idx & (h - 1);
-            const V a = src[o + i], b = src[o + M - 1 - i];
-            dst[o + i] = O::add(a, b);
-            dst[o + h + i] = O::mul(O::sub(a, b), twm[i]);
+        const typename O::W* twa = tw + (h - 1);
+        const typename O::W* twb = tw + (M - 1);
+        for (int g = lane; g < (N >> 2); g += 32) {
+            const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
+            const V A = src[o2 + i], B = src[o2 + 2 * M - 1 - i], C = src[o2 + M - 1 - i], D = src[o2 + M + i];
+            const V x0 = O::add(A, B), x1 = O::add(C, D);
+            const V y0 = O::mul(O::sub(A, B), twb[i]);
+            const V y1 = O::mul(O::sub(C, D), twb[M - 1 - i]);
+            const typename O::W ta = twa[i];
+            dst[o2 + i] = O::add(x0, x1);
+            dst[o2 + h + i] = O::mul(O::sub(x0, x1), ta);
+            dst[o2 + M + i] = O::add(y0, y1);
+            dst[o2 + M + h + i] = O::mul(O::sub(y0, y1), ta);
+        }
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+    }
+    if (lgN & 1) {                                    // level 1 alone, last (the forward runs it first)
+        for (int i0 = lane; i0 < half; i0 += 32) {
+            const V a = src[2 * i0], b = src[2 * i0 + 1];
+            dst[2 * i0] = O::add(a, b);
+            dst[2 * i0 + 1] = O::mul(O::sub(a, b), tw[0]);
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
