@@ -246,9 +246,19 @@ def model_bytes_per_solve(prof, n, d):
     it = prof["cg_iterations"] / solves
     inner = prof["inner_solves"] / solves
     res = prof["residuals"] / solves
-    # per CG iteration (per cell): apply 6 words, fine pre 9.25, fine post 5.25, level-1 pre+post 2.3, coarse 0.35
-    cg = (6 + 9.25 + 5.25 + 2.3 + 0.35) * w
-    start = (4.25 + 5.25 + 2.3 + 0.35) * w                     # z0 = M r0 per inner solve
+    # per V-cycle below the finest level (words per finest cell): each tiled level l >= 1 (n_l > 32)
+    # pre-smoothing 4.25 words of its cells (r, Kw, Ks in; e, 1/4 restricted out) and post-smoothing
+    # 5.25 (r, e, Kw, Ks, 1/4 parent in; e2 out), a fraction 4^-l of the finest cells; the coarse
+    # kernel (32^2 and below) reads the coarse faces (2 words x 1/48) and its top level's r, writes e2
+    n = int(round(cells ** 0.5))
+    lower, l = 0.0, 1
+    while (n >> l) > 32:
+        lower += 9.5 * 4.0 ** -l
+        l += 1
+    lower += 2.0 / 48.0 + 2.0 * 4.0 ** -l
+    # per CG iteration (per cell): apply 6 words, fine pre 9.25, fine post 5.25, and the levels below
+    cg = (6 + 9.25 + 5.25 + lower) * w
+    start = (4.25 + 5.25 + lower) * w                          # z0 = M r0 per inner solve
     refine = 24.0 + 28.0                                      # w += x (w, x in and out); residual (w, faces hi/lo in; r out)
     # set-up: synthesis passes (T^T out and in, u out: 16 B), faces (u in, faces hi/lo out: 24 B),
     # coarsening (2.7 words), w and x cleared and r = b (16 B)
