@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "darcy256_precision"
+SMALL_WORKLOAD = "darcy64_bimodal"
 TRAFFIC_BYTES_PER_CELL = 36.03   # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tpre<2,1,4> per cell
 METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
 UNIT = "solves/s"
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient timing")
+    ap.add_argument("--no-layers", action="store_true", help="skip the whole SMC run timed layer by layer")
+    ap.add_argument("--no-small", action="store_true", help="skip the 64^2 workload (GPU and CPU oracle)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -93,7 +96,7 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_rate(budget_s, procs=None):
+def cpu_oracle_rate(budget_s, procs=None, workload=WORKLOAD):
     """Solves/s of the oracle on the host cores: one process per core (BLAS pinned to one thread
     each), process i moving particles i, i + procs, ...; the rate is all their solves over the
     longest process's time."""
@@ -101,7 +104,7 @@ def cpu_oracle_rate(budget_s, procs=None):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     running = []
     for i in range(procs):
-        code = CPU_SNIPPET % dict(root=ROOT, name=WORKLOAD, budget=budget_s, start=i, stride=procs)
+        code = CPU_SNIPPET % dict(root=ROOT, name=workload, budget=budget_s, start=i, stride=procs)
         running.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
                                         stderr=subprocess.PIPE, text=True, env=env))
     outs = []
@@ -219,6 +222,105 @@ def time_gradient(wl, N, smcgm, torch, calls=2):
                 solves_per_gradient=prof["solves"] / (N * calls), cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_forward(s, torch, calls=2):
+    """Solver-only throughput: smc_forward (KL synthesis, Darcy solve, observation, Phi; no proposal,
+    mixture terms or accept) of the sampler's N particles, CUDA events on the library's stream
+    after one untimed call."""
+    X = torch.tensor(s.particles()[0], dtype=torch.float64, device="cuda")
+    Phi = torch.empty(X.shape[0], dtype=torch.float64, device="cuda")
+    s.smc_forward(X, Phi)
+    s.smc_profile_query(reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record(s.stream)
+    for _ in range(calls):
+        s.smc_forward(X, Phi)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / calls
+    prof = s.smc_profile_query(reset=True)
+    return dict(value=X.shape[0] / (ms / 1000.0), unit=UNIT, ms_per_call=ms,
+                cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
+
+
+def time_layers(wl, N, smcgm, torch, max_layers=60):
+    """A whole SMC run of the workload (Alg. 2): every tempering layer reweights (ESS bisection),
+    resamples, fits the mixture and makes L pCN-GM moves; each layer's smc_move is timed with
+    CUDA events.  Returns solves/s of the first layer's moves, of the moves of the layers with
+    0.1 < t < 1 and of all layers, with the layer count and the run's wall time."""
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N))
+    L = wl["mcmc_steps"]
+    rows, logz = [], 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max_layers):
+        _, _, lz, done = s.smc_temper_step()
+        logz += lz
+        s.smc_resample()
+        s.gm_fit()
+        t = s.smc_get_schedule()[0]
+        s.smc_profile_query(reset=True)
+        e0, e1 = _events(torch)
+        e0.record(s.stream)
+        acc, _ = s.smc_move(L, allow_noconv=True)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        prof = s.smc_profile_query(reset=True)
+        rows.append(dict(t=t, ms=e0.elapsed_time(e1), solves=prof["solves"], cg=prof["cg_iterations"], acc=acc))
+        if done:
+            break
+    seconds = time.perf_counter() - t0
+    s.close()
+
+    def agg(sel):
+        if not sel:
+            return None
+        ms = sum(r["ms"] for r in sel)
+        sv = sum(r["solves"] for r in sel)
+        return dict(layers=len(sel), solves_per_s=sv / (ms / 1000.0), cg_per_solve=sum(r["cg"] for r in sel) / max(1, sv),
+                    acceptance=sum(r["acc"] for r in sel) / len(sel))
+    first = agg(rows[:1])
+    first["t"] = rows[0]["t"]
+    return dict(count=len(rows), finished=bool(rows[-1]["t"] >= 1.0), moves_per_layer=L, run_seconds=seconds,
+                log_evidence=logz, first=first, t_between_0p1_and_1=agg([r for r in rows if 0.1 < r["t"] < 1.0]),
+                all=agg(rows))
+
+
+def precision_agreement(s64, moves, wl, N, smcgm):
+    """The mixed-precision path against the FP64 path from the same state: a fresh mixed-precision
+    sampler of the workload taken through the FP64 sampler's history (one tempering layer, then
+    `moves` single moves with the same random streams).  Returns the largest absolute difference
+    of the posterior mean and variance of the KL coefficients, the largest relative difference of
+    Phi and the number of particles whose states differ."""
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
+    for _ in range(moves):
+        s.smc_move(1, allow_noconv=True)
+    X, P = s.particles()
+    X64, P64 = s64.particles()
+    m, v = s.smc_posterior_moments()[:2]
+    m64, v64 = s64.smc_posterior_moments()[:2]
+    s.close()
+    return dict(moves=moves, max_abs_posterior_mean_diff=float(np.max(np.abs(m - m64))),
+                max_abs_posterior_var_diff=float(np.max(np.abs(v - v64))),
+                max_rel_phi_diff=float(np.max(np.abs(P - P64) / np.maximum(np.abs(P64), 1e-300))),
+                particles_differing=int(np.sum(np.any(X != X64, axis=1))), target=1e-6)
+
+
+def time_small(args, smcgm, torch, barrier):
+    """GPU solves/s on the 64^2 workload (32^2 modes, N = 1024, K = 4), timed like the headline."""
+    from paper_2503_16028_gb300 import inputs
+    wl = inputs.load_workload(SMALL_WORKLOAD)
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, wl["n_particles"], smcgm)
+    ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
+    s.close()
+    return dict(workload=SMALL_WORKLOAD, particles=wl["n_particles"], value=wl["n_particles"] * args.steps / (ms / 1000.0),
+                unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
+
+
 def time_moves(s, steps, warmup, torch, barrier):
     for _ in range(warmup):
         s.smc_move(1, allow_noconv=True)
@@ -303,6 +405,11 @@ def run_native(args, rank, world, local):
         cpu = dict(value=rate, unit=UNIT, cores=o["cores"], kind="oracle",
                    sample="%d solves of the 256^2 workload (prior draw + one pCN step per particle, sparse LU), "
                           "%.1f s on %d processes" % (o["solves"], o["seconds"], o["cores"]))
+    cpu_small = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.no_small:
+        rate, o = cpu_oracle_rate(args.cpu_seconds / 3.0, workload=SMALL_WORKLOAD)
+        cpu_small = dict(value=rate, unit=UNIT, cores=o["cores"], kind="oracle",
+                         sample="%d solves of the 64^2 workload in %.1f s on %d processes" % (o["solves"], o["seconds"], o["cores"]))
     wl = inputs.load_workload(WORKLOAD)
     N = args.particles or wl["n_particles"]
     from paper_2503_16028_gb300 import build
@@ -348,10 +455,11 @@ def run_native(args, rank, world, local):
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
     e2e = dict(value=whole_job_rate(N * e2e_steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
                d2h_bytes_per_step=N * d * 8 + N * 8)
+    forward = time_forward(s, torch)
     s.close()
     del s
     torch.cuda.empty_cache()
-    fp64 = None
+    fp64 = agree = None
     if not args.no_fp64:
         s64 = make_sampler(wl, smcgm.SMC_P_FP64, N, smcgm)
         ms64, prof64 = time_moves(s64, max(2, args.steps // 2), 1, torch, barrier)
@@ -360,10 +468,16 @@ def run_native(args, rank, world, local):
         fp64 = dict(value=whole_job_rate(N * st64, world, ms64), ms_per_step=ms64 / st64,
                     cg_per_solve=prof64["cg_iterations"] / max(1, prof64["solves"]),
                     dominant_kernel_gbs=prof64["dom_bytes"] / (prof64["dom_ms"] / 1000.0) / 1e9 if prof64["dom_ms"] else None)
+        agree = precision_agreement(s64, 1 + st64, wl, N, smcgm)
         s64.close()
     grad = None
     if not args.no_gradient:
         grad = time_gradient(wl, N, smcgm, torch)
+    layers = None if args.no_layers else time_layers(wl, N, smcgm, torch)
+    small = None
+    if not args.no_small:
+        small = time_small(args, smcgm, torch, barrier)
+        small["cpu_oracle"] = cpu_small
     if rank != 0:
         return
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -376,8 +490,9 @@ def run_native(args, rank, world, local):
                 roofline=roof, hbm_roofline_step=dict(model_bytes_per_solve=bps, achieved_gbs=step_hbm,
                                                       frac=step_hbm / hbm_peak, peak=hbm_peak),
                 iterations=iters, fp64=fp64,
-                speedup_vs_fp64=(value / fp64["value"]) if fp64 else None,
-                e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu, adjoint_gradient=grad)
+                speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, fp64_agreement=agree,
+                solver_only=forward, e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu,
+                adjoint_gradient=grad, smc_run=layers, small_workload=small)
     print(json.dumps(line), flush=True)
 
 
