@@ -49,4 +49,20 @@ __device__ inline double recip_nr(double x) {
     return y;
 }
 
+// Asynchronous copy of one element from global to shared memory (cp.async,
+// 4 or 8 bytes; both addresses aligned to the element).  A block issues all
+// its copies and then waits once, instead of one DRAM round trip per copy:
+// an ordinary load into a shared array cannot pass the preceding shared
+// store, because the compiler cannot rule out that the two alias.
+template <typename T>
+__device__ inline void cp_async_elem(T* shared_dst, const T* global_src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async copies 4 or 8 bytes here");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(shared_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(global_src), "n"((int)sizeof(T)) : "memory");
+}
+
+// Waits for every cp.async this thread issued; a __syncthreads() after it
+// makes the copies of all threads visible to the block.
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace smcgm

@@ -485,7 +485,7 @@ __device__ inline void chalf(const T* kw, const T* ks, const T* E, const T* Nn, 
 }
 
 template <typename T, int NU>
-__global__ void __launch_bounds__(256) k_coarse(CoarseLevelPtrs<T> P, T cc, const int* __restrict__ active) {
+__global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, const int* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int pb = active[blockIdx.x];   // active-particle list
     T* kw[12]; T* ks[12]; T* E[12]; T* Nn[12]; T* r[12]; T* e[12];
@@ -501,15 +501,22 @@ __global__ void __launch_bounds__(256) k_coarse(CoarseLevelPtrs<T> P, T cc, cons
         Nn[l] = cur; cur += nl;
         const T* gkw = P.Kw[l] + (size_t)pb * nn;
         const T* gks = P.Ks[l] + (size_t)pb * nn;
-        for (int i = threadIdx.x; i < nn; i += blockDim.x) { kw[l][i] = gkw[i]; ks[l][i] = gks[i]; }
-        for (int i = threadIdx.x; i < nl; i += blockDim.x) { E[l][i] = P.E[l][(size_t)pb * nl + i]; Nn[l][i] = P.Nn[l][(size_t)pb * nl + i]; }
+        for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+            cp_async_elem(kw[l] + i, gkw + i);
+            cp_async_elem(ks[l] + i, gks + i);
+        }
+        for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+            cp_async_elem(E[l] + i, P.E[l] + (size_t)pb * nl + i);
+            cp_async_elem(Nn[l] + i, P.Nn[l] + (size_t)pb * nl + i);
+        }
         nl >>= 1;
     }
     {
         const int nn = P.ntop * P.ntop;
         const T* g = P.rtop + (size_t)pb * nn;
-        for (int i = threadIdx.x; i < nn; i += blockDim.x) r[0][i] = g[i];
+        for (int i = threadIdx.x; i < nn; i += blockDim.x) cp_async_elem(r[0] + i, g + i);
     }
+    cp_async_wait_all();   // every copy of this thread is in shared memory
     __syncthreads();
     // down
     nl = P.ntop;
