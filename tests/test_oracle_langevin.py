@@ -8,6 +8,11 @@
 * No drift (t = 0, or a zero gradient): the pCN proposal and acceptance.
 * The Crank-Nicolson step: beta = sqrt(8 delta)/(2 + delta) gives
   gamma = (2 - delta)/(2 + delta) and a drift factor 2 delta/(2 + delta).
+* The samplers against the densities: both proposals are affine in z, with
+  the mean and the per-coordinate scale of the Gaussians the detailed-balance
+  tests write out.
+* The move's wiring: t = 0 accepts the Philox-driven proposal, a potential of
+  +inf at the proposal rejects it and keeps the particle.
 """
 import numpy as np
 import pytest
@@ -126,3 +131,65 @@ def test_gm_special_cases():
     a = langevin.gm_log_alpha(u, v, 1.0, 0.5, g_u, g_v, mix, 0.3, 0.0)
     b = pcngm.log_alpha(0.0, 1.0, 0.5, pcngm.log_mixture_ratio(u, v, mix, 0.3))
     assert a == pytest.approx(b, rel=1e-12, abs=1e-12)
+
+
+def test_propose_is_mean_plus_scaled_noise():
+    """v is affine in z: z = 0 gives the drifted mean gamma u - (1 - gamma) t C g that the
+    detailed-balance test writes into q(u, .), and z = e_i adds beta sqrt(lambda_i) e_i."""
+    d = 6
+    lam = (1.0 + 0.3 * np.arange(d)) ** -2.0
+    rng = np.random.default_rng(21)
+    u, g = rng.standard_normal(d), rng.standard_normal(d)
+    beta, t = 0.4, 0.6
+    gm = np.sqrt(1 - beta ** 2)
+    mean = langevin.propose(u, g, lam, beta, t, np.zeros(d))
+    assert np.allclose(mean, gm * u - (1 - gm) * t * lam * g, rtol=0, atol=1e-15)
+    for i in range(d):
+        e = np.zeros(d); e[i] = 1.0
+        step = langevin.propose(u, g, lam, beta, t, e) - mean
+        expect = np.zeros(d); expect[i] = beta * np.sqrt(lam[i])
+        assert np.allclose(step, expect, rtol=0, atol=1e-15)
+
+
+def test_gm_propose_is_component_mean_plus_scaled_noise():
+    """The GMpCN-Langevin proposal from component j: z = 0 gives gamma u + (1 - gamma) m_j -
+    (1 - gamma) t C_j g (m_j and C_j = diag(lambda_j) on S, 0 and the prior off S), and z = e_i
+    adds beta sqrt(C_j,ii) e_i."""
+    d, r, K = 7, 4, 3
+    mix = _mixture(d, r, K, 13)
+    rng = np.random.default_rng(22)
+    u, g = rng.standard_normal(d), rng.standard_normal(d)
+    beta, t = 0.5, 0.3
+    gm = np.sqrt(1 - beta ** 2)
+    for j in range(K):
+        lamj = mix.lam0.copy(); lamj[:r] = mix.lam[j]
+        mj = np.zeros(d); mj[:r] = mix.m[j]
+        mean = langevin.gm_propose(u, g, j, np.zeros(d), mix, beta, t)
+        assert np.allclose(mean, gm * u + (1 - gm) * mj - (1 - gm) * t * lamj * g, rtol=0, atol=1e-15)
+        for i in range(d):
+            e = np.zeros(d); e[i] = 1.0
+            step = langevin.gm_propose(u, g, j, e, mix, beta, t) - mean
+            assert step[i] == pytest.approx(beta * np.sqrt(lamj[i]), rel=1e-14)
+            assert np.count_nonzero(np.abs(step) > 1e-15) == 1
+
+
+def test_move_particle_accepts_and_rejects():
+    """At t = 0 every proposal is accepted (log alpha = 0) and the new state is the proposal
+    from the Philox normals; with a potential of +inf at the proposal (t > 0) it is rejected
+    and the particle, its potential and gradient stay."""
+    from oracle import philox
+    d = 5
+    lam = np.linspace(1.0, 0.2, d)
+    x = np.linspace(-0.3, 0.4, d)
+    g = np.ones(d)
+    seed, n, step, beta = 7, 3, 2, 0.3
+    z = philox.normals(seed, d, n, step, philox.NORMAL)
+    v = langevin.propose(x, g, lam, beta, 0.0, z)
+    x2, phi2, g2, acc, la, pv = langevin.move_particle(x, 1.0, g, lam, beta, 0.0, seed, n, step,
+                                                       lambda y: (2.0, -y))
+    assert acc and la == 0.0 and pv == 2.0 and phi2 == 2.0
+    assert np.array_equal(x2, v) and np.array_equal(g2, -v)
+    x3, phi3, g3, acc3, la3, _ = langevin.move_particle(x, 1.0, g, lam, beta, 0.5, seed, n, step,
+                                                        lambda y: (np.inf, np.zeros(d)))
+    assert not acc3 and la3 == -np.inf
+    assert np.array_equal(x3, x) and phi3 == 1.0 and np.array_equal(g3, g)

@@ -95,6 +95,7 @@ def test_beta_one_is_independence_sampler_ratio():
             return pcngm.logsumexp(np.array(q)) - stats.multivariate_normal(np.zeros(4), np.diag(lam0)).logpdf(x)
         ref = logq_over_prior(u) - logq_over_prior(v)
         assert abs(pcngm.log_mixture_ratio(u, v, mix, 1.0) - ref) < 1e-11
+        assert abs(pcngm.log_density_kl(u, mix) - logq_over_prior(u)) < 1e-11
 
 
 def test_proposal_mean_and_components():
