@@ -1,5 +1,6 @@
 """Pins for the oracle's Darcy solver (Sec. 3.2, eq. example2:PDE)."""
 import numpy as np
+import pytest
 import sympy as sp
 
 from oracle import darcy
@@ -83,3 +84,22 @@ def test_manufactured_solution_1d_second_order():
         errs.append(np.max(np.abs(darcy.solve_1d(uf(xm), ff(xn)) - wf(xn))))
     ratios = [errs[i] / errs[i + 1] for i in range(3)]
     assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
+
+
+def test_sources_at_cell_centres_and_nodes():
+    """The Gaussian source of the 2D workloads: symmetric under x -> 1 - x and y -> 1 - y, the
+    value at a cell centre from the formula, and a midpoint sum equal to the integral of the
+    Gaussian over the plane, amp pi / width (the mass outside the unit square is below 1e-5 of
+    it at width 50); the 1D source at the interior nodes i/n; the constant kind."""
+    n, amp, width = 256, 10.0, 50.0
+    f = darcy.source_2d(n, 1, amp, width)
+    assert f.shape == (n, n)
+    assert np.array_equal(f, f[:, ::-1]) and np.array_equal(f, f[::-1, :]) and np.array_equal(f, f.T)
+    i, j = 37, 201
+    assert f[j, i] == pytest.approx(amp * np.exp(-width * (((i + 0.5) / n - 0.5) ** 2 + ((j + 0.5) / n - 0.5) ** 2)), rel=1e-15)
+    assert f.sum() / n ** 2 == pytest.approx(amp * np.pi / width, rel=1e-5)
+    assert np.array_equal(darcy.source_2d(8, 0, 3.0, 0.0), np.full((8, 8), 3.0))
+    g = darcy.source_1d(16, 1, amp, width)
+    assert g.shape == (15,) and g[7] == amp                        # node 8/16 = 1/2
+    assert g[2] == pytest.approx(amp * np.exp(-width * (3 / 16 - 0.5) ** 2), rel=1e-15)
+    assert np.array_equal(darcy.source_1d(16, 0, 1.0, 0.0), np.ones(15))
