@@ -1131,7 +1131,7 @@ struct Passes {
             A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list; A.a.err = c.dev_err;
             A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
             A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;
-            k_wapply<T><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
+            k_wapply<T, sizeof(T) == 4 ? 7 : 4><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
         } else {
             k_apply<T><<<dim3(ntiles, nact), Own<TILE + 2>::THREADS, 0, c.stream>>>(n, L0.Kw, L0.Ks, L0.E, L0.Nn, s.z, s.p[pc],
                                                                                    s.p[1 - pc], s.q, c.sc.betac, c.part.pq, s.list,

@@ -571,8 +571,11 @@ struct WApplyArgs {
 // loses it to cancellation.  CG's recursive residual r - alpha q then tracks
 // the true residual of the FP32 iterate closely, and each refinement phase's
 // reduction holds for the FP64 residual too.
-template <typename T>
-__global__ void __launch_bounds__(32 * WPB) k_wapply(WApplyArgs<T> A) {
+// MINB: resident blocks per SM asked of the register allocator (7 for FP32:
+// 72 registers without spills, 28 warps per SM to cover the load latency;
+// 4 for FP64: 128 registers).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(32 * WPB, MINB) k_wapply(WApplyArgs<T> A) {
     constexpr int PW = 48;                    // staged p row stride (tile + ring: 18 columns used)
     constexpr int PR = WT + 2;                // staged rows
     __shared__ T smp[WPB][PR * PW];
