@@ -169,8 +169,11 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl,
 
 /* Forward map F for `count` coefficient vectors already on the device
  * (d_X: count x d, FP64): synthesis, Darcy solve, observation, Phi.
- * d_Phi (count) and d_w (count x grid, FP64, may be NULL) are device
- * outputs; iters (host, may be NULL) gets the largest CG iteration count. */
+ * d_Phi (count) and d_w (count x grid, FP64, may be NULL; grid = n x n
+ * cells in 2D, the n - 1 interior nodes in 1D) are device
+ * outputs; iters (host, may be NULL) gets the largest CG iteration count.
+ * SMC_EINVAL if a device argument is host memory CUDA does not know (an
+ * ordinary malloc or stack address), checked before any kernel runs. */
 smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_w, int* iters);
 
 /* Potential and its gradient for `count` coefficient vectors on the device
@@ -182,7 +185,8 @@ smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi
  * (dK_f/du_c)(lam_c - lam_nb)(w_c - w_nb) with dK_f/du_c = K_f^2 e^{-u_c} / 2
  * for a harmonic face and K_f for a wall face; dPhi/dx is the transpose of the
  * synthesis applied to it.  The drift of the Langevin equation of App. B.
- * Needs cfg.gradient = 1 and dim = 2 (else SMC_ESTATE / SMC_EINVAL). */
+ * Needs cfg.gradient = 1 and dim = 2 (else SMC_ESTATE / SMC_EINVAL); device
+ * arguments are checked as in smc_forward. */
 smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_grad);
 
 /* Full-covariance mixtures (cfg.full_cov = 1): set or read the components'
@@ -277,8 +281,9 @@ smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t byt
  * device address with that device current (call it once before capturing work
  * into a stream graph).  All calls share the array: calls that overlap on the
  * GPU race and must be serialised by the caller (e.g. one stream).  Returns
- * SMC_EINVAL for n_particles outside [1, SMC_STATIC_RESAMPLE_MAX] (message in
- * smc_last_error(NULL)), SMC_ECUDA if a CUDA call fails.  Asynchronous on
+ * SMC_EINVAL for n_particles outside [1, SMC_STATIC_RESAMPLE_MAX] or a
+ * d_logw / d_indices that CUDA reports as unregistered host memory (message
+ * in smc_last_error(NULL)), SMC_ECUDA if a CUDA call fails.  Asynchronous on
  * `stream` (a cudaStream_t, NULL = default stream). */
 smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
                                        int* d_indices, void* stream);

@@ -640,6 +640,8 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl, 
 smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_grad) {
     if (!ctx || !d_X || !d_Phi || !d_grad || count < 1) return SMC_EINVAL;
     Ctx& c = ctx->c;
+    if (!device_visible(d_X) || !device_visible(d_Phi) || !device_visible(d_grad))
+        return fail(ctx, SMC_EINVAL, "smc_gradient: d_X, d_Phi and d_grad must be device memory");
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "smc_gradient: context not initialised");
     if (!c.lam64) return fail(ctx, SMC_ESTATE, "smc_gradient: the context was set up without cfg.gradient = 1");
     API_BEGIN
@@ -654,6 +656,8 @@ smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Ph
 smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_w, int* iters) {
     if (!ctx || !d_X || !d_Phi || count < 1) return SMC_EINVAL;
     Ctx& c = ctx->c;
+    if (!device_visible(d_X) || !device_visible(d_Phi) || (d_w && !device_visible(d_w)))
+        return fail(ctx, SMC_EINVAL, "smc_forward: d_X, d_Phi and d_w must be device memory");
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "smc_forward: context not initialised");
     API_BEGIN
     const long long nc0 = c.nonconv;

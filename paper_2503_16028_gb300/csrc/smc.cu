@@ -286,6 +286,10 @@ extern "C" smc_status smc_resample_indices_static(const double* d_logw, int n_pa
         set_global_error("smc_resample_indices_static: n_particles must be in [1, SMC_STATIC_RESAMPLE_MAX] (32768)");
         return SMC_EINVAL;
     }
+    if (!device_visible(d_logw) || !device_visible(d_indices)) {
+        set_global_error("smc_resample_indices_static: d_logw and d_indices must be device memory");
+        return SMC_EINVAL;
+    }
     try {
         int dev = 0;
         check(cudaGetDevice(&dev), "cudaGetDevice");

@@ -44,6 +44,20 @@ __host__ __device__ inline double open53(uint32_t a, uint32_t b) {
 }
 
 struct Key { uint32_t k0, k1; };
+// False when CUDA reports `p` as host memory it does not know (an ordinary
+// malloc or stack address), which a kernel must not dereference.  Device,
+// managed and registered (mapped) host memory pass; so does a pointer whose
+// query fails, which leaves the decision to the caller's contract rather than
+// rejecting valid memory.
+inline bool device_visible(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return a.type != cudaMemoryTypeUnregistered;
+}
+
 inline Key key_of(unsigned long long seed) { return Key{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)}; }
 
 // ---------------------------------------------------------------------------

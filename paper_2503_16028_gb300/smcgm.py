@@ -113,6 +113,37 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _device_f64(t, count, name):
+    """Check that `t` is a contiguous float64 CUDA tensor with at least `count` elements (the
+    library's kernels read it as device memory)."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if str(t.dtype) != "torch.float64":
+        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < count:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), count))
+    return t
+
+
+def _host_f64(a, count, name):
+    """Check that `a` is a contiguous float64 host array (numpy or CPU tensor) with at least
+    `count` elements (the library copies it with cudaMemcpyAsync)."""
+    if getattr(a, "is_cuda", False):
+        raise ValueError("%s must be host memory" % name)
+    dt = str(a.dtype)
+    if dt not in ("float64", "torch.float64"):
+        raise ValueError("%s must be float64, got %s" % (name, dt))
+    contiguous = a.is_contiguous() if hasattr(a, "is_contiguous") else a.flags["C_CONTIGUOUS"]
+    if not contiguous:
+        raise ValueError("%s must be contiguous" % name)
+    n = a.numel() if hasattr(a, "numel") else a.size
+    if n < count:
+        raise ValueError("%s holds %d elements, %d needed" % (name, n, count))
+    return a
+
+
 def make_config(preset, **overrides):
     """smc_config from a dict (inputs.PRESETS entry merged with obs/data arrays); keeps the arrays alive."""
     lib = load_library()
@@ -200,6 +231,9 @@ class Sampler:
         return acc.value, it.value
 
     def smc_move_host(self, X_in, Phi_in, X_out, Phi_out):
+        for a, cnt, nm in ((X_in, self.N * self.d, "X_in"), (Phi_in, self.N, "Phi_in"),
+                           (X_out, self.N * self.d, "X_out"), (Phi_out, self.N, "Phi_out")):
+            _host_f64(a, cnt, nm)
         acc = ctypes.c_double()
         self._check(self.lib.smc_move_host(self.ctx, _ptr(X_in), _ptr(Phi_in), _ptr(X_out), _ptr(Phi_out),
                                            ctypes.byref(acc)), self.ctx)
@@ -214,6 +248,12 @@ class Sampler:
         return (mean, var, mg, vg) if grid else (mean, var)
 
     def smc_forward(self, X_dev, Phi_dev, w_dev=None):
+        count = int(X_dev.shape[0])
+        _device_f64(X_dev, count * self.d, "X_dev")
+        _device_f64(Phi_dev, count, "Phi_dev")
+        if w_dev is not None:
+            cells = (self.cfg.n ** 2) if self.cfg.dim == 2 else self.cfg.n - 1
+            _device_f64(w_dev, count * cells, "w_dev")
         it = ctypes.c_int()
         self._check(self.lib.smc_forward(self.ctx, _ptr(X_dev), int(X_dev.shape[0]), _ptr(Phi_dev), _ptr(w_dev),
                                          ctypes.byref(it)), self.ctx)
@@ -221,6 +261,10 @@ class Sampler:
 
     def smc_gradient(self, X_dev, Phi_dev, G_dev):
         """Phi(x) and dPhi/dx of the rows of X_dev (device tensors, FP64) into Phi_dev and G_dev."""
+        count = int(X_dev.shape[0])
+        _device_f64(X_dev, count * self.d, "X_dev")
+        _device_f64(Phi_dev, count, "Phi_dev")
+        _device_f64(G_dev, count * self.d, "G_dev")
         self._check(self.lib.smc_gradient(self.ctx, _ptr(X_dev), int(X_dev.shape[0]), _ptr(Phi_dev), _ptr(G_dev)), self.ctx)
 
     # --- state access ----------------------------------------------------
