@@ -8,6 +8,7 @@ import os
 import shutil
 import subprocess
 import sys
+import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -40,24 +41,31 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     exe = nvcc()
-    jobs = []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        jobs.append((src, obj, [exe] + ARCH + FLAGS + ["-c", src, "-o", obj]))
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
-        futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): src for src, _, cmd in jobs}
-        for f in cf.as_completed(futs):
-            res = f.result()
-            if res.returncode != 0:
-                raise RuntimeError("nvcc failed on %s:\n%s" % (futs[f], res.stderr[-4000:]))
-            if verbose and res.stderr.strip():
-                print(res.stderr)
-    tmp = LIB + ".tmp"
-    cmd = [exe] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + [o for _, o, _ in jobs]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("link failed:\n" + res.stderr[-4000:])
-    os.replace(tmp, LIB)
+    # objects and the linked library go to a directory private to this build, so builds
+    # started by several processes at once never link each other's half-written objects;
+    # the finished library replaces the old one atomically (same file system)
+    work = tempfile.mkdtemp(prefix="objs-", dir=BUILD)
+    try:
+        jobs = []
+        for src in sources():
+            obj = os.path.join(work, os.path.basename(src)[:-3] + ".o")
+            jobs.append((src, obj, [exe] + ARCH + FLAGS + ["-c", src, "-o", obj]))
+        with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+            futs = {ex.submit(subprocess.run, cmd, capture_output=True, text=True): src for src, _, cmd in jobs}
+            for f in cf.as_completed(futs):
+                res = f.result()
+                if res.returncode != 0:
+                    raise RuntimeError("nvcc failed on %s:\n%s" % (futs[f], res.stderr[-4000:]))
+                if verbose and res.stderr.strip():
+                    print(res.stderr)
+        tmp = os.path.join(work, os.path.basename(LIB))
+        cmd = [exe] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + [o for _, o, _ in jobs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("link failed:\n" + res.stderr[-4000:])
+        os.replace(tmp, LIB)
+    finally:
+        shutil.rmtree(work, ignore_errors=True)
     return LIB
 
 

@@ -53,3 +53,35 @@ def test_host_arguments():
         smcgm._host_f64(torch.zeros((3, 8), dtype=torch.float64)[:, ::2], 12, "X")
     with pytest.raises(ValueError, match="13 needed"):
         smcgm._host_f64(a, 13, "X")
+
+
+def test_concurrent_builds_use_private_objects(tmp_path, monkeypatch):
+    """Two builds at once (threads standing in for processes): no object file is written by
+    both, the library ends up in place, and the private directories are removed."""
+    import concurrent.futures as cf
+    import os
+    import subprocess
+    import threading
+    import time
+    from paper_2503_16028_gb300 import build
+    monkeypatch.setattr(build, "BUILD", str(tmp_path / "_build"))
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libsmcgm.so"))
+    monkeypatch.setattr(build, "nvcc", lambda: "nvcc")
+    written, lock = [], threading.Lock()
+
+    def fake_run(cmd, capture_output=True, text=True):
+        out = cmd[cmd.index("-o") + 1]
+        with lock:
+            written.append(out)
+        time.sleep(0.005)
+        with open(out, "w") as fh:
+            fh.write("x")
+        return subprocess.CompletedProcess(cmd, 0, "", "")
+
+    monkeypatch.setattr(build.subprocess, "run", fake_run)
+    with cf.ThreadPoolExecutor(2) as ex:
+        libs = list(ex.map(lambda _: build.build(force=True), range(2)))
+    objs = [o for o in written if o.endswith(".o")]
+    assert len(objs) == 2 * len(build.sources()) and len(set(objs)) == len(objs)
+    assert libs == [build.LIB, build.LIB] and os.path.exists(build.LIB)
+    assert os.listdir(build.BUILD) == []
