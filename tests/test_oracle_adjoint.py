@@ -82,3 +82,42 @@ def test_kl_gradient_matches_finite_differences(seed):
         e /= np.linalg.norm(e)
         fd = (prob.potential(x + eps * e) - prob.potential(x - eps * e)) / (2 * eps)
         assert abs(fd - grad @ e) <= 1e-6 * np.linalg.norm(grad), (fd, grad @ e)
+
+
+def test_face_derivatives_against_central_differences():
+    """The face coefficients are the harmonic means 2 k_a k_b / (k_a + k_b) (walls: 2 k_c), and
+    each derivative with respect to u = log k is the central difference of those faces: a
+    cell's own west/south face, its east/north neighbour's west/south face (as that face's
+    neighbour), and the east/north wall faces of the last column/row; no other face moves."""
+    rng = np.random.default_rng(31)
+    n, eps = 6, 1e-6
+    u = 0.7 * rng.standard_normal((n, n))
+    k = np.exp(u)
+    Kw, Ks, dWo, dWn, dSo, dSn, Ke, Kn = adjoint.face_derivatives(k)
+    assert np.allclose(Kw[:, 1:], 2 * k[:, 1:] * k[:, :-1] / (k[:, 1:] + k[:, :-1]), rtol=1e-14, atol=0)
+    assert np.allclose(Ks[1:, :], 2 * k[1:, :] * k[:-1, :] / (k[1:, :] + k[:-1, :]), rtol=1e-14, atol=0)
+    assert np.array_equal(Kw[:, 0], 2 * k[:, 0]) and np.array_equal(Ks[0, :], 2 * k[0, :])
+    assert np.array_equal(Ke, 2 * k[:, -1]) and np.array_equal(Kn, 2 * k[-1, :])
+    for j, i in [(2, 3), (0, 0), (5, 5), (0, 4), (3, 0), (5, 1)]:
+        up, um = u.copy(), u.copy()
+        up[j, i] += eps
+        um[j, i] -= eps
+        P = adjoint.face_derivatives(np.exp(up))
+        M = adjoint.face_derivatives(np.exp(um))
+        dKw, dKs = (P[0] - M[0]) / (2 * eps), (P[1] - M[1]) / (2 * eps)
+        dKe, dKn = (P[6] - M[6]) / (2 * eps), (P[7] - M[7]) / (2 * eps)
+        ew, es = np.zeros((n, n)), np.zeros((n, n))
+        ew[j, i] = dWo[j, i]
+        es[j, i] = dSo[j, i]
+        if i + 1 < n:
+            ew[j, i + 1] = dWn[j, i + 1]
+        if j + 1 < n:
+            es[j + 1, i] = dSn[j + 1, i]
+        assert np.allclose(dKw, ew, rtol=1e-8, atol=1e-9), (j, i)
+        assert np.allclose(dKs, es, rtol=1e-8, atol=1e-9), (j, i)
+        ee, en = np.zeros(n), np.zeros(n)
+        if i == n - 1:
+            ee[j] = Ke[j]
+        if j == n - 1:
+            en[i] = Kn[i]
+        assert np.allclose(dKe, ee, rtol=1e-8, atol=1e-9) and np.allclose(dKn, en, rtol=1e-8, atol=1e-9), (j, i)

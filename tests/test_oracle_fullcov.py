@@ -97,3 +97,19 @@ def test_recovers_correlated_mixture_and_loglik_monotone():
     assert mix.w[j1] == pytest.approx(0.35, abs=0.01)
     assert np.allclose(mix.m[j1], [1.0, 0.0], atol=0.01) and np.allclose(mix.m[j2], [-1.0, 0.5], atol=0.01)
     assert np.allclose(mix.cov[j1], C1, atol=0.004) and np.allclose(mix.cov[j2], C2, atol=0.004)
+
+
+def test_full_e_step_against_scipy_densities():
+    """Responsibilities g_nj = w_j N(x_n; m_j, C_j) / sum_k w_k N(x_n; m_k, C_k) and the
+    log-likelihood sum_n log sum_j w_j N(x_n; m_j, C_j), with the densities from scipy."""
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(8)
+    N, r, K = 40, 5, 3
+    xs = rng.standard_normal((N, r))
+    w = rng.dirichlet(np.ones(K))
+    m = 0.5 * rng.standard_normal((K, r))
+    cov = np.stack([_spd(r, rng, 0.8) for _ in range(K)])
+    g, ll = gm.e_step_full(xs, w, m, cov)
+    dens = np.stack([w[j] * stats.multivariate_normal(m[j], cov[j]).pdf(xs) for j in range(K)], axis=1)
+    assert np.allclose(g, dens / dens.sum(axis=1, keepdims=True), rtol=1e-12, atol=1e-15)
+    assert ll == pytest.approx(float(np.sum(np.log(dens.sum(axis=1)))), rel=1e-12)
