@@ -1,0 +1,205 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in one oracle function on the CPU (monkeypatched
+for the duration of the case: a dropped term, a wrong sign, an operand
+transposed, an off-by-one, a wrong mean or scale), runs the pins written for
+that function, and requires at least one of them to fail with an assertion.
+The oracle's own functions look each other up through their module, so a
+planted mistake also reaches the functions built on it.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint, darcy, gm, langevin, observe, pcngm, prior, smc
+
+import test_oracle_adjoint as t_adj
+import test_oracle_darcy as t_darcy
+import test_oracle_fullcov as t_full
+import test_oracle_gm as t_gm
+import test_oracle_langevin as t_lang
+import test_oracle_observe as t_obs
+import test_oracle_pcngm as t_pcngm
+import test_oracle_prior as t_prior
+import test_oracle_smc as t_smc
+
+
+# --- the planted mistakes (each takes the original function) ------------------------------
+
+def log_r_without_logdet(orig):
+    def f(b, a, mix, beta):
+        out = orig(b, a, mix, beta)
+        if mix.cov is None:
+            l0 = mix.lam0[mix.S]
+            out = out - np.array([np.sum(0.5 * np.log(l0 / mix.lam[j])) for j in range(mix.K)])
+        return out
+    return f
+
+
+def propose_shift_gamma(orig):
+    def f(u, j, z, mix, beta):
+        v = orig(u, j, z, mix, beta)
+        g = pcngm.gamma_of(beta)
+        v[mix.S] += (2.0 * g - 1.0) * mix.m[j]          # gamma m_j instead of (1 - gamma) m_j
+        return v
+    return f
+
+
+def propose_full_with_covariance(orig):
+    def f(u, j, z, mix, beta):
+        if mix.cov is None:
+            return orig(u, j, z, mix, beta)
+        v = orig(u, j, z, mix, beta)
+        L = np.linalg.cholesky(mix.cov[j])
+        v[mix.S] += beta * ((mix.cov[j] - L) @ z[mix.S])   # C_j z instead of L_j z
+        return v
+    return f
+
+
+def ess_without_square(orig):
+    def f(phi, h):
+        e = np.exp(-h * (phi - np.min(phi)))
+        return np.sum(e) / np.sum(e * e)
+    return f
+
+
+def log_z_without_mean(orig):
+    def f(phi, h):
+        return orig(phi, h) + np.log(phi.shape[0])
+    return f
+
+
+def systematic_strict_walk(orig):
+    def f(logw, u48):
+        N = len(logw)
+        cdf = smc.fixed_point_cdf(smc.normalised_weights(np.asarray(logw, dtype=np.float64)))
+        out = np.empty(N, dtype=np.int64)
+        i = 0
+        for k in range(N):
+            target = k * smc.RESAMPLE_T + u48
+            while i < N - 1 and N * cdf[i] < target:      # '<' where the walk needs '<='
+                i += 1
+            out[k] = i
+        return out
+    return f
+
+
+def arithmetic_faces(orig):
+    def f(kc):
+        kc = np.asarray(kc, dtype=np.float64)
+        Kw = np.zeros_like(kc)
+        Ks = np.zeros_like(kc)
+        Kw[..., :, 1:] = 0.5 * (kc[..., :, 1:] + kc[..., :, :-1])
+        Ks[..., 1:, :] = 0.5 * (kc[..., 1:, :] + kc[..., :-1, :])
+        D = Kw.copy()
+        D[..., :, :-1] += Kw[..., :, 1:]
+        D += Ks
+        D[..., :-1, :] += Ks[..., 1:, :]
+        D[..., :, 0] += 2.0 * kc[..., :, 0]
+        D[..., :, -1] += 2.0 * kc[..., :, -1]
+        D[..., 0, :] += 2.0 * kc[..., 0, :]
+        D[..., -1, :] += 2.0 * kc[..., -1, :]
+        return Kw, Ks, D
+    return f
+
+
+def observe_transposed(orig):
+    def f(w, obs_xy):
+        return orig(w, np.ascontiguousarray(np.asarray(obs_xy)[:, ::-1]))
+    return f
+
+
+def eigenvalues_first_power(orig):
+    def f(Km, alpha):
+        return orig(Km, alpha) ** 0.5                   # (1 + alpha mu)^-1 instead of ^-2
+    return f
+
+
+def gradient_without_walls(orig):
+    def f(kc, w, lam):
+        g = orig(kc, w, lam)
+        Kw, Ks, dWo, dWn, dSo, dSn, Ke, Kn = adjoint.face_derivatives(kc)
+        g[:, 0] += dWo[:, 0] * lam[:, 0] * w[:, 0]
+        g[0, :] += dSo[0, :] * lam[0, :] * w[0, :]
+        g[:, -1] += Ke * lam[:, -1] * w[:, -1]
+        g[-1, :] += Kn * lam[-1, :] * w[-1, :]
+        return g
+    return f
+
+
+def e_step_without_normaliser(orig):
+    def f(xs, w, m, lam):
+        N, K = xs.shape[0], w.shape[0]
+        logp = np.empty((N, K))
+        for j in range(K):
+            logp[:, j] = np.log(w[j]) + np.sum(-(xs - m[j]) ** 2 / (2.0 * lam[j]), axis=1)
+        mx = np.max(logp, axis=1, keepdims=True)
+        lse = mx[:, 0] + np.log(np.sum(np.exp(logp - mx), axis=1))
+        return np.exp(logp - lse[:, None]), float(np.sum(lse))
+    return f
+
+
+def rho_sign_flipped(orig):
+    def f(a, b, g_a, lam, beta, t):
+        gm_ = langevin.gamma_of(beta)
+        k = (1.0 - gm_) * t
+        return k * float(g_a @ (b - gm_ * a)) / beta ** 2 - k * k * float(g_a @ (lam * g_a)) / (2.0 * beta ** 2)
+    return f
+
+
+def langevin_drift_without_t(orig):
+    def f(x, g, lam, beta, t, z):
+        return orig(x, g, lam, beta, 1.0 if t != 0.0 else 0.0, z)
+    return f
+
+
+CASES = {
+    "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
+                                        [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
+                                         t_pcngm.test_beta_one_is_independence_sampler_ratio]),
+    "proposal shifts by gamma m_j": (pcngm, "propose", propose_shift_gamma,
+                                     [t_pcngm.test_proposal_mean_and_components]),
+    "full-covariance proposal scales by C_j": (pcngm, "propose", propose_full_with_covariance,
+                                               [t_full.test_diagonal_covariance_is_the_diagonal_kernel]),
+    "ESS without the square": (smc, "ess_of_h", ess_without_square,
+                               [t_smc.test_ess_limits_and_monotonicity, t_smc.test_bisection_brackets_target]),
+    "log Z increment without -log N": (smc, "log_z_increment", log_z_without_mean,
+                                       [t_smc.test_log_z_increment_direct_sum]),
+    "resampling walk off by one": (smc, "systematic_indices", systematic_strict_walk,
+                                   [t_smc.test_systematic_resampling_brute_force,
+                                    t_smc.test_equal_weights_identity_and_extremes]),
+    "arithmetic instead of harmonic faces": (darcy, "face_coefficients", arithmetic_faces,
+                                             [t_darcy.test_assembled_operator_matches_flux_definition,
+                                              t_adj.test_face_derivatives_against_central_differences]),
+    "observation with x and y swapped": (observe, "observe_2d", observe_transposed,
+                                         [t_obs.test_cell_centre_points_select_exactly,
+                                          t_obs.test_bilinear_reproduces_affine_fields_inside]),
+    "prior eigenvalues to the first power": (prior, "eigenvalues_2d", eigenvalues_first_power,
+                                             [t_prior.test_cosine_modes_are_neumann_laplacian_eigenfunctions]),
+    "adjoint gradient drops the wall faces": (adjoint, "grad_u_from_adjoint", gradient_without_walls,
+                                              [t_adj.test_grid_gradient_matches_finite_differences_per_cell]),
+    "E-step without the Gaussian normaliser": (gm, "e_step", e_step_without_normaliser,
+                                               [t_gm.test_recovers_separated_mixture_and_loglik_monotone]),
+    "Langevin ratio with the drift term's sign flipped": (langevin, "rho", rho_sign_flipped,
+                                                          [lambda: t_lang.test_detailed_balance_direct_densities(0.3, 0.2)]),
+    "Langevin drift without the temperature": (langevin, "propose", langevin_drift_without_t,
+                                               [t_lang.test_propose_is_mean_plus_scaled_noise]),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_a_pin_catches_the_planted_mistake(case, monkeypatch):
+    module, name, plant, pins = CASES[case]
+    monkeypatch.setattr(module, name, plant(getattr(module, name)))
+    caught = []
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught.append(getattr(pin, "__name__", "pin"))
+    assert caught, "no pin caught: %s" % case
+
+
+def test_the_pins_pass_on_the_unmodified_oracle():
+    for case, (_, _, _, pins) in CASES.items():
+        for pin in pins:
+            pin()

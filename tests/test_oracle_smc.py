@@ -73,6 +73,10 @@ def test_equal_weights_identity_and_extremes():
     for N in (1, 5, 64):
         assert list(smc.systematic_indices(np.zeros(N), 12345)) == list(range(N))
         assert list(smc.systematic_indices(np.zeros(N), smc.RESAMPLE_T - 1)) == list(range(N))
+    # N a power of two: the fixed-point CDF is exact, so with the smallest uniform every
+    # systematic point (k + 2^-49)/N lies just above a CDF boundary and must still map to k
+    for N in (2, 8, 64):
+        assert list(smc.systematic_indices(np.zeros(N), 0)) == list(range(N))
     logw = np.array([0.0, -800.0, -800.0])
     assert list(smc.systematic_indices(logw, 7)) == [0, 0, 0]
 
