@@ -152,6 +152,57 @@ def langevin_drift_without_t(orig):
     return f
 
 
+def potential_without_half(orig):
+    def f(y, data, sigma):
+        return 2.0 * orig(y, data, sigma)
+    return f
+
+
+def cosine_basis_without_sqrt2(orig):
+    def f(n, Km):
+        B = orig(n, Km).copy()
+        B[:, 1:] /= np.sqrt(2.0)
+        return B
+    return f
+
+
+def analysis_transposed(orig):
+    def f(g, Km):
+        return orig(np.swapaxes(np.asarray(g), -1, -2), Km)
+    return f
+
+
+def accept_comparison_flipped(orig):
+    def f(log_a, U):
+        return bool(log_a >= 0.0 or np.log(U) > log_a)
+    return f
+
+
+def beta_rule_thresholds_swapped(orig):
+    def f(beta, acc_rate):
+        if acc_rate < 0.15:
+            beta = 2.0 * beta
+        elif acc_rate > 0.3:
+            beta = 0.5 * beta
+        return min(beta, 1.0)
+    return f
+
+
+def solve_without_h2(orig):
+    def f(u, f_):
+        n = u.shape[0]
+        return orig(u, f_) * (n * n)
+    return f
+
+
+def gm_log_R_without_base(orig):
+    def f(b, a, g_a, mix, beta, t):
+        gm_ = langevin.gamma_of(beta)
+        q0 = -0.5 * np.sum((b - gm_ * a) ** 2 / (beta ** 2 * mix.lam0) + np.log(beta ** 2 * mix.lam0))
+        return orig(b, a, g_a, mix, beta, t) + q0
+    return f
+
+
 CASES = {
     "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
                                         [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
@@ -183,6 +234,20 @@ CASES = {
                                                           [lambda: t_lang.test_detailed_balance_direct_densities(0.3, 0.2)]),
     "Langevin drift without the temperature": (langevin, "propose", langevin_drift_without_t,
                                                [t_lang.test_propose_is_mean_plus_scaled_noise]),
+    "potential without the 1/2": (observe, "potential", potential_without_half, [t_obs.test_potential]),
+    "cosine basis without sqrt 2": (prior, "cosine_basis_1d", cosine_basis_without_sqrt2,
+                                    [t_prior.test_basis_orthonormal_on_cell_centres,
+                                     t_prior.test_synthesis_against_pointwise_sum]),
+    "analysis with the grid transposed": (adjoint, "analysis_2d", analysis_transposed,
+                                          [t_adj.test_analysis_is_transpose_of_synthesis]),
+    "accept test inverted": (pcngm, "accept", accept_comparison_flipped,
+                             [t_pcngm.test_accept_with_probability_min_one_alpha]),
+    "beta rule thresholds swapped": (smc, "beta_rule", beta_rule_thresholds_swapped, [t_smc.test_beta_rule_table]),
+    "Darcy solve without the h^2 scaling": (darcy, "solve_2d", solve_without_h2,
+                                            [t_darcy.test_manufactured_solution_second_order]),
+    "GM-Langevin ratio without the pCN base density": (langevin, "gm_log_R", gm_log_R_without_base,
+                                                       [lambda: t_lang.test_gm_detailed_balance_direct_densities(0.3, 0.2),
+                                                        t_lang.test_gm_special_cases]),
 }
 
 

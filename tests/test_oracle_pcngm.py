@@ -141,3 +141,18 @@ def test_kernel_leaves_prior_invariant_when_potential_is_zero():
     assert 0.05 < acc / (M * steps) < 0.95
     for i in range(2):
         assert stats.kstest(X[:, i] / np.sqrt(lam0[i]), "norm").pvalue > 1e-3
+
+
+def test_accept_with_probability_min_one_alpha():
+    """The Metropolis-Hastings rule: a move with ratio alpha is taken with probability
+    min(1, alpha).  Over 40000 uniforms the accepted fraction matches it to 4 binomial
+    standard deviations; concrete cases on either side of alpha = 0.3; alpha >= 1 always."""
+    rng = np.random.default_rng(17)
+    U = rng.random(40000)
+    for alpha in (0.02, 0.3, 0.75, 1.0, 3.0):
+        frac = np.mean([pcngm.accept(np.log(alpha), u) for u in U])
+        p = min(1.0, alpha)
+        assert abs(frac - p) <= 4 * np.sqrt(max(p * (1 - p), 1e-12) / U.size) + 1e-12, (alpha, frac)
+    assert pcngm.accept(np.log(0.3), 0.2) and not pcngm.accept(np.log(0.3), 0.4)
+    assert pcngm.accept(0.0, 0.999999) and pcngm.accept(2.0, 0.5)
+    assert not pcngm.accept(-np.inf, 1e-300)
