@@ -203,6 +203,31 @@ def gm_log_R_without_base(orig):
     return f
 
 
+def sample_variance(orig):
+    def f(X):
+        m, v = orig(X)
+        N = X.shape[0]
+        return m, v * N / (N - 1)
+    return f
+
+
+def component_draw_closed_on_the_right(orig):
+    def f(w, U):
+        c = 0.0
+        for j, wj in enumerate(w):
+            c += wj
+            if U <= c:
+                return j
+        return len(w) - 1
+    return f
+
+
+def init_indices_with_repeats(orig):
+    def f(seed, layer, N, K):
+        return [int((int(smc.philox.word32(seed, k, 0, layer, smc.philox.EMINIT)) * N) >> 32) for k in range(K)]
+    return f
+
+
 CASES = {
     "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
                                         [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
@@ -245,6 +270,12 @@ CASES = {
     "beta rule thresholds swapped": (smc, "beta_rule", beta_rule_thresholds_swapped, [t_smc.test_beta_rule_table]),
     "Darcy solve without the h^2 scaling": (darcy, "solve_2d", solve_without_h2,
                                             [t_darcy.test_manufactured_solution_second_order]),
+    "posterior variance with divisor N - 1": (smc, "posterior_moments", sample_variance,
+                                              [t_smc.test_posterior_moments_closed_form]),
+    "component draw closed on the right": (pcngm, "choose_component", component_draw_closed_on_the_right,
+                                           [t_pcngm.test_component_draw_at_the_cumulative_boundaries]),
+    "EM initial particles may repeat": (gm, "init_indices", init_indices_with_repeats,
+                                        [t_gm.test_init_indices_distinct]),
     "GM-Langevin ratio without the pCN base density": (langevin, "gm_log_R", gm_log_R_without_base,
                                                        [lambda: t_lang.test_gm_detailed_balance_direct_densities(0.3, 0.2),
                                                         t_lang.test_gm_special_cases]),

@@ -156,3 +156,12 @@ def test_accept_with_probability_min_one_alpha():
     assert pcngm.accept(np.log(0.3), 0.2) and not pcngm.accept(np.log(0.3), 0.4)
     assert pcngm.accept(0.0, 0.999999) and pcngm.accept(2.0, 0.5)
     assert not pcngm.accept(-np.inf, 1e-300)
+
+
+def test_component_draw_at_the_cumulative_boundaries():
+    """j = min{j : U < w_1 + ... + w_j}: the intervals [c_{j-1}, c_j) are closed on the left,
+    so a uniform exactly on a boundary (binary fractions make the sums exact) belongs to the
+    next component; the last component takes the rest."""
+    w = np.array([0.25, 0.25, 0.5])
+    assert [pcngm.choose_component(w, u) for u in (0.0, 0.2499, 0.25, 0.4999, 0.5, 0.75, 0.9999)] == [0, 0, 1, 1, 2, 2, 2]
+    assert pcngm.choose_component(np.array([0.5, 0.5]), 0.5) == 1

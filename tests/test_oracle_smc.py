@@ -85,3 +85,17 @@ def test_beta_rule_table():
     for (acc, out) in [(0.31, 0.4), (0.3, 0.2), (0.2, 0.2), (0.15, 0.2), (0.149, 0.1), (0.0, 0.1)]:
         assert smc.beta_rule(0.2, acc) == out
     assert smc.beta_rule(0.8, 0.9) == 1.0
+
+
+def test_posterior_moments_closed_form():
+    """Mean and population variance (divisor N) of the particles: two particles per
+    coordinate pair give mean (a + b)/2 and variance ((a - b)/2)^2; an affine map of the
+    particles maps the moments as c mean + s and c^2 var."""
+    X = np.array([[1.0, 2.0, -5.0], [3.0, 6.0, -5.0]])
+    m, v = smc.posterior_moments(X)
+    assert np.array_equal(m, [2.0, 4.0, -5.0]) and np.array_equal(v, [1.0, 4.0, 0.0])
+    rng = np.random.default_rng(9)
+    Y = rng.standard_normal((50, 4))
+    m1, v1 = smc.posterior_moments(Y)
+    m2, v2 = smc.posterior_moments(-3.0 * Y + 0.5)
+    assert np.allclose(m2, -3.0 * m1 + 0.5, rtol=1e-13) and np.allclose(v2, 9.0 * v1, rtol=1e-13)
