@@ -10,7 +10,7 @@ planted mistake also reaches the functions built on it.
 import numpy as np
 import pytest
 
-from oracle import adjoint, darcy, gm, langevin, observe, pcngm, prior, smc
+from oracle import adjoint, darcy, gm, langevin, observe, pcngm, philox, prior, smc
 
 import test_oracle_adjoint as t_adj
 import test_oracle_darcy as t_darcy
@@ -18,6 +18,7 @@ import test_oracle_fullcov as t_full
 import test_oracle_gm as t_gm
 import test_oracle_langevin as t_lang
 import test_oracle_observe as t_obs
+import test_oracle_philox as t_philox
 import test_oracle_pcngm as t_pcngm
 import test_oracle_prior as t_prior
 import test_oracle_smc as t_smc
@@ -228,6 +229,73 @@ def init_indices_with_repeats(orig):
     return f
 
 
+def bisection_returns_upper_bracket(orig):
+    def f(phi, t, target, iters=64):
+        rest = 1.0 - t
+        if smc.ess_of_h(phi, rest) >= target:
+            return rest
+        lo, hi = 0.0, rest
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            if smc.ess_of_h(phi, mid) >= target:
+                lo = mid
+            else:
+                hi = mid
+        return hi
+    return f
+
+
+def prior_draw_without_sqrt(orig):
+    def f(seed, lam, n):
+        return orig(seed, lam, n) / np.sqrt(lam)
+    return f
+
+
+def solve_1d_without_h2(orig):
+    def f(u_mid, f_nodes):
+        n = u_mid.shape[0]
+        return orig(u_mid, f_nodes) * (n * n)
+    return f
+
+
+def sine_basis_at_nodes(orig):
+    def f(n, Km):
+        x = np.arange(n) / n
+        return np.sqrt(2.0) * np.sin(np.pi * np.outer(x, np.arange(1, Km + 1)))
+    return f
+
+
+def observe_1d_shifted(orig):
+    def f(w_interior, obs_x):
+        n = w_interior.shape[-1] + 1
+        return orig(w_interior, np.clip(np.asarray(obs_x) + 0.5 / n, 0.0, 1.0))
+    return f
+
+
+def gm_propose_prior_noise(orig):
+    def f(x, g, j, z, mix, beta, t):
+        v = orig(x, g, j, z, mix, beta, t)
+        lamj = mix.lam0.copy()
+        lamj[mix.S] = mix.lam[j]
+        return v + beta * (np.sqrt(mix.lam0) - np.sqrt(lamj)) * z
+    return f
+
+
+def box_muller_half_angle(orig):
+    def f(seed, npairs, c1, c2, purpose):
+        k0, k1 = philox.key_of(seed)
+        m = np.arange(npairs, dtype=np.uint64)
+        w = philox.philox4x32_10(m, c1, c2, purpose, k0, k1)
+        u1 = philox.uniform_open(w[0], w[1])
+        u2 = philox.uniform_open(w[2], w[3])
+        r = np.sqrt(-2.0 * np.log(u1))
+        z = np.empty(2 * npairs)
+        z[0::2] = r * np.cos(np.pi * u2)                 # pi where the angle needs 2 pi
+        z[1::2] = r * np.sin(np.pi * u2)
+        return z
+    return f
+
+
 CASES = {
     "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
                                         [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
@@ -276,6 +344,19 @@ CASES = {
                                            [t_pcngm.test_component_draw_at_the_cumulative_boundaries]),
     "EM initial particles may repeat": (gm, "init_indices", init_indices_with_repeats,
                                         [t_gm.test_init_indices_distinct]),
+    "bisection returns the upper bracket": (smc, "bisect_h", bisection_returns_upper_bracket,
+                                            [t_smc.test_bisection_brackets_target]),
+    "prior draw without sqrt(lambda)": (smc, "prior_draw", prior_draw_without_sqrt,
+                                        [t_smc.test_prior_draws_have_the_prior_moments]),
+    "1D solve without the h^2 scaling": (darcy, "solve_1d", solve_1d_without_h2,
+                                         [t_darcy.test_manufactured_solution_1d_second_order]),
+    "1D synthesis at the nodes instead of the midpoints": (prior, "sine_basis_midpoints", sine_basis_at_nodes,
+                                                           [t_prior.test_synthesis_1d_against_pointwise_sum]),
+    "1D observation half a cell off": (observe, "observe_1d", observe_1d_shifted, [t_obs.test_linear_1d]),
+    "GM-Langevin noise with the prior variances": (langevin, "gm_propose", gm_propose_prior_noise,
+                                                   [t_lang.test_gm_propose_is_component_mean_plus_scaled_noise]),
+    "Box-Muller angle pi instead of 2 pi": (philox, "normal_pairs", box_muller_half_angle,
+                                            [t_philox.test_normals_distribution]),
     "GM-Langevin ratio without the pCN base density": (langevin, "gm_log_R", gm_log_R_without_base,
                                                        [lambda: t_lang.test_gm_detailed_balance_direct_densities(0.3, 0.2),
                                                         t_lang.test_gm_special_cases]),

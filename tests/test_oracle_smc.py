@@ -99,3 +99,14 @@ def test_posterior_moments_closed_form():
     m1, v1 = smc.posterior_moments(Y)
     m2, v2 = smc.posterior_moments(-3.0 * Y + 0.5)
     assert np.allclose(m2, -3.0 * m1 + 0.5, rtol=1e-13) and np.allclose(v2, 9.0 * v1, rtol=1e-13)
+
+
+def test_prior_draws_have_the_prior_moments():
+    """x_n = sqrt(lambda) z_n: over 20000 particles the coordinates have mean 0 and variance
+    lambda (4 standard errors), and draws of different particles are uncorrelated."""
+    lam = np.array([1.0, 0.25, 0.04, 1e-4])
+    N = 20000
+    X = np.stack([smc.prior_draw(7, lam, n) for n in range(N)])
+    assert np.all(np.abs(X.mean(axis=0)) < 4 * np.sqrt(lam / N))
+    assert np.all(np.abs(X.var(axis=0) / lam - 1.0) < 4 * np.sqrt(2.0 / N))
+    assert abs(np.corrcoef(X[:-1, 0], X[1:, 0])[0, 1]) < 4 / np.sqrt(N)
