@@ -1,6 +1,6 @@
 """Writes tests/golden/workload_<name>.json: observation points, the synthetic
-truth (a prior draw, as in Sec. 3.2 "an underlying true signal sampled from the
-prior") and its noisy observations, computed with the oracle only.
+truth (a prior draw: Sec. 3.2 takes its true field from the prior) and its noisy
+observations, computed with the oracle only.
 
 To avoid the inverse crime (Sec. 3.2) the data come from a grid refined by the
 preset's ``data_refine`` factor; noise is sigma * N(0, 1) from Philox purpose
