@@ -15,6 +15,7 @@ Every candidate meets the same FP64 tolerance, so the choice changes speed,
 not the answer beyond that tolerance.
 """
 import concurrent.futures as cf
+import json
 import time
 
 import numpy as np
@@ -22,19 +23,41 @@ import numpy as np
 from . import smcgm
 
 
-def run_smc(sampler, mcmc_steps, max_layers=200):
+def run_smc(sampler, mcmc_steps, max_layers=200, log=None):
     """Alg. 1 on one context until t = 1: reweight (ESS bisection), resample,
     fit the mixture, move.  Returns the per-layer (h, ess, log Z increment,
-    acceptance) and the final particles."""
+    acceptance) and the final particles.
+
+    log: None, a file path or a writable text file.  With a log, each layer
+    appends one JSON object: layer index, temperature t and step h, ESS, log Z
+    increment, mixture log-likelihood, the beta the moves used, acceptance, the
+    largest CG iteration count, CG iterations and refinement phases per solve,
+    and the solves of the layer (the library's counters, reset per layer)."""
     layers = []
-    for _ in range(max_layers):
-        h, ess, lz, done = sampler.smc_temper_step()
-        sampler.smc_resample()
-        sampler.gm_fit()
-        acc, _ = sampler.smc_move(mcmc_steps, allow_noconv=True)
-        layers.append(dict(h=h, ess=ess, logz=lz, acc=acc))
-        if done:
-            break
+    fh = open(log, "a") if isinstance(log, str) else log
+    try:
+        for _ in range(max_layers):
+            h, ess, lz, done = sampler.smc_temper_step()
+            sampler.smc_resample()
+            ll = sampler.gm_fit()
+            if fh is not None:
+                t, beta, layer, _ = sampler.smc_get_schedule()
+                sampler.smc_profile_query(reset=True)
+            acc, it_max = sampler.smc_move(mcmc_steps, allow_noconv=True)
+            layers.append(dict(h=h, ess=ess, logz=lz, acc=acc))
+            if fh is not None:
+                prof = sampler.smc_profile_query(reset=True)
+                solves = max(1, prof["solves"])
+                fh.write(json.dumps(dict(layer=layer, t=t, h=h, ess=ess, log_z_increment=lz, gm_loglik=ll, beta=beta,
+                                         acceptance=acc, cg_max=it_max, cg_per_solve=prof["cg_iterations"] / solves,
+                                         refinements_per_solve=prof["inner_solves"] / solves,
+                                         solves=prof["solves"])) + "\n")
+                fh.flush()
+            if done:
+                break
+    finally:
+        if isinstance(log, str) and fh is not None:
+            fh.close()
     X, Phi = sampler.particles()
     return dict(layers=layers, X=X, Phi=Phi)
 
