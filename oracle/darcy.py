@@ -1,5 +1,5 @@
 """Forward PDE of Sec. 3.2 (eq. example2:PDE): -div(e^u grad w) = f on (0,1)^2,
-w = 0 on the boundary; and the 1D analogue of config 1, -(e^u w')' = f on
+w = 0 on the boundary; and its 1D analogue (the 128-interval elliptic workload), -(e^u w')' = f on
 [0, 1], w(0) = w(1) = 0.  The paper states no discretisation.  Readings:
 
 2D, cell-centred finite volumes on an n x n grid, h = 1/n:
