@@ -296,6 +296,40 @@ def box_muller_half_angle(orig):
     return f
 
 
+def observation_matrix_transposed(orig):
+    def f(n, obs_xy):
+        perm = np.arange(n * n).reshape(n, n).T.ravel()
+        return orig(n, obs_xy)[:, perm]                 # column i n + j where the grid is j n + i
+    return f
+
+
+def full_e_step_logdet_sign(orig):
+    def f(xs, w, m, cov):
+        N, r = xs.shape
+        logp = np.empty((N, w.shape[0]))
+        for j in range(w.shape[0]):
+            _, logdet = np.linalg.slogdet(cov[j])
+            dev = xs - m[j]
+            q = np.sum(dev * np.linalg.solve(cov[j], dev.T).T, axis=1)
+            logp[:, j] = np.log(w[j]) - 0.5 * (r * np.log(2.0 * np.pi) - logdet) - 0.5 * q
+        mx = np.max(logp, axis=1, keepdims=True)
+        lse = mx[:, 0] + np.log(np.sum(np.exp(logp - mx), axis=1))
+        return np.exp(logp - lse[:, None]), float(np.sum(lse))
+    return f
+
+
+def mh_potential_sign(orig):
+    def f(t, phi_u, phi_v, log_ratio):
+        return t * (phi_v - phi_u) + log_ratio
+    return f
+
+
+def langevin_alpha_without_t(orig):
+    def f(x, v, phi_x, phi_v, g_x, g_v, lam, beta, t):
+        return orig(x, v, phi_x, phi_v, g_x, g_v, lam, beta, t) + (1.0 - t) * (phi_x - phi_v)
+    return f
+
+
 CASES = {
     "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
                                         [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
@@ -357,6 +391,14 @@ CASES = {
                                                    [t_lang.test_gm_propose_is_component_mean_plus_scaled_noise]),
     "Box-Muller angle pi instead of 2 pi": (philox, "normal_pairs", box_muller_half_angle,
                                             [t_philox.test_normals_distribution]),
+    "observation matrix with the grid transposed": (adjoint, "observation_matrix_2d", observation_matrix_transposed,
+                                                    [t_adj.test_observation_matrix_matches_operator]),
+    "full-covariance E-step with the log-determinant's sign flipped": (gm, "e_step_full", full_e_step_logdet_sign,
+                                                                       [t_full.test_full_e_step_against_scipy_densities]),
+    "MH ratio with the potential difference reversed": (pcngm, "log_alpha", mh_potential_sign,
+                                                        [t_pcngm.test_log_alpha_is_detailed_balance_for_the_tempered_target]),
+    "Langevin ratio without the temperature on Phi": (langevin, "log_alpha", langevin_alpha_without_t,
+                                                      [lambda: t_lang.test_detailed_balance_direct_densities(0.3, 0.2)]),
     "GM-Langevin ratio without the pCN base density": (langevin, "gm_log_R", gm_log_R_without_base,
                                                        [lambda: t_lang.test_gm_detailed_balance_direct_densities(0.3, 0.2),
                                                         t_lang.test_gm_special_cases]),

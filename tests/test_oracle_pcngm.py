@@ -165,3 +165,36 @@ def test_component_draw_at_the_cumulative_boundaries():
     w = np.array([0.25, 0.25, 0.5])
     assert [pcngm.choose_component(w, u) for u in (0.0, 0.2499, 0.25, 0.4999, 0.5, 0.75, 0.9999)] == [0, 0, 1, 1, 2, 2, 2]
     assert pcngm.choose_component(np.array([0.5, 0.5]), 0.5) == 1
+
+
+def test_log_alpha_is_detailed_balance_for_the_tempered_target():
+    """log alpha(u, v) = [log pi_t(v) + log Q(v, u)] - [log pi_t(u) + log Q(u, v)] for the
+    tempered target pi_t(x) ~ exp(-t Phi(x)) N(x; 0, C) and the mixture proposal
+    Q(u, .) = sum_j w_j N(gamma u + (1 - gamma) m_j, beta^2 C_j), all densities written out
+    (a quadratic Phi, so that Phi(u) and Phi(v) differ)."""
+    rng = np.random.default_rng(23)
+    d = 5
+    lam0 = rng.uniform(0.2, 1.5, d)
+    S = np.array([0, 1, 2])
+    mix = _random_mixture(rng, lam0, S, 3)
+    H = rng.standard_normal((4, d))
+    phi = lambda x: 0.5 * float(np.sum((H @ x - 0.3) ** 2))
+    for t, beta in ((0.2, 0.3), (0.9, 0.7)):
+        g = pcngm.gamma_of(beta)
+
+        def log_q(a, b):
+            terms = []
+            for j in range(3):
+                lj = lam0.copy(); lj[S] = mix.lam[j]
+                mean = g * a.copy(); mean[S] += (1 - g) * mix.m[j]
+                terms.append(np.log(mix.w[j]) + stats.multivariate_normal(mean, beta ** 2 * np.diag(lj)).logpdf(b))
+            return pcngm.logsumexp(np.array(terms))
+
+        def log_pi(x):
+            return -t * phi(x) + stats.multivariate_normal(np.zeros(d), np.diag(lam0)).logpdf(x)
+
+        for _ in range(4):
+            u, v = np.sqrt(lam0) * rng.standard_normal(d), np.sqrt(lam0) * rng.standard_normal(d)
+            direct = (log_pi(v) + log_q(v, u)) - (log_pi(u) + log_q(u, v))
+            la = pcngm.log_alpha(t, phi(u), phi(v), pcngm.log_mixture_ratio(u, v, mix, beta))
+            assert abs(la - direct) <= 1e-10 * max(1.0, abs(direct)), (la, direct)
