@@ -67,7 +67,7 @@ struct WGeo {
 // side, east side; 8 quads each).  Otherwise the whole ring as the band of
 // lowest rows, the band of highest rows and the two side bands.
 template <int H>
-__device__ inline void quad_pos(int qi, int& qx, int& qy) {
+__host__ __device__ inline void quad_pos(int qi, int& qx, int& qy) {
     constexpr int QW = (WT + 2 * H) / 2, HB = H / 2, IQ = WT / 2;
     if (qi < IQ * IQ) { qx = HB + qi % IQ; qy = HB + qi / IQ; return; }
     int h = qi - IQ * IQ;
