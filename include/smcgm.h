@@ -81,7 +81,7 @@ typedef enum { SMC_P_FP64 = 0, SMC_P_FP32_REFINE = 1 } smc_precision;
 
 typedef struct smc_config {
     int dim;            /* 1: -(e^u w')' = f on [0,1]; 2: -div(e^u grad w) = f on (0,1)^2 (Sec. 3.2) */
-    int n;              /* 2D: cells per side (power of two, >= 64); 1D: FD intervals (>= 4) */
+    int n;              /* 2D: cells per side (power of two, 64..512); 1D: FD intervals (>= 4) */
     int kl_modes;       /* 2D: cosine modes per side, d = kl_modes^2 (<= n/2); 1D: sine modes, d = kl_modes */
     double alpha;       /* prior covariance C = (I - alpha Lap)^-2 (Sec. 2.1, Sec. 3) */
     int n_obs;          /* number of point observations N_d */

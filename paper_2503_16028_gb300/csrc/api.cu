@@ -38,6 +38,7 @@ static const char* validate(const smc_config& c) {
     if (c.dim != 1 && c.dim != 2) return "dim must be 1 or 2";
     if (c.dim == 2) {
         if (c.n < 64 || (c.n & (c.n - 1))) return "2D grid size n must be a power of two >= 64";
+        if (c.n > MAX_N2D) return "2D grid size n must be <= 512 (shared memory of the cosine-transform block)";
         if (c.kl_modes < 2 || c.kl_modes > c.n / 2 || (c.kl_modes & 1)) return "2D kl_modes must be even and in [2, n/2]";
         if (c.kl_modes > 256) return "2D kl_modes must be <= 256";
     } else {

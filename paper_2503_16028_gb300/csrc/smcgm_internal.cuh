@@ -44,6 +44,17 @@ __host__ __device__ inline double open53(uint32_t a, uint32_t b) {
 }
 
 struct Key { uint32_t k0, k1; };
+// Cosine-transform blocks (synthesis and its transpose): FCT_T transforms per
+// block (16 x 8 bytes: whole 128-byte rows), FCT_WARPS warps.  A block stages
+// FCT_T transforms of n + 1 values and gives each warp two n-value work rows,
+// all in doubles (a df32 pair is 8 bytes too).
+constexpr int FCT_T = 16;
+constexpr int FCT_WARPS = 8;
+constexpr size_t fct_smem_bytes(int n) { return 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n); }
+// Largest 2D grid: the transform block of a 1024-point grid would need 256 KB of
+// shared memory, above the 227 KB a block can have.
+constexpr int MAX_N2D = 512;
+
 // False when CUDA reports `p` as host memory it does not know (an ordinary
 // malloc or stack address), which a kernel must not dereference.  Device,
 // managed and registered (mapped) host memory pass; so does a pointer whose

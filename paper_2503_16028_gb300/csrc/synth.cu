@@ -25,8 +25,8 @@ namespace smcgm {
 // Stage 1 (along x, one transform per y-mode l) writes T^T[i][l]; stage 2
 // (along y, one transform per column i) writes U[j][i].
 // ------------------------------------------------------------------------
-constexpr int FCT_T = 16;            // transforms per block (16 x 8 bytes: whole 128-byte rows)
-constexpr int FCT_WARPS = 8;
+// FCT_T (transforms per block) and FCT_WARPS, and the block's shared memory, are in
+// smcgm_internal.cuh (the grid-size limit of the configuration follows from them).
 
 // Arithmetic of the transforms: FP64, or df32 on the FP32 pipes for the
 // mixed-precision forward solve (u to ~1e-13 absolute; the coefficients need
@@ -199,7 +199,7 @@ static void launch_fct(Ctx& c, const double* X, int count, typename O::V* tmp, t
     const int n = c.n, Km = c.Km;
     int lgn = 0;
     while ((1 << lgn) < n) ++lgn;
-    const size_t smem = 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
+    const size_t smem = fct_smem_bytes(n);
     static size_t attr = 0;
     if (attr < smem) {
         check(cudaFuncSetAttribute(k_fct<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");
@@ -341,7 +341,7 @@ static void launch_fct_t(Ctx& c, const double* g, int count, typename O::V* tmp,
     const int n = c.n, Km = c.Km;
     int lgn = 0;
     while ((1 << lgn) < n) ++lgn;
-    const size_t smem = 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n);
+    const size_t smem = fct_smem_bytes(n);
     static size_t attr = 0;
     if (attr < smem) {
         check(cudaFuncSetAttribute(k_fct_t<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "attr");

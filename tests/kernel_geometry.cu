@@ -8,8 +8,9 @@
 //   16-byte multiples as inner extents, cover the region (faces, right-hand
 //   side, correction, parent correction) and sit 128-byte aligned in the
 //   staging buffer;
-// * the dynamic shared memory of the staged kernels and the static shared
-//   memory of the operator pass fit the blocks per SM their launches ask for.
+// * the dynamic shared memory of the staged kernels, of the cosine transform
+//   and the static shared memory of the operator pass fit the blocks per SM
+//   their launches ask for, and the largest accepted 2D grid fits a block.
 #include <cstdio>
 #include <set>
 #include <utility>
@@ -105,6 +106,11 @@ int main() {
     check_staged<2, false, 4>();
     check_staged<4, true, 2>();
     check_staged<4, false, 2>();
+    // the cosine-transform block fits up to the largest accepted 2D grid and not beyond it;
+    // three blocks share an SM at 256^2
+    CHECK(fct_smem_bytes(MAX_N2D) <= BLOCK_MAX);
+    CHECK(fct_smem_bytes(2 * MAX_N2D) > BLOCK_MAX);
+    CHECK(3 * (fct_smem_bytes(256) + BLOCK_RESERVED) <= SM_SHARED);
     // the operator pass: 7 blocks of 4 warps with their p tiles in static shared memory
     constexpr size_t wapply = (size_t)WPB * (WT + 2) * 48 * sizeof(float);
     CHECK(7 * (wapply + BLOCK_RESERVED) <= SM_SHARED);

@@ -55,6 +55,12 @@ def test_workspace_size_and_validation(lib):
     assert size.value < 64 << 30
     bad = smcgm.make_config(wl, n=200)
     assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    # the largest 2D grid is 512^2 (the cosine-transform block's shared memory)
+    ok = smcgm.make_config(wl, n=512)
+    assert lib.smc_workspace_size(ctypes.byref(ok), ctypes.byref(size)) == 0
+    bad = smcgm.make_config(wl, n=1024)
+    assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
+    assert b"512" in lib.smc_last_error(None)
     bad = smcgm.make_config(wl, n_particles=40000)
     assert lib.smc_workspace_size(ctypes.byref(bad), ctypes.byref(size)) == smcgm.SMC_EINVAL
     bad = smcgm.make_config(wl, n_particles=1)           # a single particle's weights carry no information
