@@ -167,8 +167,32 @@ def make_config(preset, **overrides):
     return cfg
 
 
+def choose_solve_batch(workspace_size, n_particles, budget):
+    """Largest solve batch B in [1, N] whose workspace (workspace_size(B) bytes) fits `budget`
+    bytes; N itself when it fits.  The results do not depend on B (each particle's solve is
+    its own), only the memory and the number of batches do.  Raises MemoryError when even
+    B = 1 does not fit (the particle arrays alone exceed the budget)."""
+    if workspace_size(n_particles) <= budget:
+        return n_particles
+    if workspace_size(1) > budget:
+        raise MemoryError("the workspace needs %d bytes even with one particle per solve batch; %d available"
+                          % (workspace_size(1), budget))
+    lo, hi = 1, n_particles          # workspace_size(lo) fits, workspace_size(hi) does not
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if workspace_size(mid) <= budget:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
 class Sampler:
-    """One smc_ctx with its caller-owned device workspace (a torch uint8 tensor)."""
+    """One smc_ctx with its caller-owned device workspace (a torch uint8 tensor).
+
+    With cfg.solve_batch = 0 (all particles in one solve batch) and a workspace larger than
+    90 % of the device's free memory, the batch is reduced to the largest that fits
+    (choose_solve_batch); cfg.solve_batch is updated to the value used."""
 
     def __init__(self, cfg, device="cuda:0", stream=None):
         import torch
@@ -176,6 +200,23 @@ class Sampler:
         self.cfg = cfg
         size = ctypes.c_size_t()
         self._check(self.lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)), None)
+        budget = None
+        if cfg.solve_batch == 0:
+            try:
+                budget = int(0.9 * torch.cuda.mem_get_info(torch.device(device))[0])
+            except Exception:          # no memory figure: one batch of all particles, as configured
+                budget = None
+        if budget is not None and size.value + 256 > budget:
+            def ws(b):
+                cfg.solve_batch = int(b)
+                self._check(self.lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)), None)
+                return size.value + 256
+            try:
+                cfg.solve_batch = choose_solve_batch(ws, cfg.n_particles, budget)
+            except MemoryError:
+                cfg.solve_batch = 0
+                raise
+            ws(cfg.solve_batch)                 # size.value: the workspace of the batch chosen
         self.ws = torch.empty(size.value + 256, dtype=torch.uint8, device=device)
         base = self.ws.data_ptr()
         aligned = (base + 255) & ~255

@@ -85,3 +85,16 @@ def test_concurrent_builds_use_private_objects(tmp_path, monkeypatch):
     assert len(objs) == 2 * len(build.sources()) and len(set(objs)) == len(objs)
     assert libs == [build.LIB, build.LIB] and os.path.exists(build.LIB)
     assert os.listdir(build.BUILD) == []
+
+
+def test_choose_solve_batch():
+    """The largest batch whose workspace fits the budget: a workspace of base + B * per bytes."""
+    base, per, N = 1000, 37, 4096
+    size = lambda b: base + b * per
+    assert smcgm.choose_solve_batch(size, N, size(N)) == N
+    assert smcgm.choose_solve_batch(size, N, 10 ** 12) == N
+    for budget in (size(1), size(2) - 1, size(777), size(777) + per - 1, size(N) - 1):
+        b = smcgm.choose_solve_batch(size, N, budget)
+        assert size(b) <= budget and (b == N or size(b + 1) > budget), (budget, b)
+    with pytest.raises(MemoryError):
+        smcgm.choose_solve_batch(size, N, size(1) - 1)
