@@ -1,7 +1,7 @@
 """Host logic of bench.py's secondary measurements, on CPU with a stand-in
 sampler and event clock: the per-layer aggregation of the whole SMC run (first
 layer, the layers with 0.1 < t < 1, all layers), the solver-only rate and the
-mixed-precision agreement counters."""
+mixed-precision agreement counters, and the whole-move HBM byte model."""
 import os
 import sys
 import types
@@ -144,3 +144,25 @@ def test_precision_agreement_counts(monkeypatch):
     assert out["max_abs_posterior_mean_diff"] == pytest.approx(1e-3 / 6)
     assert out["max_rel_phi_diff"] == pytest.approx(1e-9, rel=1e-3)
     assert mixed.counts["solves"] == 3 * 6       # the mixed sampler replays the FP64 sampler's moves
+
+
+def test_whole_move_byte_model_by_hand():
+    """The whole-move HBM model at 256^2 with the measured counters (14.71 CG iterations and
+    3.155 refinement phases per solve, FP32 inner solver), worked out from its parts: tiled
+    levels below the finest 128^2 and 64^2 (9.5 words each per own cell), the coarse kernel's
+    faces and top level, 6 + 9.25 + 5.25 words per finest cell per CG iteration, 4.25 + 5.25
+    per inner-solve start, 52 B per refinement, 66.8 B of set-up, 4 d doubles of KL vectors."""
+    prof = dict(word_bytes=4, cells=65536, solves=100, cg_iterations=1471, inner_solves=315.5, residuals=315.5)
+    lower = 9.5 / 4 + 9.5 / 16 + 2.0 / 48 + 2.0 / 64
+    per_cell = (14.71 * (6 + 9.25 + 5.25 + lower) * 4 + 3.155 * (4.25 + 5.25 + lower) * 4
+                + 3.155 * 52.0 + (16 + 24 + 2.7 * 4 + 16))
+    expect = per_cell * 65536 + 4 * 16384 * 8
+    got = bench.model_bytes_per_solve(prof, 256, 16384)
+    assert got == pytest.approx(expect, rel=1e-12)
+    assert got == pytest.approx(116.8e6, rel=2e-3)
+    # 64^2: no tiled level below the finest; the coarse kernel starts at 32^2
+    prof64 = dict(prof, cells=4096)
+    lower64 = 2.0 / 48 + 2.0 / 4
+    per_cell64 = (14.71 * (6 + 9.25 + 5.25 + lower64) * 4 + 3.155 * (4.25 + 5.25 + lower64) * 4
+                  + 3.155 * 52.0 + (16 + 24 + 2.7 * 4 + 16))
+    assert bench.model_bytes_per_solve(prof64, 64, 1024) == pytest.approx(per_cell64 * 4096 + 4 * 1024 * 8, rel=1e-12)
