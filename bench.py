@@ -13,6 +13,14 @@ Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload.  Multi-GPU: one process per GPU
 (torchrun), each an independent replica of the workload (weak scaling, no
 collective in the timed region), timed with a barrier and the maximum over ranks.
+
+Beside the headline the line carries: the roofline of the dominant kernel and
+the whole-move HBM byte model, the FP64 solver's rate and its agreement with the
+mixed-precision path, the solver-only rate (smc_forward), the end-to-end rate
+through smc_move_host with host buffers, the adjoint-gradient rate, a whole SMC
+run timed layer by layer, the 64^2 workload on the GPU and on the CPU oracle,
+the SM clocks sampled during the timed region and the CPU oracle baseline.
+--no-fp64, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
 """
 import argparse
 import json
