@@ -253,14 +253,18 @@ typedef struct smc_profile {
     int word_bytes;            /* bytes per word of the inner solver (4: FP32, 8: FP64) */
 } smc_profile;
 
-/* enable: 1 turns event timing of the dominant kernel on, 0 off, -1 leaves
- * it as is.  If out is non-NULL the counters accumulated since the last
- * reset are copied there and, when reset is non-zero, cleared. */
+/* enable: 1 turns event timing of the dominant kernel on, 0 off, any other
+ * value (-1) leaves it as is.  If out is non-NULL (host, caller-owned) the
+ * counters accumulated since the last reset are copied there and, when reset
+ * is non-zero, cleared.  SMC_EINVAL for a NULL ctx, SMC_ECUDA if the timing
+ * events cannot be created. */
 smc_status smc_profile_query(smc_ctx* ctx, int enable, smc_profile* out, int reset);
 
 /* Copies `bytes` from device address `src` (e.g. a view returned above) to
  * host memory `dst` on the context's stream and waits for it: a helper for
- * bindings that have no CUDA runtime of their own. */
+ * bindings that have no CUDA runtime of their own.  Both buffers stay the
+ * caller's.  SMC_EINVAL for a NULL ctx or a NULL pointer with bytes > 0,
+ * SMC_ECUDA if the copy fails (message in smc_last_error(ctx)). */
 smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t bytes);
 
 /* Largest particle count smc_resample_indices_static() accepts: its scratch is
@@ -288,10 +292,11 @@ smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t byt
 smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
                                        int* d_indices, void* stream);
 
-/* Library version string. */
+/* Library version string (static storage owned by the library; never NULL). */
 const char* smc_version(void);
 
-/* sizeof(smc_config) as compiled into the library (lets bindings check their layout). */
+/* sizeof(smc_config) as compiled into the library (lets bindings check their
+ * layout before passing a config; a mismatch means the binding is stale). */
 size_t smc_config_size(void);
 
 #ifdef __cplusplus
