@@ -123,8 +123,14 @@ smc_status smc_config_init(smc_config* cfg);
 smc_status smc_workspace_size(const smc_config* cfg, size_t* bytes);
 
 /* Sets up a context on `stream` (a cudaStream_t, NULL = default stream):
- * copies the host inputs, draws v_n ~ mu_0 = N(0, C) (Alg. 1 "Input"), solves
- * the N forward problems and stores Phi(v_n).  t = 0, beta = beta0. */
+ * copies the host inputs, draws v_n ~ mu_0 = N(0, C) (the input step of
+ * Alg. 1), solves the N forward problems and stores Phi(v_n).  t = 0,
+ * beta = beta0.  d_workspace: the caller's device buffer of `bytes` >=
+ * smc_workspace_size() bytes, 256-byte aligned, kept until smc_destroy().
+ * On success *out is the new context (release it with smc_destroy()).
+ * SMC_EINVAL for an invalid cfg (reason in smc_last_error(NULL)), SMC_ENOMEM
+ * when bytes is too small (checked before the GPU is touched), SMC_ECUDA if a
+ * CUDA call fails. */
 smc_status smc_init(const smc_config* cfg, void* d_workspace, size_t bytes, void* stream, smc_ctx** out);
 
 /* Reweighting step of Alg. 1 with the tempering rule of App. C: finds
