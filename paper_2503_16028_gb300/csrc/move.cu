@@ -312,8 +312,10 @@ __global__ void __launch_bounds__(256) k_accept(int d, int K, int r, int kernel,
         double la;
         int a;
         if (kernel == SMC_K_GM_INDEP) {
-            la = 0.0;
-            a = 1;
+            // Alg. 3 takes every proposal, except one whose potential could not be
+            // evaluated (a field outside the mixed-precision range gets +inf)
+            a = isfinite(PhiV[p]) ? 1 : 0;
+            la = a ? 0.0 : -INFINITY;
         } else {
             const double ratio = lse_terms(lw, lrev + (size_t)p * K, K) - lse_terms(lw, lfwd + (size_t)p * K, K);
             la = t * (Phi[p] - PhiV[p]) + ratio;
