@@ -330,6 +330,80 @@ def langevin_alpha_without_t(orig):
     return f
 
 
+def cdf_ceil(orig):
+    def f(w):
+        q = [int(np.ceil(wi * smc.RESAMPLE_T)) for wi in w]      # ceil where the reading floors
+        q[int(np.argmax(w))] += smc.RESAMPLE_T - sum(q)
+        return list(np.cumsum(np.array(q, dtype=object)))
+    return f
+
+
+def cdf_remainder_to_smallest(orig):
+    def f(w):
+        q = [int(np.floor(wi * smc.RESAMPLE_T)) for wi in w]
+        q[int(np.argmin(w))] += smc.RESAMPLE_T - sum(q)        # smallest weight takes the remainder
+        return list(np.cumsum(np.array(q, dtype=object)))
+    return f
+
+
+def cdf_ties_to_highest_index(orig):
+    def f(w):
+        q = [int(np.floor(wi * smc.RESAMPLE_T)) for wi in w]
+        w = np.asarray(w)
+        q[len(w) - 1 - int(np.argmax(w[::-1]))] += smc.RESAMPLE_T - sum(q)   # last of the equal largest
+        return list(np.cumsum(np.array(q, dtype=object)))
+    return f
+
+
+def _fit_variant(reseed_highest=False, collapse_weight_k=False, floor_at_lambda=False):
+    """gm.fit with one planted change (the rest as the oracle's EM)."""
+    def fit(X, S, lam0, K, iters, seed, layer, var_floor=1e-3):
+        X = np.asarray(X, dtype=np.float64)
+        N = X.shape[0]
+        xs = X[:, S]
+        lamS = np.asarray(lam0)[S]
+        floor = lamS if floor_at_lambda else var_floor * lamS
+        pm = np.mean(xs, axis=0)
+        pooled = np.maximum(np.mean((xs - pm) ** 2, axis=0), floor)
+        idx = gm.init_indices(seed, layer, N, K)
+        w = np.full(K, 1.0 / K)
+        m = xs[idx].copy()
+        lam = np.tile(pooled, (K, 1))
+        hist = []
+        for _ in range(iters):
+            g, ll = gm.e_step(xs, w, m, lam)
+            hist.append(ll)
+            Nj = np.sum(g, axis=0)
+            for j in range(K):
+                if Nj[j] < 2.0:
+                    mg = np.max(g, axis=1)
+                    n_star = int(np.argmax(mg)) if reseed_highest else int(np.argmin(mg))
+                    m[j] = xs[n_star]
+                    lam[j] = pooled
+                    w[j] = 1.0 / K if collapse_weight_k else 1.0 / N
+                    continue
+                w[j] = Nj[j] / N
+                m[j] = np.sum(g[:, j:j + 1] * xs, axis=0) / Nj[j]
+                lam[j] = np.maximum(np.sum(g[:, j:j + 1] * (xs - m[j]) ** 2, axis=0) / Nj[j], floor)
+            w = w / np.sum(w)
+        g, ll = gm.e_step(xs, w, m, lam)
+        hist.append(ll)
+        return pcngm.Mixture(S, w, m, lam, lam0), hist
+    return fit
+
+
+def fit_reseed_at_highest(orig):
+    return _fit_variant(reseed_highest=True)
+
+
+def fit_collapse_weight_one_over_k(orig):
+    return _fit_variant(collapse_weight_k=True)
+
+
+def fit_floor_at_lambda(orig):
+    return _fit_variant(floor_at_lambda=True)
+
+
 CASES = {
     "log_r drops the log-determinant": (pcngm, "log_r", log_r_without_logdet,
                                         [t_pcngm.test_ratio_equals_theorem2_block_gaussian_densities,
@@ -402,6 +476,18 @@ CASES = {
     "GM-Langevin ratio without the pCN base density": (langevin, "gm_log_R", gm_log_R_without_base,
                                                        [lambda: t_lang.test_gm_detailed_balance_direct_densities(0.3, 0.2),
                                                         t_lang.test_gm_special_cases]),
+    "fixed-point CDF rounds up": (smc, "fixed_point_cdf", cdf_ceil,
+                                  [t_smc.test_fixed_point_cdf_hand_computed]),
+    "fixed-point remainder on the smallest weight": (smc, "fixed_point_cdf", cdf_remainder_to_smallest,
+                                                     [t_smc.test_fixed_point_cdf_hand_computed]),
+    "fixed-point remainder on the last of equal largest weights": (smc, "fixed_point_cdf", cdf_ties_to_highest_index,
+                                                                   [t_smc.test_fixed_point_cdf_hand_computed]),
+    "EM collapse re-seeds at the highest max-responsibility": (gm, "fit", fit_reseed_at_highest,
+                                                               [t_gm.test_collapse_reseeds_at_lowest_max_responsibility]),
+    "EM collapse weight 1/K instead of 1/N": (gm, "fit", fit_collapse_weight_one_over_k,
+                                              [t_gm.test_collapse_reseeds_at_lowest_max_responsibility]),
+    "EM variance floor at lambda instead of 1e-3 lambda": (gm, "fit", fit_floor_at_lambda,
+                                                           [t_gm.test_variance_floor_binds_on_a_constant_coordinate]),
 }
 
 

@@ -110,3 +110,46 @@ def test_prior_draws_have_the_prior_moments():
     assert np.all(np.abs(X.mean(axis=0)) < 4 * np.sqrt(lam / N))
     assert np.all(np.abs(X.var(axis=0) / lam - 1.0) < 4 * np.sqrt(2.0 / N))
     assert abs(np.corrcoef(X[:-1, 0], X[1:, 0])[0, 1]) < 4 / np.sqrt(N)
+
+
+# Fixed-point CDFs written out by hand (Alg. 1 resampling; the reading: T = 2^48, floor, the
+# remainder to the largest weight, lowest index among equal largest weights).  Each weight's
+# binary expansion is stated so that the floors can be checked without running anything.
+T48 = 1 << 48
+HAND_CDFS = [
+    # 1/8, 3/8, 1/2 are exact: q = 2^45, 3 * 2^45, 2^47 and nothing is left over
+    ([0.125, 0.375, 0.5], [35184372088832, 140737488355328, 281474976710656]),
+    # the double nearest 1/3 is 6004799503160661 * 2^-54, so w T = 93824992236885.328125;
+    # three floors leave 1, which goes to index 0 (a three-way tie for the largest weight)
+    ([1 / 3, 1 / 3, 1 / 3], [93824992236886, 187649984473771, 281474976710656]),
+    # 0.2 = 3602879701896397 * 2^-54 -> 56294995342131.203125, 0.4 -> 112589990684262.40625;
+    # the floors leave 1, which goes to index 1 (tie between 1 and 2: lowest index)
+    ([0.2, 0.4, 0.4], [56294995342131, 168884986026394, 281474976710656]),
+    # 0.1 -> 28147497671065.6015625, 0.3 -> 84442493013196.796875; the floors leave 2,
+    # which go to the largest weight 0.4 (index 3)
+    ([0.1, 0.2, 0.3, 0.4], [28147497671065, 84442493013196, 168884986026392, 281474976710656]),
+    # five weights: the floors leave 3, which go to index 0 (0.3 twice: lowest index)
+    ([0.3, 0.3, 0.2, 0.1, 0.1], [84442493013199, 168884986026395, 225179981368526, 253327479039591,
+                                 281474976710656]),
+]
+
+
+def test_fixed_point_cdf_hand_computed():
+    assert smc.RESAMPLE_T == T48
+    for w, cdf in HAND_CDFS:
+        assert list(smc.fixed_point_cdf(np.array(w))) == cdf, w
+
+
+def test_systematic_indices_hand_computed():
+    """logw = (log 2, 0, 0) normalises to exactly (1/2, 1/4, 1/4): CDF/T = (1/2, 3/4, 1), and
+    the points (k + U)/3 with U = (u48 + 1/2)/2^48 fall, by hand:
+      u48 = 0:           ~0, ~1/3, ~2/3          -> 0, 0, 1
+      u48 = 2^47 - 1:    U = 1/2 - 2^-49: 1/6, 1/2 - 2^-49/3, 5/6 - ...  -> 0, 0, 2
+      u48 = 2^47:        U = 1/2 + 2^-49: 1/6, 1/2 + 2^-49/3, 5/6 + ...  -> 0, 1, 2
+      u48 = 2^48 - 1:    ~1/3, ~2/3, ~1 (below)  -> 0, 1, 2
+    The second and third straddle the CDF boundary 1/2: index i is taken only when the
+    point lies strictly below CDF_i."""
+    logw = np.array([np.log(2.0), 0.0, 0.0])
+    assert list(smc.normalised_weights(logw)) == [0.5, 0.25, 0.25]
+    for u48, ref in [(0, [0, 0, 1]), ((1 << 47) - 1, [0, 0, 2]), (1 << 47, [0, 1, 2]), (T48 - 1, [0, 1, 2])]:
+        assert list(smc.systematic_indices(logw, u48)) == ref, u48
