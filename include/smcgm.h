@@ -179,7 +179,8 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl,
  * cells in 2D, the n - 1 interior nodes in 1D) are device
  * outputs; iters (host, may be NULL) gets the largest CG iteration count.
  * SMC_EINVAL if a device argument is host memory CUDA does not know (an
- * ordinary malloc or stack address), checked before any kernel runs. */
+ * ordinary malloc or stack address) or memory of another GPU than the
+ * current one, checked before any kernel runs. */
 smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi, double* d_w, int* iters);
 
 /* Potential and its gradient for `count` coefficient vectors on the device
@@ -287,13 +288,15 @@ smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t byt
  * n_particles ints) receives the indices.  Scratch is a file-scope device
  * array of SMC_STATIC_RESAMPLE_MAX words that each GPU loading the library
  * keeps until the process exits; the library calls no cudaMalloc, cudaFree or
- * allocating routine.  The first call on a device looks up the array's
- * device address with that device current (call it once before capturing work
- * into a stream graph).  All calls share the array: calls that overlap on the
+ * allocating routine.  Every call looks up the array's device address on the
+ * current device (so a device reset in between does no harm); the first call
+ * on a device also loads the array there, so make it before capturing work
+ * into a stream graph.  All calls share the array: calls that overlap on the
  * GPU race and must be serialised by the caller (e.g. one stream).  Returns
  * SMC_EINVAL for n_particles outside [1, SMC_STATIC_RESAMPLE_MAX] or a
- * d_logw / d_indices that CUDA reports as unregistered host memory (message
- * in smc_last_error(NULL)), SMC_ECUDA if a CUDA call fails.  Asynchronous on
+ * d_logw / d_indices that CUDA reports as unregistered host memory or as
+ * memory of another GPU than the current one (message in
+ * smc_last_error(NULL)), SMC_ECUDA if a CUDA call fails.  Asynchronous on
  * `stream` (a cudaStream_t, NULL = default stream). */
 smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
                                        int* d_indices, void* stream);

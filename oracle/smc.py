@@ -26,6 +26,8 @@ capped at 1 (the paper is silent on the cap).
 
 Accept test (Alg. 2): U < min(1, alpha) with U = (u53 + 1/2) 2^-53.
 """
+import bisect
+
 import numpy as np
 from . import philox, pcngm, gm
 
@@ -89,6 +91,28 @@ def systematic_indices(logw, u48):
             i += 1
         out[k] = i
     return out
+
+
+def resampling_near_ties(logw, u48, units=64):
+    """Systematic points that lie within `units` CDF units (of 2^48) of a CDF boundary.
+
+    Particle k's point sits at k T + u48 + 1/2 on the scale of N * CDF, and the index
+    changes where it crosses N * CDF_i.  The weights come from floating-point exponentials
+    and a log-sum-exp, whose last bits depend on the summation order and the exp routine, so
+    two correct implementations may floor a w_i T differently by one unit and shift later
+    CDF entries by a few units.  A point farther than `units` from every boundary gets the
+    same index under any such difference; the points returned here are the near-ties."""
+    N = len(logw)
+    cdf = fixed_point_cdf(normalised_weights(np.asarray(logw, dtype=np.float64)))
+    bounds = [2 * N * c for c in cdf[:-1]]      # twice the scaled boundaries: integers
+    ties = []
+    for k in range(N):
+        p2 = 2 * (k * RESAMPLE_T + u48) + 1     # twice the point
+        i = bisect.bisect_left(bounds, p2)      # bounds[i - 1] < p2 <= bounds[i]
+        gaps = [abs(bounds[j] - p2) for j in (i - 1, i) if 0 <= j < len(bounds)]
+        if gaps and min(gaps) < 2 * N * units:
+            ties.append(k)
+    return ties
 
 
 def beta_rule(beta, acc_rate):

@@ -11,7 +11,6 @@
 // prefix sums CDF_i; particle k takes min{i : N CDF_i > k T + u48} with u48 one
 // Philox draw.  Integer arithmetic makes the indices independent of summation
 // order.
-#include <mutex>
 #include "smcgm_internal.cuh"
 #include "common.cuh"
 
@@ -258,19 +257,14 @@ void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, doubl
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned long long g_static_cdf[SMC_STATIC_RESAMPLE_MAX];
 
-// Device address of g_static_cdf per device, looked up once with that device current.
-static unsigned long long* static_cdf_ptr(int dev) {
-    constexpr int MAXDEV = 64;
-    static std::mutex mu;
-    static unsigned long long* ptrs[MAXDEV] = {nullptr};
-    if (dev < 0 || dev >= MAXDEV) throw CudaError{cudaErrorInvalidDevice, "device index out of range"};
-    std::lock_guard<std::mutex> lock(mu);
-    if (!ptrs[dev]) {
-        void* p = nullptr;
-        check(cudaGetSymbolAddress(&p, g_static_cdf), "cudaGetSymbolAddress(g_static_cdf)");
-        ptrs[dev] = reinterpret_cast<unsigned long long*>(p);
-    }
-    return ptrs[dev];
+// Device address of g_static_cdf on the current device.  It is looked up on every
+// call (the lookup allocates nothing): a cached address would go stale if the
+// process reset the device, which unloads the library's module there.  The first
+// lookup on a device also loads the module's copy of the array onto it.
+static unsigned long long* static_cdf_ptr() {
+    void* p = nullptr;
+    check(cudaGetSymbolAddress(&p, g_static_cdf), "cudaGetSymbolAddress(g_static_cdf)");
+    return reinterpret_cast<unsigned long long*>(p);
 }
 
 }  // namespace smcgm
@@ -291,9 +285,7 @@ extern "C" smc_status smc_resample_indices_static(const double* d_logw, int n_pa
         return SMC_EINVAL;
     }
     try {
-        int dev = 0;
-        check(cudaGetDevice(&dev), "cudaGetDevice");
-        unsigned long long* cdf = static_cdf_ptr(dev);
+        unsigned long long* cdf = static_cdf_ptr();
         const Key key = key_of(seed);
         const U4 w = philox(0u, 0u, (uint32_t)layer, P_RESAMPLE, key.k0, key.k1);
         const unsigned long long u48 = ((unsigned long long)w.x << 16) | (unsigned long long)(w.y >> 16);

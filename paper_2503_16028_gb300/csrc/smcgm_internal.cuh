@@ -56,17 +56,28 @@ constexpr size_t fct_smem_bytes(int n) { return 8 * ((size_t)FCT_T * (n + 1) + (
 constexpr int MAX_N2D = 512;
 
 // False when CUDA reports `p` as host memory it does not know (an ordinary
-// malloc or stack address), which a kernel must not dereference.  Device,
-// managed and registered (mapped) host memory pass; so does a pointer whose
-// query fails, which leaves the decision to the caller's contract rather than
-// rejecting valid memory.
+// malloc or stack address), which a kernel must not dereference, or as device
+// memory of another GPU than the current one (a kernel here would read it as a
+// peer access, which faults unless peer access was enabled).  Device memory of
+// the current GPU, managed and registered (mapped) host memory pass; so does a
+// pointer whose query fails, which leaves the decision to the caller's contract
+// rather than rejecting valid memory.
 inline bool device_visible(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return true;
     }
-    return a.type != cudaMemoryTypeUnregistered;
+    if (a.type == cudaMemoryTypeUnregistered) return false;
+    if (a.type == cudaMemoryTypeDevice) {
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return true;
+        }
+        return a.device == dev;
+    }
+    return true;
 }
 
 inline Key key_of(unsigned long long seed) { return Key{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)}; }

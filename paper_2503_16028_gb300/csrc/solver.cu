@@ -973,12 +973,15 @@ template <typename T>
 static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
     k_compact<<<1, 1024, 0, c.stream>>>(count, c.sc.act_in, s.list, s.nact); ++c.pc.launches;
     int h[4];
+    int err[2] = {0, 0};
     check(cudaMemcpyAsync(h, s.nact, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "nact d2h");
     check(cudaMemcpyAsync(hcount, c.sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
+    check(cudaMemcpyAsync(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "err d2h");
     check(cudaStreamSynchronize(c.stream), "sync");
-    int err[2] = {0, 0};
-    check(cudaMemcpy(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost), "err d2h");
-    if (err[0] || err[1]) check(cudaMemset(c.dev_err, 0, 2 * sizeof(int)), "err reset");   // the context stays usable
+    if (err[0] || err[1]) {   // cleared in stream order, so the context stays usable and no later flag is lost
+        check(cudaMemsetAsync(c.dev_err, 0, 2 * sizeof(int), c.stream), "err reset");
+        check(cudaStreamSynchronize(c.stream), "sync");
+    }
     if (err[0]) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
     if (err[1] && !c.lenient)
         throw InputError{"log-permeability |u| >= 64 is outside the mixed-precision range (use the FP64 solver)"};

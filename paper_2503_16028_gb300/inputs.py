@@ -80,3 +80,27 @@ def random_particles(seed, N, d, scale=None):
 
 def random_potentials(seed, N, low=0.0, high=100.0):
     return np.random.default_rng(seed).uniform(low, high, size=N)
+
+
+def structured_potentials(seed, N, low=0.0, high=200.0):
+    """Seeded potentials with the structures that matter for reweighting and resampling:
+    uniform values, the smallest value twice (a tie for the largest weight), a run of 16
+    equal values (equal weights) and one value far below the rest (a dominant weight,
+    at index N // 3)."""
+    phi = np.random.default_rng(seed).uniform(low, high, size=N)
+    lo = float(np.min(phi))
+    phi[N // 2] = phi[N // 5] = lo                      # tie for the largest weight
+    phi[N // 4:N // 4 + 16] = phi[N // 4]               # equal weights
+    phi[N // 3] = lo - 0.05 * (high - low)              # dominant weight
+    return phi
+
+
+def structured_log_weights(seed, N, scale=3.0):
+    """Seeded unnormalised log weights: normal values, a tie for the largest weight, a run of
+    equal weights and one dominant weight (the log-weight analogue of structured_potentials)."""
+    lw = np.random.default_rng(seed).normal(0.0, scale, size=N)
+    hi = float(np.max(lw))
+    lw[N // 2] = lw[N // 5] = hi
+    lw[N // 4:N // 4 + 16] = lw[N // 4]
+    lw[N // 3] = hi + 2.0
+    return lw

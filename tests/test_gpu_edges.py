@@ -174,3 +174,44 @@ def test_move_rejects_out_of_range_proposal():
         assert bool(dg["accepted"][n]) == bool(acc)
         assert _rel(X2[n], x) < 1e-13
     s.close()
+
+
+def test_smc_gm_does_not_take_out_of_range_proposal():
+    """SMC-GM (Alg. 3, beta = 1: every mixture draw is taken) with one component whose mean
+    puts the constant mode at 80: a particle that draws that component gets a field
+    outside the mixed-precision range, so its proposal is not taken and its state and
+    potential stay; every other particle takes its proposal, equal to the oracle's."""
+    wl = inputs.load_workload("darcy64_bimodal")
+    N = 8
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, n_components=2, precision=smcgm.SMC_P_FP32_REFINE,
+                                        kernel=smcgm.SMC_K_GM_INDEP))
+    prob = oproblem.from_workload(wl)
+    X, Phi = s.particles()
+    w, m, lam, modes = s.smc_get_mixture()
+    assert modes[0] == 0                                  # the constant mode leads the mixture modes
+    w = np.array([0.5, 0.5])
+    m = np.zeros_like(m)
+    m[1, 0] = 80.0
+    s.smc_set_mixture(w, m, lam)
+    mix = opcngm.Mixture(modes, w, m, lam, prob.lam)
+    step = 4
+    s.smc_set_schedule(0.3, 1.0, 0, step)
+    s.smc_move(1)
+    X2, Phi2 = s.particles()
+    dg = s.diagnostics()
+    far = 0
+    for n in range(N):
+        Uc = float(osmc.philox.uniforms(wl["seed"], 0, n, step, osmc.philox.COMP))
+        j = opcngm.choose_component(w, Uc)
+        if j == 1:
+            far += 1
+            assert not dg["accepted"][n] and np.isinf(dg["phi_proposed"][n])
+            assert np.array_equal(X2[n], X[n]) and Phi2[n] == Phi[n]
+        else:
+            v, pv, acc, _, _ = osmc.move_particle(X[n], Phi[n], mix, 1.0, 0.3, wl["seed"], n, step, prob.potential,
+                                                  always_accept=True)
+            assert dg["accepted"][n]
+            assert _rel(X2[n], v) < 1e-13
+            assert abs(Phi2[n] - pv) <= 1e-10 * abs(pv)
+    assert 0 < far < N
+    s.close()

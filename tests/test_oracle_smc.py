@@ -153,3 +153,22 @@ def test_systematic_indices_hand_computed():
     assert list(smc.normalised_weights(logw)) == [0.5, 0.25, 0.25]
     for u48, ref in [(0, [0, 0, 1]), ((1 << 47) - 1, [0, 0, 2]), (1 << 47, [0, 1, 2]), (T48 - 1, [0, 1, 2])]:
         assert list(smc.systematic_indices(logw, u48)) == ref, u48
+
+
+def test_resampling_near_ties_hand_computed():
+    """Weights (1/2, 1/4, 1/4), N = 3: with u48 = 2^47 - 1 the second point is
+    (3/2 - 2^-49)/3 = 1/2 - 2^-49/3, i.e. half a CDF unit below the boundary 1/2 on the
+    scale N * CDF (2 * 3 * 2^47 - (2 (2^48 + 2^47 - 1) + 1) = 1): a near-tie for any margin.
+    With u48 = 2^46 (U just above 1/4) the third point is (2 + 1/4)/3 = 3/4 plus a
+    fraction of a unit, on the boundary 3/4; with u48 = 2^45 (U ~ 1/8) the points 1/24,
+    3/8, 17/24 stay at least T/24 from the boundaries 1/2 and 3/4: none."""
+    logw = np.array([np.log(2.0), 0.0, 0.0])
+    assert smc.resampling_near_ties(logw, (1 << 47) - 1, units=1) == [1]
+    assert smc.resampling_near_ties(logw, 1 << 46, units=1) == [2]
+    assert smc.resampling_near_ties(logw, 1 << 45, units=1 << 40) == []
+    assert smc.resampling_near_ties(logw, 1 << 47, units=1) == [1]
+    # equal weights with N a power of two: CDF_i = (i + 1) T / N exactly, the points sit
+    # u48 + 1/2 units above k T, i.e. u48 + 1/2 above the boundary below them
+    assert smc.resampling_near_ties(np.zeros(4), 10, units=11) == [1, 2, 3]
+    assert smc.resampling_near_ties(np.zeros(4), 10, units=10) == [1, 2, 3]
+    assert smc.resampling_near_ties(np.zeros(4), 10, units=2) == []

@@ -1,5 +1,6 @@
 """The allocation-free resampling entry point (smc_resample_indices_static) gives
-the same indices as the context-based smc_resample().
+the same indices as the context-based smc_resample(), and the oracle's systematic
+indices at the metric workload's 4096 particles and at its cap of 32768.
 
 Callers that cannot give the library device memory -- an application whose own
 pool owns all device memory, or a loop that must not risk cudaMalloc's implicit
@@ -54,3 +55,28 @@ def test_static_resampling_rejects_oversize(lib):
                                          ctypes.c_void_p(out.data_ptr()), None)
     assert st == smcgm.SMC_EINVAL
     assert b"SMC_STATIC_RESAMPLE_MAX" in lib.smc_last_error(None)
+
+
+@pytest.mark.parametrize("N", [4096, 32768])
+def test_static_resampling_matches_oracle_at_scale(lib, N):
+    """Seeded log weights with a tie for the largest weight, a run of equal weights and one
+    dominant weight, at layer 7, twice in a row: the indices equal the oracle's systematic
+    indices (after checking that no systematic point is a near-tie)."""
+    from paper_2503_16028_gb300 import inputs, smcgm
+    from oracle import smc as osmc
+    assert N <= smcgm.SMC_STATIC_RESAMPLE_MAX == 32768
+    seed, layer = 2503016028, 7
+    logw = inputs.structured_log_weights(N + 3, N)
+    u48 = osmc.resample_u48(seed, layer)
+    assert osmc.resampling_near_ties(logw, u48) == []
+    ref = osmc.systematic_indices(logw, u48)
+    d_logw = torch.tensor(logw, dtype=torch.float64, device="cuda")
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        out.fill_(-1)
+        st = lib.smc_resample_indices_static(ctypes.c_void_p(d_logw.data_ptr()), N, seed, layer,
+                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+        assert st == smcgm.SMC_OK, lib.smc_last_error(None)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
