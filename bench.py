@@ -255,18 +255,28 @@ def time_forward(s, torch, calls=2):
                 cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
-def time_layers(wl, N, smcgm, torch, max_layers=60):
-    """A whole SMC run of the workload (Alg. 2): every tempering layer reweights (ESS bisection),
-    resamples, fits the mixture and makes L pCN-GM moves; each layer's smc_move is timed with
-    CUDA events.  Returns solves/s of the first layer's moves, of the moves of the layers with
-    0.1 < t < 1 and of all layers, with the layer count and the run's wall time."""
+def time_layers(wl, N, smcgm, torch, max_layers=60, fp64=True):
+    """A whole SMC run of the workload (Alg. 2) to t = 1: every tempering layer reweights (ESS
+    bisection), resamples, fits the mixture and makes L pCN-GM moves; each layer's smc_move of the
+    mixed-precision sampler is timed with CUDA events.  Returns solves/s of the first layer's
+    moves, of the moves of the layers with 0.1 < t < 1 and of all layers, with the layer count and
+    the run's wall time.
+
+    With fp64, an FP64 sampler of the same workload and seed runs beside it in lockstep, and the
+    result carries the error of the mixed-precision run against it: per layer the temperature
+    step, the resampling indices, the acceptance rate and the potentials; at t = 1 the relative
+    L2 error of the posterior mean and variance of the KL coefficients (the target is 1e-6), and
+    the first layer at which any decision (an index or an accept) differs, if one does."""
     s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N))
+    s64 = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, precision=smcgm.SMC_P_FP64)) if fp64 else None
     L = wl["mcmc_steps"]
     rows, logz = [], 0.0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(max_layers):
-        _, _, lz, done = s.smc_temper_step()
+    cmp = dict(max_rel_h_diff=0.0, max_rel_phi_diff=0.0, first_layer_decisions_differ=None)
+    run_seconds = 0.0
+    for layer in range(max_layers):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h, _, lz, done = s.smc_temper_step()
         logz += lz
         s.smc_resample()
         s.gm_fit()
@@ -277,11 +287,32 @@ def time_layers(wl, N, smcgm, torch, max_layers=60):
         acc, _ = s.smc_move(L, allow_noconv=True)
         e1.record(s.stream)
         torch.cuda.synchronize()
+        run_seconds += time.perf_counter() - t0
         prof = s.smc_profile_query(reset=True)
         rows.append(dict(t=t, ms=e0.elapsed_time(e1), solves=prof["solves"], cg=prof["cg_iterations"], acc=acc))
+        if s64 is not None:
+            h64, _, _, done64 = s64.smc_temper_step()
+            s64.smc_resample()
+            idx_differ = not np.array_equal(s.diagnostics()["indices"], s64.diagnostics()["indices"])
+            s64.gm_fit()
+            acc64, _ = s64.smc_move(L, allow_noconv=True)
+            _, P = s.particles()
+            _, P64 = s64.particles()
+            cmp["max_rel_h_diff"] = max(cmp["max_rel_h_diff"], abs(h - h64) / h64)
+            cmp["max_rel_phi_diff"] = max(cmp["max_rel_phi_diff"],
+                                          float(np.max(np.abs(P - P64) / np.maximum(np.abs(P64), 1e-300))))
+            if cmp["first_layer_decisions_differ"] is None and (idx_differ or acc != acc64 or done != done64):
+                cmp["first_layer_decisions_differ"] = layer
+            if done != done64:
+                break
         if done:
             break
-    seconds = time.perf_counter() - t0
+    if s64 is not None:
+        m, v = s.smc_posterior_moments()
+        m64, v64 = s64.smc_posterior_moments()
+        cmp.update(layers=len(rows), posterior_mean_rel_l2=float(np.linalg.norm(m - m64) / np.linalg.norm(m64)),
+                   posterior_var_rel_l2=float(np.linalg.norm(v - v64) / np.linalg.norm(v64)), target=1e-6)
+        s64.close()
     s.close()
 
     def agg(sel):
@@ -293,9 +324,10 @@ def time_layers(wl, N, smcgm, torch, max_layers=60):
                     acceptance=sum(r["acc"] for r in sel) / len(sel))
     first = agg(rows[:1])
     first["t"] = rows[0]["t"]
-    return dict(count=len(rows), finished=bool(rows[-1]["t"] >= 1.0), moves_per_layer=L, run_seconds=seconds,
-                log_evidence=logz, first=first, t_between_0p1_and_1=agg([r for r in rows if 0.1 < r["t"] < 1.0]),
-                all=agg(rows))
+    out = dict(count=len(rows), finished=bool(rows[-1]["t"] >= 1.0), moves_per_layer=L, run_seconds=run_seconds,
+               log_evidence=logz, first=first, t_between_0p1_and_1=agg([r for r in rows if 0.1 < r["t"] < 1.0]),
+               all=agg(rows))
+    return out, (cmp if s64 is not None else None)
 
 
 def precision_agreement(s64, moves, wl, N, smcgm):
@@ -456,7 +488,7 @@ def run_native(args, rank, world, local):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     for _ in range(e2e_steps):
         s.smc_move_host(Xh, Ph, Xo, Po)
     torch.cuda.synchronize()
@@ -481,7 +513,9 @@ def run_native(args, rank, world, local):
     grad = None
     if not args.no_gradient:
         grad = time_gradient(wl, N, smcgm, torch)
-    layers = None if args.no_layers else time_layers(wl, N, smcgm, torch)
+    layers = posterior = None
+    if not args.no_layers:
+        layers, posterior = time_layers(wl, N, smcgm, torch, fp64=not args.no_fp64)
     small = None
     if not args.no_small:
         small = time_small(args, smcgm, torch, barrier)
@@ -498,7 +532,8 @@ def run_native(args, rank, world, local):
                 roofline=roof, hbm_roofline_step=dict(model_bytes_per_solve=bps, achieved_gbs=step_hbm,
                                                       frac=step_hbm / hbm_peak, peak=hbm_peak),
                 iterations=iters, fp64=fp64,
-                speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, fp64_agreement=agree,
+                speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, posterior_error_vs_fp64=posterior,
+                fp64_agreement=agree,
                 solver_only=forward, e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu,
                 adjoint_gradient=grad, smc_run=layers, small_workload=small)
     print(json.dumps(line), flush=True)

@@ -52,8 +52,9 @@ class _Sampler:
     """Temperatures 0.05, 0.15, ..., 1; the move at layer l takes (l + 1) ms for N * L solves
     and (10 + l) CG iterations per solve."""
 
-    def __init__(self, N=8, d=4, L=10, X=None, P=None):
+    def __init__(self, N=8, d=4, L=10, X=None, P=None, acc_at=None):
         self.N, self.d, self.L, self.stream = N, d, L, None
+        self.acc_at = acc_at or {}
         self.layer, self.t = -1, 0.0
         self.X = np.zeros((N, d)) if X is None else X
         self.P = np.ones(N) if P is None else P
@@ -77,7 +78,10 @@ class _Sampler:
         _Clock.now += self.layer + 1.0
         self.counts["solves"] += self.N * steps
         self.counts["cg"] += self.N * steps * (10 + self.layer)
-        return 0.25, 20
+        return self.acc_at.get(self.layer, 0.25), 20
+
+    def diagnostics(self):
+        return dict(indices=np.arange(self.N))
 
     def smc_forward(self, X, Phi):
         _Clock.now += 4.0
@@ -100,14 +104,17 @@ class _Sampler:
         pass
 
 
-def _smcgm(sampler):
-    return types.SimpleNamespace(Sampler=lambda cfg: sampler, make_config=lambda wl, **kw: None,
+def _smcgm(sampler, fp64_sampler=None):
+    """Stand-in module: make_config returns the precision, Sampler picks the stand-in by it."""
+    return types.SimpleNamespace(Sampler=lambda cfg: fp64_sampler if cfg == 0 else sampler,
+                                 make_config=lambda wl, **kw: kw.get("precision", 1),
                                  SMC_P_FP32_REFINE=1, SMC_P_FP64=0)
 
 
 def test_layers_aggregate_first_window_and_all():
     s = _Sampler()
-    out = bench.time_layers(dict(mcmc_steps=10), 8, _smcgm(s), _Torch)
+    out, cmp = bench.time_layers(dict(mcmc_steps=10), 8, _smcgm(s), _Torch, fp64=False)
+    assert cmp is None
     assert out["count"] == 11 and out["finished"] and out["log_evidence"] == pytest.approx(-5.5)
     # first layer: t = 0.05, 80 solves in 1 ms
     assert out["first"]["t"] == pytest.approx(0.05)
@@ -166,3 +173,23 @@ def test_whole_move_byte_model_by_hand():
     per_cell64 = (14.71 * (6 + 9.25 + 5.25 + lower64) * 4 + 3.155 * (4.25 + 5.25 + lower64) * 4
                   + 3.155 * 52.0 + (16 + 24 + 2.7 * 4 + 16))
     assert bench.model_bytes_per_solve(prof64, 64, 1024) == pytest.approx(per_cell64 * 4096 + 4 * 1024 * 8, rel=1e-12)
+
+
+def test_layers_lockstep_against_fp64():
+    """The mixed-precision run and the FP64 run in lockstep: identical layers give no differing
+    decision; an acceptance rate that differs at layer 3 is reported as the first layer at which
+    decisions differ; the posterior errors are relative L2 norms of the moment differences."""
+    X = np.array([[1.0, 2.0], [3.0, 6.0]])
+    same, cmp = bench.time_layers(dict(mcmc_steps=10), 2, _smcgm(_Sampler(N=2, d=2, X=X), _Sampler(N=2, d=2, X=X)),
+                                  _Torch, fp64=True)
+    assert cmp["first_layer_decisions_differ"] is None and cmp["layers"] == 11
+    assert cmp["posterior_mean_rel_l2"] == 0.0 and cmp["posterior_var_rel_l2"] == 0.0
+    X2 = X.copy()
+    X2[0, 0] += 0.5
+    _, cmp = bench.time_layers(dict(mcmc_steps=10), 2,
+                               _smcgm(_Sampler(N=2, d=2, X=X2, acc_at={3: 0.5}), _Sampler(N=2, d=2, X=X)), _Torch, fp64=True)
+    assert cmp["first_layer_decisions_differ"] == 3
+    m64, m = X.mean(axis=0), X2.mean(axis=0)
+    assert cmp["posterior_mean_rel_l2"] == pytest.approx(np.linalg.norm(m - m64) / np.linalg.norm(m64))
+    v64, v = X.var(axis=0), X2.var(axis=0)
+    assert cmp["posterior_var_rel_l2"] == pytest.approx(np.linalg.norm(v - v64) / np.linalg.norm(v64))
