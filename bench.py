@@ -18,8 +18,10 @@ Beside the headline the line carries: the roofline of the dominant kernel and
 the whole-move HBM byte model, the FP64 solver's rate and its agreement with the
 mixed-precision path, the solver-only rate (smc_forward), the end-to-end rate
 through smc_move_host with host buffers, the adjoint-gradient rate, a whole SMC
-run timed layer by layer, the 64^2 workload on the GPU and on the CPU oracle,
-the SM clocks sampled during the timed region and the CPU oracle baseline.
+run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
+(the posterior error of the mixed-precision run against it), the 64^2 workload on
+the GPU and on the CPU oracle, the SM clocks sampled during the timed region and
+the CPU oracle baseline.
 --no-fp64, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
 """
 import argparse
