@@ -22,7 +22,8 @@ run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
 (the posterior error of the mixed-precision run against it), the 64^2 workload on
 the GPU and on the CPU oracle, the SM clocks sampled during the timed region and
 the CPU oracle baseline.
---no-fp64, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
+--smoother bf16 times the BF16-smoother mode as the headline; --no-fp64, --no-alt-smoother,
+--no-e2e, --no-forward, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
 """
 import argparse
 import json
@@ -56,6 +57,11 @@ def parse():
     ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient timing")
     ap.add_argument("--no-layers", action="store_true", help="skip the whole SMC run timed layer by layer")
     ap.add_argument("--no-small", action="store_true", help="skip the 64^2 workload (GPU and CPU oracle)")
+    ap.add_argument("--smoother", default="fp32", choices=["fp32", "bf16"],
+                    help="face storage of the multigrid smoother in the headline (mixed-precision) sampler")
+    ap.add_argument("--no-alt-smoother", action="store_true", help="skip the timing of the other smoother storage")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (host buffers)")
+    ap.add_argument("--no-forward", action="store_true", help="skip the solver-only leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -363,6 +369,29 @@ def time_small(args, smcgm, torch, barrier):
                 unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
+def time_e2e(s, N, d, steps, torch, barrier, world):
+    """End to end through the C ABI (smc_move_host): every step copies the particles and potentials
+    from pinned host buffers to the device, moves them and copies them back, inside the timed region
+    (wall clock over all steps, after one untimed call)."""
+    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
+    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    X0, P0 = s.particles()
+    Xh.numpy()[:] = X0
+    Ph.numpy()[:] = P0
+    Xo = torch.empty_like(Xh).pin_memory()
+    Po = torch.empty_like(Ph).pin_memory()
+    s.smc_move_host(Xh, Ph, Xo, Po)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.smc_move_host(Xh, Ph, Xo, Po)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
+    return dict(value=whole_job_rate(N * steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
+                d2h_bytes_per_step=N * d * 8 + N * 8, steps=steps)
+
+
 def time_moves(s, steps, warmup, torch, barrier):
     for _ in range(warmup):
         s.smc_move(1, allow_noconv=True)
@@ -457,7 +486,9 @@ def run_native(args, rank, world, local):
     from paper_2503_16028_gb300 import build
     build.build()
     smcgm.load_library()
-    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
+    prec_of = {"fp32": smcgm.SMC_P_FP32_REFINE, "bf16": smcgm.SMC_P_BF16SMOOTH_REFINE}
+    alt = "bf16" if args.smoother == "fp32" else "fp32"
+    s = make_sampler(wl, prec_of[args.smoother], N, smcgm)
     d = s.d
     clocks = ClockSampler(local)
     ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
@@ -468,10 +499,13 @@ def run_native(args, rank, world, local):
     dom_ach = prof["dom_bytes"] / (prof["dom_ms"] / 1000.0) / 1e9 if prof["dom_ms"] > 0 else 0.0
     # DRAM bytes per cell of the dominant kernel from one ncu capture of the current kernel on
     # the 512-particle case, scaled to the average particles of a launch here
-    traffic = TRAFFIC_BYTES_PER_CELL * 65536 * prof["dom_particles"] / max(1, prof["dom_launches"])
+    # (a capture of the FP32-face kernel: none for the BF16-face kernel, whose traffic is reported as null)
+    traffic = (TRAFFIC_BYTES_PER_CELL * 65536 * prof["dom_particles"] / max(1, prof["dom_launches"])
+               if args.smoother == "fp32" else None)
     roof = dict(bound="hbm", achieved=dom_ach, peak=hbm_peak, unit="GB/s", frac=dom_ach / hbm_peak, traffic=traffic,
                 algorithmic_bytes_per_launch=prof["dom_bytes"] / max(1, prof["dom_launches"]),
-                kernel="k_tpre<2,CG> (finest level, CG update + pre-smoothing + restriction, TMA-staged)", peak_source=peak_src,
+                kernel="k_tpre<2,CG> (finest level, CG update + pre-smoothing + restriction, TMA-staged; %s smoother faces)"
+                % args.smoother.upper(), peak_source=peak_src,
                 launches=prof["dom_launches"], ms_per_launch=prof["dom_ms"] / max(1, prof["dom_launches"]))
     bps = model_bytes_per_solve(prof, 256, d)
     step_hbm = bps * N / (ms / args.steps / 1000.0) / 1e9
@@ -479,28 +513,25 @@ def run_native(args, rank, world, local):
                  inner_solves_per_solve=prof["inner_solves"] / max(1, prof["solves"]),
                  residuals_per_solve=prof["residuals"] / max(1, prof["solves"]))
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
-    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
-    X0, P0 = s.particles()
-    Xh.numpy()[:] = X0
-    Ph.numpy()[:] = P0
-    Xo = torch.empty_like(Xh).pin_memory()
-    Po = torch.empty_like(Ph).pin_memory()
-    s.smc_move_host(Xh, Ph, Xo, Po)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_steps = args.steps
-    for _ in range(e2e_steps):
-        s.smc_move_host(Xh, Ph, Xo, Po)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
-    e2e = dict(value=whole_job_rate(N * e2e_steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
-               d2h_bytes_per_step=N * d * 8 + N * 8)
-    forward = time_forward(s, torch)
+    e2e = None if args.no_e2e else time_e2e(s, N, d, args.steps, torch, barrier, world)
+    forward = None if args.no_forward else time_forward(s, torch)
     s.close()
     del s
     torch.cuda.empty_cache()
+    alt_leg = None
+    if not args.no_alt_smoother:
+        sb = make_sampler(wl, prec_of[alt], N, smcgm)
+        msb, profb = time_moves(sb, args.steps, min(args.warmup, 2), torch, barrier)
+        sb.close()
+        msb = max_over_ranks(msb, world, "cuda")
+        dom_b = profb["dom_bytes"] / (profb["dom_ms"] / 1000.0) / 1e9 if profb["dom_ms"] > 0 else 0.0
+        alt_leg = dict(smoother=alt, value=whole_job_rate(N * args.steps, world, msb), unit=UNIT, ms_per_step=msb / args.steps,
+                       cg_per_solve=profb["cg_iterations"] / max(1, profb["solves"]),
+                       inner_solves_per_solve=profb["inner_solves"] / max(1, profb["solves"]),
+                       dominant_kernel=dict(achieved=dom_b, frac=dom_b / hbm_peak,
+                                            algorithmic_bytes_per_launch=profb["dom_bytes"] / max(1, profb["dom_launches"]),
+                                            ms_per_launch=profb["dom_ms"] / max(1, profb["dom_launches"])))
+        torch.cuda.empty_cache()
     fp64 = agree = None
     if not args.no_fp64:
         s64 = make_sampler(wl, smcgm.SMC_P_FP64, N, smcgm)
@@ -528,7 +559,8 @@ def run_native(args, rank, world, local):
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
                 data="synthetic",
                 config=dict(workload=WORKLOAD, particles=N, grid="256x256", kl_modes="128x128", components=8,
-                            observations=64, solver="FP32 MG-PCG (RB-GS 2+2, Galerkin, coarse x2) + FP64 refinement to 1e-10",
+                            observations=64, solver="FP32 MG-PCG (RB-GS 2+2, Galerkin, coarse x2; %s smoother faces) + FP64 refinement to 1e-10"
+                            % args.smoother.upper(),
                             l2="inputs larger than L2 (%.1f GB device working set)" % (s_bytes(N) / 1e9),
                             parallelism="replicas" if world > 1 else "single GPU"),
                 roofline=roof, hbm_roofline_step=dict(model_bytes_per_solve=bps, achieved_gbs=step_hbm,
@@ -536,7 +568,8 @@ def run_native(args, rank, world, local):
                 iterations=iters, fp64=fp64,
                 speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, posterior_error_vs_fp64=posterior,
                 fp64_agreement=agree,
-                solver_only=forward, e2e=e2e, clocks=clk, gpu_launches=prof["launches"], cpu_baseline=cpu,
+                solver_only=forward, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
+                cpu_baseline=cpu,
                 adjoint_gradient=grad, smc_run=layers, small_workload=small)
     print(json.dumps(line), flush=True)
 

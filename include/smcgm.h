@@ -76,8 +76,19 @@ typedef enum { SMC_K_PCN = 0, SMC_K_PCN_GM = 1, SMC_K_GM_INDEP = 2, SMC_K_PCNL =
  * tol_outer / 2 of the right-hand side, whichever comes first);
  * the coefficients (e^u and the harmonic faces) and the residual's products
  * are formed in double-float (pairs of FP32) arithmetic, ~1e-14 relative, and
- * need |u| < 64 (else the call fails; use SMC_P_FP64). */
-typedef enum { SMC_P_FP64 = 0, SMC_P_FP32_REFINE = 1 } smc_precision;
+ * need |u| < 64 (else the call fails; use SMC_P_FP64).
+ * SMC_P_BF16SMOOTH_REFINE: SMC_P_FP32_REFINE with the multigrid smoother's
+ * face coefficients stored in BF16 on every tiled level (n_l > 32): the
+ * red-black Gauss-Seidel sweeps, the V-cycle residuals and the restriction
+ * read the interior west / south faces as BF16 (8-bit significand, converted
+ * to FP32 as they are read; FP32 arithmetic throughout), the wall faces,
+ * right-hand sides and corrections stay FP32.  The faces are fixed during a
+ * solve, so the V-cycle stays a fixed symmetric positive definite
+ * preconditioner of the FP32 CG operator, which keeps its FP32 faces; the
+ * coarse levels (n_l <= 32) keep FP32 faces; the FP64-accurate refinement
+ * is unchanged, so w and Phi meet the same tol_outer.  The paper specifies
+ * no solver: this is a storage precision choice of the preconditioner. */
+typedef enum { SMC_P_FP64 = 0, SMC_P_FP32_REFINE = 1, SMC_P_BF16SMOOTH_REFINE = 2 } smc_precision;
 
 typedef struct smc_config {
     int dim;            /* 1: -(e^u w')' = f on [0,1]; 2: -div(e^u grad w) = f on (0,1)^2 (Sec. 3.2) */

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_grad_u_df(int n, const float2* __restri
 int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out) {
     const int n = c.n;
     const size_t nn = (size_t)n * n;
-    const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
+    const bool mixed = mixed_precision(c.cfg);
     int itmax = 0;
     for (int off = 0; off < count; off += c.B) {
         const int cnt = std::min(c.B, count - off);

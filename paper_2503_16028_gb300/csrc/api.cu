@@ -57,7 +57,7 @@ static const char* validate(const smc_config& c) {
     if (c.kernel < 0 || c.kernel > 4) return "unknown kernel";
     if ((c.kernel == SMC_K_PCNL || c.kernel == SMC_K_GMPCNL) && (!c.gradient || c.dim != 2))
         return "the Langevin kernels need gradient = 1 and dim = 2";
-    if (c.precision < 0 || c.precision > 1) return "unknown precision";
+    if (c.precision < 0 || c.precision > 2) return "unknown precision";
     if (!(c.tol_inner > 0 && c.tol_inner < 1) || !(c.tol_outer > 0 && c.tol_outer < 1)) return "tolerances must be in (0, 1)";
     if (c.max_iter < 1 || c.max_refine < 1) return "max_iter and max_refine must be >= 1";
     if (c.smooth_sweeps != 1 && c.smooth_sweeps != 2) return "smooth_sweeps must be 1 or 2";
@@ -77,7 +77,7 @@ static const char* validate(const smc_config& c) {
 
 template <typename T>
 static void plan_inner(Planner& P, InnerSolver<T>& s, int n, int B, int coarse_top, bool alias0, double* Kw64, double* Ks64,
-                       double* E64, double* N64) {
+                       double* E64, double* N64, bool bf16_faces = false) {
     s.nlev = ilog2(n) + 1;
     int nt = 0;
     for (int l = 0; l < s.nlev; ++l) if ((n >> l) > coarse_top) ++nt;
@@ -98,6 +98,7 @@ static void plan_inner(Planner& P, InnerSolver<T>& s, int n, int B, int coarse_t
         }
         L.e = P.take<T>(cells);
         if (l > 0) { L.r = P.take<T>(cells); L.e2 = P.take<T>(cells); }
+        if (bf16_faces && l < s.ntile_levels) { L.Kwb = P.take<__nv_bfloat16>(cells); L.Ksb = P.take<__nv_bfloat16>(cells); }
     }
     s.list = P.take<int>(B); s.nact = P.take<int>(4);
     s.r[0] = P.take<T>(nn); s.r[1] = P.take<T>(nn);
@@ -144,7 +145,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
         C.u64 = P.take<double>(bn);
         C.fct_tw = P.take<double>(n);
         C.fct_tmp = P.take<double>((size_t)B * n * Km);
-        if (cfg.precision == SMC_P_FP32_REFINE) {
+        if (mixed_precision(cfg)) {
             C.Kwlo = P.take<float>(bn); C.Kslo = P.take<float>(bn);
             C.Elo = P.take<float>((size_t)B * n); C.Nlo = P.take<float>((size_t)B * n);
             C.w64 = P.take<double>(bn);
@@ -177,8 +178,8 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
         s.count = P.take<int>(4);
         // levels with n_l <= coarse_top run in the one-block-per-particle coarse kernel
         const int ctop = 32;
-        if (cfg.precision == SMC_P_FP32_REFINE)
-            plan_inner<float>(P, C.s32, n, B, ctop, false, nullptr, nullptr, nullptr, nullptr);
+        if (mixed_precision(cfg))
+            plan_inner<float>(P, C.s32, n, B, ctop, false, nullptr, nullptr, nullptr, nullptr, bf16_smoother(cfg));
         else
             plan_inner<double>(P, C.s64, n, B, 32, true, C.Kw64, C.Ks64, C.E64, C.N64);
     } else {
@@ -452,7 +453,7 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
         check(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev), "sm count");
     }
     if (c.dim == 2) {
-        if (c.cfg.precision == SMC_P_FP32_REFINE) build_tma_maps<float>(c, c.s32);
+        if (mixed_precision(c.cfg)) build_tma_maps<float>(c, c.s32);
         else build_tma_maps<double>(c, c.s64);
     }
     set_prior_mixture(c);

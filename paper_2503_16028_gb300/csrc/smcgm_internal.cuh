@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -96,7 +97,17 @@ struct LevelArrays {
     T* r = nullptr;   // right-hand side at this level (levels >= 1)
     T* e = nullptr;   // pre-smoothed correction
     T* e2 = nullptr;  // post-smoothed correction (levels >= 1)
+    // SMC_P_BF16SMOOTH_REFINE: BF16 copies of Kw and Ks for the smoother (tiled levels)
+    __nv_bfloat16* Kwb = nullptr;
+    __nv_bfloat16* Ksb = nullptr;
 };
+
+// The mixed-precision solver (FP32 inner solves, FP64-accurate refinement),
+// with FP32 or BF16 smoother faces.
+inline bool mixed_precision(const smc_config& cfg) {
+    return cfg.precision == SMC_P_FP32_REFINE || cfg.precision == SMC_P_BF16SMOOTH_REFINE;
+}
+inline bool bf16_smoother(const smc_config& cfg) { return cfg.precision == SMC_P_BF16SMOOTH_REFINE; }
 
 struct SolverScalars {       // per particle, device
     double *rz, *rr0, *rr, *pq, *alpha, *betac, *res2, *b2;
@@ -108,6 +119,7 @@ struct SolverScalars {       // per particle, device
 // Tensor maps of the TMA-staged smoothing kernels (FP32 inner solver).
 struct TmaMaps {
     CUtensorMap kw[12], ks[12], r[12], e[12], ec[12];   // per tiled level
+    CUtensorMap kwb[12], ksb[12];                        // BF16 smoother faces (SMC_P_BF16SMOOTH_REFINE)
     CUtensorMap r0[2], q, x, p[2];                       // finest level, CG vectors
 };
 

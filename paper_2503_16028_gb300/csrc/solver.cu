@@ -44,12 +44,14 @@ __global__ void k_exp_neg(double* __restrict__ u, size_t total) {
 struct FaceOut {
     double* f64;
     float *hi, *lo;
+    __nv_bfloat16* bf = nullptr;   // the BF16 smoother's copy of hi (interior faces)
     __device__ void put(size_t i, double v) const {
         if (f64) f64[i] = v;
         if (hi) {
             const float h = __double2float_rn(v);
             hi[i] = h;
             if (lo) lo[i] = __double2float_rn(v - (double)h);
+            if (bf) bf[i] = __float2bfloat16_rn(h);
         }
     }
 };
@@ -81,12 +83,14 @@ __global__ void k_faces(int n, int count, const double* __restrict__ s, FaceOut 
 // 2 / (s_c + s_nb) (2 / s_c on a wall) and the east / north wall faces.  The
 // high parts are the inner solver's FP32 faces, the low parts complete them
 // to ~1e-14 relative for the FP64-accurate residual.  |u| >= 64 (beyond the
-// FP32 range of e^u) sets err[1] and is reported by the host.
+// FP32 range of e^u) sets err[1] and is reported by the host.  With Kwb, Ksb
+// (the BF16 smoother faces) the interior faces are also stored rounded to BF16.
 constexpr int FX = 32, FY = 8;
 __global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __restrict__ u, const float2* __restrict__ exptab,
                                                       ExpConsts ec, float* __restrict__ Kwh, float* __restrict__ Kwl,
                                                       float* __restrict__ Ksh, float* __restrict__ Ksl, float* __restrict__ Eh,
                                                       float* __restrict__ El, float* __restrict__ Nh, float* __restrict__ Nl,
+                                                      __nv_bfloat16* __restrict__ Kwb, __nv_bfloat16* __restrict__ Ksb,
                                                       int* __restrict__ err, int* __restrict__ badp) {
     __shared__ float2 tab[64];
     __shared__ float2 S[FY + 1][FX + 1];
@@ -129,15 +133,17 @@ __global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __res
     if (j > 0) { const float2 s2 = S[ly][lx + 1]; ks = df_two_over(df_add(sc, df32{s2.x, s2.y})); }
     Kwh[t] = kw.hi; Kwl[t] = kw.lo;
     Ksh[t] = ks.hi; Ksl[t] = ks.lo;
+    if (Kwb) { Kwb[t] = __float2bfloat16_rn(kw.hi); Ksb[t] = __float2bfloat16_rn(ks.hi); }
     if (i == n - 1) { Eh[(size_t)p * n + j] = wall.hi; El[(size_t)p * n + j] = wall.lo; }
     if (j == n - 1) { Nh[(size_t)p * n + i] = wall.hi; Nl[(size_t)p * n + i] = wall.lo; }
 }
 
-// Galerkin coarsening for piecewise-constant prolongation.
+// Galerkin coarsening for piecewise-constant prolongation; with Kwcb, Kscb the
+// coarse interior faces are also stored rounded to BF16 (the BF16 smoother).
 template <typename T>
 __global__ void k_coarsen(int m, int count, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E,
                           const T* __restrict__ Nn, T* __restrict__ Kwc, T* __restrict__ Ksc, T* __restrict__ Ec,
-                          T* __restrict__ Nnc) {
+                          T* __restrict__ Nnc, __nv_bfloat16* __restrict__ Kwcb, __nv_bfloat16* __restrict__ Kscb) {
     const int n = 2 * m;
     const size_t mm = (size_t)m * m, nn = (size_t)n * n;
     const size_t total = mm * count;
@@ -149,8 +155,11 @@ __global__ void k_coarsen(int m, int count, const T* __restrict__ Kw, const T* _
         const int I = c % m, J = c / m;
         const T* kw = Kw + p * nn;
         const T* ks = Ks + p * nn;
-        Kwc[t] = kw[(2 * J) * n + 2 * I] + kw[(2 * J + 1) * n + 2 * I];
-        Ksc[t] = ks[(2 * J) * n + 2 * I] + ks[(2 * J) * n + 2 * I + 1];
+        const T kwv = kw[(2 * J) * n + 2 * I] + kw[(2 * J + 1) * n + 2 * I];
+        const T ksv = ks[(2 * J) * n + 2 * I] + ks[(2 * J) * n + 2 * I + 1];
+        Kwc[t] = kwv;
+        Ksc[t] = ksv;
+        if (Kwcb) { Kwcb[t] = __float2bfloat16_rn((float)kwv); Kscb[t] = __float2bfloat16_rn((float)ksv); }
         if (I == m - 1) Ec[p * m + J] = E[p * n + 2 * J] + E[p * n + 2 * J + 1];
         if (J == m - 1) Nnc[p * m + I] = Nn[p * n + 2 * I] + Nn[p * n + 2 * I + 1];
     }
@@ -835,19 +844,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 static inline int wtiles(int n) { return (n / WT) * (n / WT); }
 
-// 3-D map over a particle-major [B][n][n] FP32 array, box bx x by x 1 (x innermost).
-static CUtensorMap make_map(const float* base, int n, int B, int bx, int by) {
+// 3-D map over a particle-major [B][n][n] array of FP32 (es = 4) or BF16 (es = 2)
+// values, box bx x by x 1 (x innermost).
+static CUtensorMap make_map_es(const void* base, int es_bytes, int n, int B, int bx, int by) {
     CUtensorMap m;
     cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)B};
-    cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(float), (cuuint64_t)n * n * sizeof(float)};
+    cuuint64_t strides[2] = {(cuuint64_t)n * es_bytes, (cuuint64_t)n * n * es_bytes};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+    const CUtensorMapDataType dt = es_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    if ((bx * es_bytes) % 16 != 0) throw CudaError{cudaErrorInvalidValue, "tensor map box row not a multiple of 16 bytes"};
+    const CUresult r = tensor_map_encoder()(&m, dt, 3, const_cast<void*>(base), dims, strides, box,
                                             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
     return m;
 }
+static CUtensorMap make_map(const float* base, int n, int B, int bx, int by) { return make_map_es(base, 4, n, B, bx, by); }
 
 // Halo (2 nu) of the tiled level l: the finest level uses fine_sweeps, the others smooth_sweeps.
 static inline int level_halo(const Ctx& c, int l) { return 2 * (l == 0 ? c.cfg.fine_sweeps : c.cfg.smooth_sweeps); }
@@ -855,9 +868,14 @@ static inline int level_halo(const Ctx& c, int l) { return 2 * (l == 0 ? c.cfg.f
 template <int H>
 static void level_maps(TmaMaps& M, InnerSolver<float>& s, int B, int l) {
     using G = TGeo<H>;
+    using GB = TGeo<H, 2>;
     LevelArrays<float>& L = s.lv[l];
-    M.kw[l] = make_map(L.Kw, L.n, B, G::KWX, G::RW);
-    M.ks[l] = make_map(L.Ks, L.n, B, G::BX, G::RW + 1);
+    M.kw[l] = make_map(L.Kw, L.n, B, G::KWE, G::RW);
+    M.ks[l] = make_map(L.Ks, L.n, B, G::KSE, G::RW + 1);
+    if (L.Kwb) {
+        M.kwb[l] = make_map_es(L.Kwb, 2, L.n, B, GB::KWE, GB::RW);
+        M.ksb[l] = make_map_es(L.Ksb, 2, L.n, B, GB::KSE, GB::RW + 1);
+    }
     M.e[l] = make_map(L.e, L.n, B, G::BX, G::RW);
     if (l > 0) M.r[l] = make_map(L.r, L.n, B, G::BX, G::RW);
     M.ec[l] = make_map(s.lv[l + 1].e2, s.lv[l + 1].n, B, G::CX, G::CY);
@@ -899,10 +917,11 @@ static inline int persistent_grid(int total_warps, int per_sm, int sms) {
 }
 
 // Pre-smoothing pass of the TMA-staged path on level `level`; cg = 1 only on the finest level.
-template <int H, bool CG, int MINB>
+// FB = 2: the smoother reads the BF16 interior faces.
+template <int H, bool CG, int MINB, int FB>
 static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
                           int want_rr, int pc) {
-    static const int per_sm = staged_occupancy(k_tpre<H, CG, MINB>, tpre_smem<H, CG>());
+    static const int per_sm = staged_occupancy(k_tpre<H, CG, MINB, FB>, tpre_smem<H, CG, FB>());
     LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
     WPreArgs<float> A{};
@@ -910,32 +929,38 @@ static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, co
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = s.p[pc];
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
     A.cg = CG ? 1 : 0; A.want_rr = want_rr;
-    k_tpre<H, CG, MINB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpre_smem<H, CG>(), c.stream>>>(
-        A, M.kw[level], M.ks[level], mr, M.q, M.x, M.p[pc]); ++c.pc.launches;
+    const CUtensorMap& mkw = FB == 2 ? M.kwb[level] : M.kw[level];
+    const CUtensorMap& mks = FB == 2 ? M.ksb[level] : M.ks[level];
+    k_tpre<H, CG, MINB, FB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpre_smem<H, CG, FB>(), c.stream>>>(
+        A, mkw, mks, mr, M.q, M.x, M.p[pc]); ++c.pc.launches;
 }
 template <int H, bool CG>
 static void launch_tpre(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
                         int want_rr, int pc) {
     // blocks per SM asked of the register allocator: 4 (<= 128 registers, 16 warps) on a
     // 20 x 20 region, 2 on the 24 x 24 region of two sweeps
-    launch_tpre_b<H, CG, H == 2 ? 4 : 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
+    if (s.lv[level].Kwb) launch_tpre_b<H, CG, H == 2 ? 4 : 2, 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
+    else launch_tpre_b<H, CG, H == 2 ? 4 : 2, 4>(c, s, level, nact, mr, rin, rout, want_rr, pc);
 }
 
-template <int H, bool CG, int MINB>
+template <int H, bool CG, int MINB, int FB>
 static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
-    static const int per_sm = staged_occupancy(k_tpost<H, CG, MINB>, tpost_smem<H>());
+    static const int per_sm = staged_occupancy(k_tpost<H, CG, MINB, FB>, tpost_smem<H, FB>());
     LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
     WPostArgs<float> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (float)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = CG ? 1 : 0;
-    k_tpost<H, CG, MINB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpost_smem<H>(), c.stream>>>(
-        A, M.kw[level], M.ks[level], mr, M.e[level], M.ec[level]); ++c.pc.launches;
+    const CUtensorMap& mkw = FB == 2 ? M.kwb[level] : M.kw[level];
+    const CUtensorMap& mks = FB == 2 ? M.ksb[level] : M.ks[level];
+    k_tpost<H, CG, MINB, FB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpost_smem<H, FB>(), c.stream>>>(
+        A, mkw, mks, mr, M.e[level], M.ec[level]); ++c.pc.launches;
 }
 template <int H, bool CG>
 static void launch_tpost(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
-    launch_tpost_b<H, CG, H == 2 ? 4 : 2>(c, s, level, nact, mr, r, eout);
+    if (s.lv[level].Kwb) launch_tpost_b<H, CG, H == 2 ? 4 : 2, 2>(c, s, level, nact, mr, r, eout);
+    else launch_tpost_b<H, CG, H == 2 ? 4 : 2, 4>(c, s, level, nact, mr, r, eout);
 }
 
 template <typename T, int NU>
@@ -999,9 +1024,18 @@ static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T*
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
-    A.cg = cg; A.want_rr = want_rr;
-    if (cg) k_wpre<T, H, true><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
-    else k_wpre<T, H, false><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    A.cg = cg; A.want_rr = want_rr; A.Kwb = L.Kwb; A.Ksb = L.Ksb;
+    const int grid = (A.a.total + WPB - 1) / WPB;
+    if constexpr (sizeof(T) == 4) {
+        if (L.Kwb) {   // the BF16 smoother faces
+            if (cg) k_wpre<T, H, true, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+            else k_wpre<T, H, false, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+            ++c.pc.launches;
+            return;
+        }
+    }
+    if (cg) k_wpre<T, H, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+    else k_wpre<T, H, false><<<grid, 32 * WPB, 0, c.stream>>>(A);
     ++c.pc.launches;
 }
 
@@ -1011,9 +1045,18 @@ static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T
     WPostArgs<T> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
-    A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg;
-    if (cg) k_wpost<T, H, true><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
-    else k_wpost<T, H, false><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A);
+    A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg; A.Kwb = L.Kwb; A.Ksb = L.Ksb;
+    const int grid = (A.a.total + WPB - 1) / WPB;
+    if constexpr (sizeof(T) == 4) {
+        if (L.Kwb) {   // the BF16 smoother faces
+            if (cg) k_wpost<T, H, true, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+            else k_wpost<T, H, false, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+            ++c.pc.launches;
+            return;
+        }
+    }
+    if (cg) k_wpost<T, H, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+    else k_wpost<T, H, false><<<grid, 32 * WPB, 0, c.stream>>>(A);
     ++c.pc.launches;
 }
 
@@ -1182,7 +1225,8 @@ static int inner_solve(Ctx& c, InnerSolver<T>& s, int count, double tol, double 
     P.lower(nact);
     P.post(nact, cur);
     k_scalar<<<wgrid, 128, 0, c.stream>>>(SM_RZ_FIRST, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
-    const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T);   // per cell: r,q,x,p,Kw,Ks in; r,x,e,rc out
+    // per cell: r, q, x, p, Kw, Ks in (the faces 2 bytes each with the BF16 smoother); r, x, e, rc out
+    const double dom_bpc = (double)(6 * sizeof(T) + 3 * sizeof(T)) + 0.25 * sizeof(T) - (s.lv[0].Kwb ? 2.0 * (sizeof(T) - 2) : 0.0);
     for (int it = 0; it < maxit; ++it) {
         P.apply(nact, pc, it == 0);
         pc ^= 1;
@@ -1235,7 +1279,8 @@ void launch_coarsen_all(Ctx& c, InnerSolver<T>& s, int count) {
         LevelArrays<T>& A = s.lv[l];
         LevelArrays<T>& Bc = s.lv[l + 1];
         const size_t total = (size_t)Bc.n * Bc.n * count;
-        k_coarsen<T><<<grid_for(total), 256, 0, c.stream>>>(Bc.n, count, A.Kw, A.Ks, A.E, A.Nn, Bc.Kw, Bc.Ks, Bc.E, Bc.Nn); ++c.pc.launches;
+        k_coarsen<T><<<grid_for(total), 256, 0, c.stream>>>(Bc.n, count, A.Kw, A.Ks, A.E, A.Nn, Bc.Kw, Bc.Ks, Bc.E, Bc.Nn,
+                                                            Bc.Kwb, Bc.Ksb); ++c.pc.launches;
     }
 }
 template void launch_coarsen_all<float>(Ctx&, InnerSolver<float>&, int);
@@ -1244,21 +1289,22 @@ template void launch_coarsen_all<double>(Ctx&, InnerSolver<double>&, int);
 void launch_setup_coeffs(Ctx& c, int count) {
     const int n = c.n;
     const size_t total = (size_t)n * n * count;
-    const bool mixed = c.cfg.precision == SMC_P_FP32_REFINE;
+    const bool mixed = mixed_precision(c.cfg);
     if (mixed && n % FX == 0 && n % FY == 0) {
         LevelArrays<float>& f0 = c.s32.lv[0];
         check(cudaMemsetAsync(c.badp, 0, count * sizeof(int), c.stream), "memset badp");
         k_faces_df<<<dim3((n / FX) * (n / FY), count), FX * FY, 0, c.stream>>>(
             n, reinterpret_cast<const float2*>(c.u64), reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
-            c.dev_err, c.badp); ++c.pc.launches;
+            f0.Kwb, f0.Ksb, c.dev_err, c.badp); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
         return;
     }
     k_exp_neg<<<grid_for(total), 256, 0, c.stream>>>(c.u64, total); ++c.pc.launches;
     if (mixed) {
         LevelArrays<float>& f0 = c.s32.lv[0];
-        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, FaceOut{nullptr, f0.Kw, c.Kwlo}, FaceOut{nullptr, f0.Ks, c.Kslo},
-                                                       FaceOut{nullptr, f0.E, c.Elo}, FaceOut{nullptr, f0.Nn, c.Nlo}); ++c.pc.launches;
+        k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, FaceOut{nullptr, f0.Kw, c.Kwlo, f0.Kwb},
+                                                       FaceOut{nullptr, f0.Ks, c.Kslo, f0.Ksb}, FaceOut{nullptr, f0.E, c.Elo},
+                                                       FaceOut{nullptr, f0.Nn, c.Nlo}); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
     } else {
         k_faces<<<grid_for(total), 256, 0, c.stream>>>(n, count, c.u64, FaceOut{c.Kw64, nullptr, nullptr}, FaceOut{c.Ks64, nullptr, nullptr},
@@ -1334,12 +1380,12 @@ __global__ void k_mark_out_of_range(int count, const int* __restrict__ badp, dou
 }
 
 void launch_mark_out_of_range(Ctx& c, int count, double* Phi) {
-    if (!c.lenient || !c.badp || c.cfg.precision != SMC_P_FP32_REFINE) return;
+    if (!c.lenient || !c.badp || !mixed_precision(c.cfg)) return;
     k_mark_out_of_range<<<(count + 127) / 128, 128, 0, c.stream>>>(count, c.badp, Phi); ++c.pc.launches;
 }
 
 int solve_batch(Ctx& c, int count, const Rhs& R, double* W) {
-    return c.cfg.precision == SMC_P_FP32_REFINE ? solve_batch_t<float>(c, c.s32, count, R, W)
+    return mixed_precision(c.cfg) ? solve_batch_t<float>(c, c.s32, count, R, W)
                                                  : solve_batch_t<double>(c, c.s64, count, R, W);
 }
 
@@ -1353,7 +1399,7 @@ int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w
     for (int off = 0; off < count; off += c.B) {
         const int cnt = std::min(c.B, count - off);
         // the mixed-precision set-up takes the field as df32 pairs (in the FP64 field's storage)
-        if (c.cfg.precision == SMC_P_FP32_REFINE && c.n % FX == 0 && c.n % FY == 0)
+        if (mixed_precision(c.cfg) && c.n % FX == 0 && c.n % FY == 0)
             launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
         else
             launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);

@@ -356,7 +356,7 @@ static void launch_fct_t(Ctx& c, const double* g, int count, typename O::V* tmp,
 // G = S^T g for `count` grids (FP64 in and out), in df32 for the mixed-precision
 // context (inputs and outputs FP64, ~1e-13 relative) and FP64 otherwise.
 void launch_analysis2d(Ctx& c, const double* g, int count, double* G) {
-    if (c.cfg.precision == SMC_P_FP32_REFINE)
+    if (mixed_precision(c.cfg))
         launch_fct_t<DfOps>(c, g, count, reinterpret_cast<df32*>(c.fct_tmp), G, reinterpret_cast<const float2*>(c.fct_tw_df));
     else
         launch_fct_t<F64Ops>(c, g, count, c.fct_tmp, G, c.fct_tw);

@@ -17,7 +17,9 @@
 // edge and moves one cell per half-sweep, which the halo H = 2 nu keeps out of
 // the tile interior (the first pre-smoothing half-sweep is pointwise from zero).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace smcgm {
 
@@ -110,6 +112,19 @@ __device__ inline void st2(T* p, T a, T b) {
     *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
 }
 
+// Face coefficients as stored (the solver's own type, or BF16 for the BF16
+// smoother) read as the solver's type: a pair at an even cell, or one value.
+template <typename T>
+__device__ inline void ldf2(const T* p, T& a, T& b) { ld2(p, a, b); }
+__device__ inline void ldf2(const __nv_bfloat16* p, float& a, float& b) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    a = v.x;
+    b = v.y;
+}
+template <typename T>
+__device__ inline T ldf1(const T* p) { return *p; }
+__device__ inline float ldf1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
 // Sum over the warp in the solver's own precision (a tile's partial of a CG
 // dot product: FP32 for the FP32 solver, keeping the FP64 pipe free), widened
 // to double for the per-particle sums over tiles.
@@ -135,15 +150,15 @@ struct WRaw {
     T s0, s1, m0, m1, t0, t1;      // south faces rows gy, gy+1, gy+2 (north of gy+1)
 };
 
-template <typename T>
-__device__ inline void load_faces_raw(WRaw<T>& R, const T* kw, const T* ks, const T* E, const T* Nn, int n, int gx, int gy) {
-    ld2(kw + (size_t)gy * n + gx, R.a0, R.a1);
-    ld2(kw + (size_t)(gy + 1) * n + gx, R.b0, R.b1);
-    R.ea = gx + 2 < n ? kw[(size_t)gy * n + gx + 2] : E[gy];
-    R.eb = gx + 2 < n ? kw[(size_t)(gy + 1) * n + gx + 2] : E[gy + 1];
-    ld2(ks + (size_t)gy * n + gx, R.s0, R.s1);
-    ld2(ks + (size_t)(gy + 1) * n + gx, R.m0, R.m1);
-    if (gy + 2 < n) ld2(ks + (size_t)(gy + 2) * n + gx, R.t0, R.t1);
+template <typename T, typename F>
+__device__ inline void load_faces_raw(WRaw<T>& R, const F* kw, const F* ks, const T* E, const T* Nn, int n, int gx, int gy) {
+    ldf2(kw + (size_t)gy * n + gx, R.a0, R.a1);
+    ldf2(kw + (size_t)(gy + 1) * n + gx, R.b0, R.b1);
+    R.ea = gx + 2 < n ? ldf1(kw + (size_t)gy * n + gx + 2) : E[gy];
+    R.eb = gx + 2 < n ? ldf1(kw + (size_t)(gy + 1) * n + gx + 2) : E[gy + 1];
+    ldf2(ks + (size_t)gy * n + gx, R.s0, R.s1);
+    ldf2(ks + (size_t)(gy + 1) * n + gx, R.m0, R.m1);
+    if (gy + 2 < n) ldf2(ks + (size_t)(gy + 2) * n + gx, R.t0, R.t1);
     else { R.t0 = Nn[gx]; R.t1 = Nn[gx + 1]; }
 }
 
@@ -215,6 +230,7 @@ struct WPreArgs {
     const double* alpha;
     double* part_rr;
     int cg, want_rr;
+    const __nv_bfloat16 *Kwb, *Ksb;   // BF16 smoother faces (kernels instantiated for them)
 };
 
 template <typename T>
@@ -225,14 +241,17 @@ struct WPostArgs {
     T* e_out;
     double* part_rz;
     int cg;
+    const __nv_bfloat16 *Kwb, *Ksb;
 };
 
 // Inputs of one work item read straight from global memory.  (x0, y0) is the
-// tile origin; every quad asked for lies inside the grid.
-template <typename T>
+// tile origin; every quad asked for lies inside the grid.  F: the storage
+// type of the interior faces kw, ks (T, or BF16 for the BF16 smoother).
+template <typename T, typename F = T>
 struct GlobalSrc {
     static constexpr bool COMBINE_EARLY = false;
-    const T *kw, *ks, *Ep, *Np, *a, *b, *x, *p;   // a: r, b: q (pre) or e_in (post)
+    const F *kw, *ks;
+    const T *Ep, *Np, *a, *b, *x, *p;   // a: r, b: q (pre) or e_in (post)
     int n;
     __device__ void faces(WRaw<T>& R, int gx, int gy) const { load_faces_raw(R, kw, ks, Ep, Np, n, gx, gy); }
     __device__ void va(T* v, int gx, int gy) const {
@@ -258,10 +277,10 @@ struct GlobalSrc {
         const int gi = gy * n + gx;
         rv = a[gi];
         qv = withq ? b[gi] : T(0);
-        fw = kw[gi];
-        fe = gx + 1 < n ? kw[gi + 1] : Ep[gy];
-        fs = ks[gi];
-        fn = gy + 1 < n ? ks[gi + n] : Np[gx];
+        fw = ldf1(kw + gi);
+        fe = gx + 1 < n ? ldf1(kw + gi + 1) : Ep[gy];
+        fs = ldf1(ks + gi);
+        fn = gy + 1 < n ? ldf1(ks + gi + n) : Np[gx];
     }
 };
 
@@ -515,10 +534,28 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
     }
 }
 
-// One warp per work item, inputs loaded from global memory.
-template <typename T, int H, bool CG>
-__global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
+template <typename F>
+struct FacePtrs {
+    const F *kw, *ks;
+};
+template <typename F>
+__device__ inline FacePtrs<F> make_pair_ptr(const F* kw, const F* ks) { return FacePtrs<F>{kw, ks}; }
+
+// The interior faces a warp kernel reads: the solver's own, or the BF16 copies.
+template <typename T, bool BF, class A>
+__device__ inline auto smoother_faces(const A& args, size_t base) {
+    if constexpr (BF) return make_pair_ptr(args.Kwb + base, args.Ksb + base);
+    else return make_pair_ptr(args.Kw + base, args.Ks + base);
+}
+
+// One warp per work item, inputs loaded from global memory.  BF: the
+// smoother's interior faces are the BF16 copies (FP32 solver only); the
+// lower levels' BF16 pre-smoothing is held to 128 registers (16 warps per SM,
+// as the FP32 kernel).
+template <typename T, int H, bool CG, bool BF = false>
+__global__ void __launch_bounds__(32 * WPB, (BF && !CG) ? 4 : 0) k_wpre(WPreArgs<T> A) {
     using G = WGeo<T, H>;
+    using F = typename std::conditional<BF, __nv_bfloat16, T>::type;
     __shared__ T sme[WPB][G::EN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WPB + warp;
@@ -528,14 +565,16 @@ __global__ void __launch_bounds__(32 * WPB) k_wpre(WPreArgs<T> A) {
     const int p = A.a.list[pi];
     const int tpr = n / WT;
     const size_t base = (size_t)p * n * n;
-    GlobalSrc<T> S{A.Kw + base, A.Ks + base, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.rin + base, A.q + base,
-                   A.x + base, A.p + base, n};
+    const auto fc = smoother_faces<T, BF>(A, base);
+    GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.rin + base, A.q + base,
+                      A.x + base, A.p + base, n};
     wpre_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
 }
 
-template <typename T, int H, bool CG>
+template <typename T, int H, bool CG, bool BF = false>
 __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     using G = WGeo<T, H>;
+    using F = typename std::conditional<BF, __nv_bfloat16, T>::type;
     __shared__ T sme[WPB][G::EN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WPB + warp;
@@ -545,8 +584,9 @@ __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     const int p = A.a.list[pi];
     const int tpr = n / WT;
     const size_t base = (size_t)p * n * n;
-    GlobalSrc<T> S{A.Kw + base, A.Ks + base, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.r + base, A.e_in + base,
-                   A.ec + (size_t)p * m * m, nullptr, n};
+    const auto fc = smoother_faces<T, BF>(A, base);
+    GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.r + base, A.e_in + base,
+                      A.ec + (size_t)p * m * m, nullptr, n};
     wpost_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
 }
 

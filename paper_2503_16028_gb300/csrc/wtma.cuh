@@ -12,7 +12,10 @@
 // Boxes start at x = 16 tx - 4 (16-byte aligned) and y = 16 ty - H; cells
 // outside the grid arrive as zeros, and the wall faces (east and north) are
 // read from the 1-D wall arrays.  The parent box of the prolongation starts at
-// x = 8 tx - 4, y = 8 ty - H/2 on the next coarser grid.
+// x = 8 tx - 4, y = 8 ty - H/2 on the next coarser grid.  With the BF16
+// smoother the interior-face boxes hold 2-byte values; a box must start on a
+// 16-byte boundary, so they start at x = 16 tx - 8 (a multiple of 8 values)
+// and span 32 values (64 bytes) per row.
 #pragma once
 #include "tma.cuh"
 #include "wtiles.cuh"
@@ -23,25 +26,32 @@ constexpr int TW_WARPS = 4;       // warps per block of the staged kernels
 
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Staged box geometry (floats) of a region with halo H.
-template <int H>
+// Staged box geometry of a region with halo H; FB: bytes per stored interior
+// face (4: FP32, 2: BF16).  Offsets count floats from the staging buffer's start.
+template <int H, int FB = 4>
 struct TGeo {
+    static_assert(FB == 4 || FB == 2, "FP32 or BF16 faces");
     static constexpr int RW = WT + 2 * H;                    // region edge
-    static constexpr int KWX = round_up(WT + H + 1 + 4, 4);  // west faces: columns 16 tx - 4 .. 16 tx + 16 + H
-    static constexpr int BX = round_up(WT + H + 4, 4);       // r, q, e, south faces: to column 16 tx + 15 + H
+    static constexpr int BX = round_up(WT + H + 4, 4);       // r, q, e: columns 16 tx - 4 .. 16 tx + 15 + H
+    static constexpr int FXO = FB == 4 ? 4 : 8;              // face boxes start at column 16 tx - FXO
+    static constexpr int FA = 16 / FB;                       // values per 16 bytes
+    static constexpr int KWE = round_up(WT + H + 1 + FXO, FA);   // west faces: columns 16 tx - FXO .. 16 tx + 16 + H
+    static constexpr int KSE = round_up(WT + H + FXO, FA);       // south faces: to column 16 tx + 15 + H
     static constexpr int CX = 16;                            // parent box: columns 8 tx - 4 .. 8 tx + 11
     static constexpr int CY = RW / 2;                        // parent box rows
-    static constexpr int KW_OFF = 0;                                   // every box 128-byte aligned
-    static constexpr int KS_OFF = KW_OFF + round_up(RW * KWX, 32);     // south faces: RW + 1 rows
-    static constexpr int R_OFF = KS_OFF + round_up((RW + 1) * BX, 32);
+    static constexpr int KW_OFF = 0;                                          // every box 128-byte aligned
+    static constexpr int KS_OFF = KW_OFF + round_up(RW * KWE * FB / 4, 32);   // south faces: RW + 1 rows
+    static constexpr int R_OFF = KS_OFF + round_up((RW + 1) * KSE * FB / 4, 32);
     static constexpr int V_OFF = R_OFF + round_up(RW * BX, 32);        // pre: q; post: e_in
     static constexpr int X_OFF = V_OFF + round_up(RW * BX, 32);        // pre: x (tile); post: parent e
     static constexpr int P_OFF = X_OFF + round_up(WT * WT, 32);        // pre: p (tile)
     static constexpr int PRE_STAGE = V_OFF;                            // without the CG vectors
     static constexpr int PRE_CG_STAGE = P_OFF + round_up(WT * WT, 32);
     static constexpr int POST_STAGE = X_OFF + round_up(CY * CX, 32);
-    static constexpr uint32_t FACE_BYTES = 4u * (RW * KWX + (RW + 1) * BX);
+    static constexpr uint32_t FACE_BYTES = (uint32_t)FB * (RW * KWE + (RW + 1) * KSE);
     static constexpr uint32_t REGION_BYTES = 4u * (RW * BX);
+    static_assert((KWE * FB) % 16 == 0 && (KSE * FB) % 16 == 0, "box rows are whole 16-byte units");
+    static_assert((FXO * FB) % 16 == 0, "face box origin 16 tx - FXO on a 16-byte boundary");
 };
 
 // Per-warp shared memory: the staging buffer, the correction array, the mbarrier.
@@ -53,25 +63,27 @@ struct TLayout {
     static constexpr size_t block_bytes() { return (size_t)TW_WARPS * WARP * 4 + 128; }
 };
 
-// Inputs of one work item read from its staging buffer.
-template <int H>
+// Inputs of one work item read from its staging buffer.  F: the storage type
+// of the interior faces (float, or BF16 for the BF16 smoother).
+template <int H, typename F = float>
 struct StagedSrc {
     static constexpr bool COMBINE_EARLY = true;
-    using G = TGeo<H>;
-    const float *kw, *ks, *a, *b, *x, *p;   // a: r; b: q (pre) or e_in (post); x: x (pre) or parent e (post)
+    using G = TGeo<H, (int)sizeof(F)>;
+    const F *kw, *ks;                       // interior-face boxes (origin column x0 + 4 - FXO)
+    const float *a, *b, *x, *p;             // a: r; b: q (pre) or e_in (post); x: x (pre) or parent e (post)
     const float *Ep, *Np;                   // wall faces of the particle (global)
     int n, x0, y0, tx0, ty0, cx0, cy0;     // box origins: region, tile, parent
     __device__ void faces(WRaw<float>& R, int gx, int gy) const {
-        const int bx = gx - x0, by = gy - y0;
-        const float* k0 = kw + by * G::KWX + bx;
-        ld2(k0, R.a0, R.a1);
-        ld2(k0 + G::KWX, R.b0, R.b1);
-        R.ea = gx + 2 < n ? k0[2] : Ep[gy];
-        R.eb = gx + 2 < n ? k0[G::KWX + 2] : Ep[gy + 1];
-        const float* s0 = ks + by * G::BX + bx;
-        ld2(s0, R.s0, R.s1);
-        ld2(s0 + G::BX, R.m0, R.m1);
-        if (gy + 2 < n) ld2(s0 + 2 * G::BX, R.t0, R.t1);
+        const int bx = gx - x0 + (G::FXO - 4), by = gy - y0;
+        const F* k0 = kw + by * G::KWE + bx;
+        ldf2(k0, R.a0, R.a1);
+        ldf2(k0 + G::KWE, R.b0, R.b1);
+        R.ea = gx + 2 < n ? ldf1(k0 + 2) : Ep[gy];
+        R.eb = gx + 2 < n ? ldf1(k0 + G::KWE + 2) : Ep[gy + 1];
+        const F* s0 = ks + by * G::KSE + bx;
+        ldf2(s0, R.s0, R.s1);
+        ldf2(s0 + G::KSE, R.m0, R.m1);
+        if (gy + 2 < n) ldf2(s0 + 2 * G::KSE, R.t0, R.t1);
         else { R.t0 = Np[gx]; R.t1 = Np[gx + 1]; }
     }
     __device__ void va(float* v, int gx, int gy) const {
@@ -94,13 +106,13 @@ struct StagedSrc {
     __device__ float parent(int, int gx, int gy) const { return x[((gy >> 1) - cy0) * G::CX + (gx >> 1) - cx0]; }
     // right-hand side (and q) and the four faces of the single cell (gx, gy)
     __device__ void cell(int gx, int gy, bool withq, float& rv, float& qv, float& fw, float& fe, float& fs, float& fn) const {
-        const int bx = gx - x0, by = gy - y0;
+        const int bx = gx - x0, by = gy - y0, fx = bx + (G::FXO - 4);
         rv = a[by * G::BX + bx];
         qv = withq ? b[by * G::BX + bx] : 0.f;
-        fw = kw[by * G::KWX + bx];
-        fe = gx + 1 < n ? kw[by * G::KWX + bx + 1] : Ep[gy];
-        fs = ks[by * G::BX + bx];
-        fn = gy + 1 < n ? ks[(by + 1) * G::BX + bx] : Np[gx];
+        fw = ldf1(kw + by * G::KWE + fx);
+        fe = gx + 1 < n ? ldf1(kw + by * G::KWE + fx + 1) : Ep[gy];
+        fs = ldf1(ks + by * G::KSE + fx);
+        fn = gy + 1 < n ? ldf1(ks + (by + 1) * G::KSE + fx) : Np[gx];
     }
 };
 
@@ -158,15 +170,17 @@ __device__ inline void warp_pipeline(const WArgs& a, uint64_t* bar, int lane, Is
     }
 }
 
-// Pre-smoothing (see wpre_item); CG stages q, x and p as well.
-template <int H, bool CG, int MINB>
+// Pre-smoothing (see wpre_item); CG stages q, x and p as well.  FB: bytes per
+// stored interior face (m_kw, m_ks map FP32 or BF16 faces).
+template <int H, bool CG, int MINB, int FB = 4>
 __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A, const __grid_constant__ CUtensorMap m_kw,
                                                         const __grid_constant__ CUtensorMap m_ks,
                                                         const __grid_constant__ CUtensorMap m_r,
                                                         const __grid_constant__ CUtensorMap m_q,
                                                         const __grid_constant__ CUtensorMap m_x,
                                                         const __grid_constant__ CUtensorMap m_p) {
-    using G = TGeo<H>;
+    using G = TGeo<H, FB>;
+    using F = typename std::conditional<FB == 2, __nv_bfloat16, float>::type;
     constexpr int STAGE = CG ? G::PRE_CG_STAGE : G::PRE_STAGE;
     using L = TLayout<H, STAGE>;
     constexpr uint32_t TX = G::FACE_BYTES + G::REGION_BYTES + (CG ? G::REGION_BYTES + 8u * WT * WT : 0u);
@@ -180,8 +194,8 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A,
         item_decode(A.a, item, p, tile, tx, ty);
         mbar_expect_tx(bar, TX);
         const int x0 = tx * WT - 4, y0 = ty * WT - H;
-        tma_load_3d(wb + G::KW_OFF, &m_kw, x0, y0, p, bar);
-        tma_load_3d(wb + G::KS_OFF, &m_ks, x0, y0, p, bar);
+        tma_load_3d(wb + G::KW_OFF, &m_kw, tx * WT - G::FXO, y0, p, bar);
+        tma_load_3d(wb + G::KS_OFF, &m_ks, tx * WT - G::FXO, y0, p, bar);
         tma_load_3d(wb + G::R_OFF, &m_r, x0, y0, p, bar);
         if (CG) {
             tma_load_3d(wb + G::V_OFF, &m_q, x0, y0, p, bar);
@@ -193,21 +207,23 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A,
         int p, tile, tx, ty;
         item_decode(A.a, item, p, tile, tx, ty);
         const float* st = wb;
-        StagedSrc<H> S{st + G::KW_OFF, st + G::KS_OFF, st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, st + G::P_OFF,
-                       A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT, 0, 0};
+        StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
+                          st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, st + G::P_OFF,
+                          A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT, 0, 0};
         wpre_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill);
     };
     warp_pipeline(A.a, bar, lane, issue, work);
 }
 
-// Prolongation and post-smoothing (see wpost_item).
-template <int H, bool CG, int MINB>
+// Prolongation and post-smoothing (see wpost_item); FB as for k_tpre.
+template <int H, bool CG, int MINB, int FB = 4>
 __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> A, const __grid_constant__ CUtensorMap m_kw,
                                                          const __grid_constant__ CUtensorMap m_ks,
                                                          const __grid_constant__ CUtensorMap m_r,
                                                          const __grid_constant__ CUtensorMap m_e,
                                                          const __grid_constant__ CUtensorMap m_ec) {
-    using G = TGeo<H>;
+    using G = TGeo<H, FB>;
+    using F = typename std::conditional<FB == 2, __nv_bfloat16, float>::type;
     constexpr int STAGE = G::POST_STAGE;
     using L = TLayout<H, STAGE>;
     constexpr uint32_t TX = G::FACE_BYTES + 2u * G::REGION_BYTES + 4u * G::CY * G::CX;
@@ -221,8 +237,8 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
         item_decode(A.a, item, p, tile, tx, ty);
         mbar_expect_tx(bar, TX);
         const int x0 = tx * WT - 4, y0 = ty * WT - H;
-        tma_load_3d(wb + G::KW_OFF, &m_kw, x0, y0, p, bar);
-        tma_load_3d(wb + G::KS_OFF, &m_ks, x0, y0, p, bar);
+        tma_load_3d(wb + G::KW_OFF, &m_kw, tx * WT - G::FXO, y0, p, bar);
+        tma_load_3d(wb + G::KS_OFF, &m_ks, tx * WT - G::FXO, y0, p, bar);
         tma_load_3d(wb + G::R_OFF, &m_r, x0, y0, p, bar);
         tma_load_3d(wb + G::V_OFF, &m_e, x0, y0, p, bar);
         tma_load_3d(wb + G::X_OFF, &m_ec, tx * (WT / 2) - 4, ty * (WT / 2) - H / 2, p, bar);
@@ -231,17 +247,18 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
         int p, tile, tx, ty;
         item_decode(A.a, item, p, tile, tx, ty);
         const float* st = wb;
-        StagedSrc<H> S{st + G::KW_OFF, st + G::KS_OFF, st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, nullptr,
-                       A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT,
-                       tx * (WT / 2) - 4, ty * (WT / 2) - H / 2};
+        StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
+                          st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, nullptr,
+                          A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT,
+                          tx * (WT / 2) - 4, ty * (WT / 2) - H / 2};
         wpost_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill);
     };
     warp_pipeline(A.a, bar, lane, issue, work);
 }
 
-template <int H, bool CG> constexpr size_t tpre_smem() {
-    return TLayout<H, CG ? TGeo<H>::PRE_CG_STAGE : TGeo<H>::PRE_STAGE>::block_bytes();
+template <int H, bool CG, int FB = 4> constexpr size_t tpre_smem() {
+    return TLayout<H, CG ? TGeo<H, FB>::PRE_CG_STAGE : TGeo<H, FB>::PRE_STAGE>::block_bytes();
 }
-template <int H> constexpr size_t tpost_smem() { return TLayout<H, TGeo<H>::POST_STAGE>::block_bytes(); }
+template <int H, int FB = 4> constexpr size_t tpost_smem() { return TLayout<H, TGeo<H, FB>::POST_STAGE>::block_bytes(); }
 
 }  // namespace smcgm

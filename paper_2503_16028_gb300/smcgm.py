@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libsmcgm.so")
 SMC_STATIC_RESAMPLE_MAX = 32768
 SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ENOCONV, SMC_EDEGENERATE, SMC_ESTATE = range(7)
 SMC_K_PCN, SMC_K_PCN_GM, SMC_K_GM_INDEP, SMC_K_PCNL, SMC_K_GMPCNL = range(5)
-SMC_P_FP64, SMC_P_FP32_REFINE = range(2)
+SMC_P_FP64, SMC_P_FP32_REFINE, SMC_P_BF16SMOOTH_REFINE = range(3)
 STATUS_NAMES = ["SMC_OK", "SMC_EINVAL", "SMC_ENOMEM", "SMC_ECUDA", "SMC_ENOCONV", "SMC_EDEGENERATE", "SMC_ESTATE"]
 
 _dp = ctypes.POINTER(ctypes.c_double)

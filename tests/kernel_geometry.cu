@@ -4,10 +4,11 @@
 // * quad_pos<H> places every quad of the smoothing region (tile plus halo H)
 //   exactly once, the tile's quads first, the four corner quads left out for
 //   one sweep (H = 2);
-// * the TMA boxes of the staged kernels start on 16-byte boundaries, have
-//   16-byte multiples as inner extents, cover the region (faces, right-hand
-//   side, correction, parent correction) and sit 128-byte aligned in the
-//   staging buffer;
+// * the TMA boxes of the staged kernels (FP32 faces, and the BF16 faces of the
+//   BF16 smoother) start on 16-byte boundaries for every tile, have 16-byte
+//   multiples as inner extents, cover every face a region quad reads (faces,
+//   right-hand side, correction, parent correction) and sit 128-byte aligned
+//   in the staging buffer;
 // * the dynamic shared memory of the staged kernels, of the cosine transform
 //   and the static shared memory of the operator pass fit the blocks per SM
 //   their launches ask for, and the largest accepted 2D grid fits a block.
@@ -62,38 +63,62 @@ void check_quads() {
     CHECK(G::QR <= G::QS);
 }
 
-template <int H, bool CG, int MINB>
+template <int H, bool CG, int MINB, int FB>
 void check_staged() {
-    using G = TGeo<H>;
-    CHECK(H <= 4);                                  // boxes start 4 columns left of the tile
-    // region columns 16 tx - H .. 16 tx + 15 + H, plus the east face of the last one
-    CHECK(G::KWX >= 4 + WT + H + 1);
-    CHECK(G::BX >= 4 + WT + H);
+    using G = TGeo<H, FB>;
+    CHECK(H <= 4);                                  // r, q, e boxes start 4 columns left of the tile
     CHECK(G::RW == WT + 2 * H);
+    // r, q, e: region columns 16 tx - H .. 16 tx + 15 + H from the box origin 16 tx - 4
+    CHECK(G::BX >= 4 + WT + H);
+    // interior faces (FP32 or BF16 values) from the box origin 16 tx - FXO: west faces to
+    // column 16 tx + 16 + H (the east face of the last column), south faces to 16 tx + 15 + H
+    CHECK(G::FXO >= H);
+    CHECK(G::KWE >= G::FXO + WT + H + 1);
+    CHECK(G::KSE >= G::FXO + WT + H);
     // parent rows and columns (8 tx - H/2 .. 8 tx + 7 + H/2) inside the parent box from 8 tx - 4
     CHECK(G::CY == (WT + 2 * H) / 2);
     CHECK(4 >= H / 2 && G::CX >= 4 + WT / 2 + H / 2);
-    // inner extents and starts on 16-byte boundaries (4 floats)
-    CHECK(G::KWX % 4 == 0 && G::BX % 4 == 0 && G::CX % 4 == 0 && WT % 4 == 0);
+    // inner extents in whole 16-byte units; every box starts on a 16-byte boundary, for
+    // any tile (negative starts included): x * bytes per value a multiple of 16
+    CHECK((G::KWE * FB) % 16 == 0 && (G::KSE * FB) % 16 == 0);
+    CHECK((G::BX * 4) % 16 == 0 && (G::CX * 4) % 16 == 0 && (WT * 4) % 16 == 0);
     for (int t = 0; t < 128; ++t) {
-        CHECK((WT * t - 4) % 4 == 0);
-        CHECK(((WT / 2) * t - 4) % 4 == 0);
+        CHECK(((WT * t - G::FXO) * FB) % 16 == 0);
+        CHECK(((WT * t - 4) * 4) % 16 == 0);
+        CHECK((((WT / 2) * t - 4) * 4) % 16 == 0);
+        CHECK(((WT * t) * 4) % 16 == 0);
     }
-    // buffers 128-byte aligned inside the staging area
+    // box extents within the tensor-map limit (256 values per dimension)
+    CHECK(G::KWE <= 256 && G::KSE <= 256 && G::BX <= 256 && G::RW + 1 <= 256);
+    // buffers 128-byte aligned inside the staging area, each after the previous one's bytes
     CHECK(G::KW_OFF % 32 == 0 && G::KS_OFF % 32 == 0 && G::R_OFF % 32 == 0);
     CHECK(G::V_OFF % 32 == 0 && G::X_OFF % 32 == 0 && G::P_OFF % 32 == 0);
-    CHECK(G::KS_OFF >= G::KW_OFF + G::RW * G::KWX);
-    CHECK(G::R_OFF >= G::KS_OFF + (G::RW + 1) * G::BX);
+    CHECK(4 * G::KS_OFF >= 4 * G::KW_OFF + FB * G::RW * G::KWE);
+    CHECK(4 * G::R_OFF >= 4 * G::KS_OFF + FB * (G::RW + 1) * G::KSE);
     CHECK(G::V_OFF >= G::R_OFF + G::RW * G::BX);
     CHECK(G::X_OFF >= G::V_OFF + G::RW * G::BX);
     CHECK(G::P_OFF >= G::X_OFF + WT * WT);
     CHECK(G::POST_STAGE >= G::X_OFF + G::CY * G::CX);
     // the transaction counts equal the bytes the boxes bring
-    CHECK(G::FACE_BYTES == 4u * (G::RW * G::KWX + (G::RW + 1) * G::BX));
+    CHECK(G::FACE_BYTES == (uint32_t)FB * (G::RW * G::KWE + (G::RW + 1) * G::KSE));
     CHECK(G::REGION_BYTES == 4u * (G::RW * G::BX));
+    // every face a quad of the region reads (StagedSrc::faces: west faces of its two columns
+    // and the east one, south faces of its two rows and the north one; StagedSrc::cell for a
+    // corner cell) lies inside its box; pairs start on an even value (4-byte loads for BF16)
+    const int tx = 3, ty = 2, x0 = WT * tx - 4, y0 = WT * ty - H;
+    for (int qy = 0; qy < G::RW / 2; ++qy)
+        for (int qx = 0; qx < G::RW / 2; ++qx) {
+            const int gx = WT * tx - H + 2 * qx, gy = WT * ty - H + 2 * qy;
+            const int bx = gx - x0 + (G::FXO - 4), by = gy - y0;
+            CHECK(bx >= 0 && bx % 2 == 0 && by >= 0);
+            CHECK((by + 1) * G::KWE + bx + 2 < G::RW * G::KWE);          // kw pairs and the east faces
+            CHECK((by + 2) * G::KSE + bx + 1 < (G::RW + 1) * G::KSE);    // ks pairs and the north row
+            CHECK(bx + 2 < G::KWE && bx + 1 < G::KSE);
+        }
+    CHECK(G::KWE % 2 == 0 && G::KSE % 2 == 0);
     // shared memory of MINB resident blocks
-    constexpr size_t pre = tpre_smem<H, CG>();
-    constexpr size_t post = tpost_smem<H>();
+    constexpr size_t pre = tpre_smem<H, CG, FB>();
+    constexpr size_t post = tpost_smem<H, FB>();
     CHECK(pre <= BLOCK_MAX && post <= BLOCK_MAX);
     CHECK(MINB * (pre + BLOCK_RESERVED) <= SM_SHARED);
     CHECK(MINB * (post + BLOCK_RESERVED) <= SM_SHARED);
@@ -102,10 +127,16 @@ void check_staged() {
 int main() {
     check_quads<2>();
     check_quads<4>();
-    check_staged<2, true, 4>();
-    check_staged<2, false, 4>();
-    check_staged<4, true, 2>();
-    check_staged<4, false, 2>();
+    check_staged<2, true, 4, 4>();
+    check_staged<2, false, 4, 4>();
+    check_staged<4, true, 2, 4>();
+    check_staged<4, false, 2, 4>();
+    // BF16 smoother faces: boxes from 16 tx - 8, 32 values (64 bytes) per row
+    check_staged<2, true, 4, 2>();
+    check_staged<2, false, 4, 2>();
+    check_staged<4, true, 2, 2>();
+    check_staged<4, false, 2, 2>();
+    CHECK((TGeo<2, 2>::FXO == 8 && TGeo<2, 2>::KWE == 32 && TGeo<2, 2>::KSE == 32));
     // the cosine-transform block fits up to the largest accepted 2D grid and not beyond it;
     // three blocks share an SM at 256^2
     CHECK(fct_smem_bytes(MAX_N2D) <= BLOCK_MAX);

@@ -78,7 +78,7 @@ def test_full_size_metric_workload_sampled():
     s.close()
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_ragged_batches_are_bit_identical(precision):
     wl = inputs.load_workload("darcy64_bimodal")
     N = 13

@@ -32,7 +32,7 @@ def _sampler(wl, N, precision, **kw):
     return smcgm.Sampler(smcgm.make_config(wl, n_particles=N, n_components=1, precision=precision, gradient=1, **kw))
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_gradient_matches_oracle_adjoint_64(precision):
     wl = inputs.load_workload("darcy64_bimodal")
     N = 6
@@ -139,7 +139,7 @@ def test_gradient_full_size_sampled():
     s.close()
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_gradient_32_directions_128(precision):
     """The differentiation workload's check: 128^2 grid, 64^2 modes, N = 2048,
     central differences with eps = 1e-6 along 32 random unit KL directions agree

@@ -39,7 +39,7 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_init_draws_and_potentials_64(precision):
     wl, cfg, s = _sampler("darcy64_bimodal", n_particles=37, n_components=3, precision=precision)
     X, Phi = s.particles()
@@ -53,7 +53,7 @@ def test_init_draws_and_potentials_64(precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_forward_solution_matches_exact_solve(precision):
     wl, cfg, s = _sampler("darcy64_bimodal", n_particles=8, precision=precision)
     X, Phi = s.particles()
@@ -71,8 +71,9 @@ def test_forward_solution_matches_exact_solve(precision):
     s.close()
 
 
-def test_forward_256_sampled_particles():
-    wl, cfg, s = _sampler("darcy256_precision", n_particles=6, n_components=2)
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
+def test_forward_256_sampled_particles(precision):
+    wl, cfg, s = _sampler("darcy256_precision", n_particles=6, n_components=2, precision=precision)
     X, Phi = s.particles()
     prob = oproblem.from_workload(wl)
     for p in (0, 5):
@@ -91,7 +92,7 @@ def _random_mixture(s, rng, lam0):
     return opcngm.Mixture(modes, w, m, lam, lam0)
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_move_step_matches_oracle(precision):
     N = 24
     wl, cfg, s = _sampler("darcy64_bimodal", n_particles=N, n_components=4, precision=precision)
@@ -243,3 +244,29 @@ def test_out_of_order_calls_are_rejected():
         s.smc_move(1)                      # pCN-GM needs a fitted mixture
     assert e.value.status == smcgm.SMC_ESTATE
     s.close()
+
+
+def test_bf16_smoother_matches_fp32_smoother():
+    """The BF16 smoother changes only the preconditioner: at 256^2 the FP64-accurate
+    solutions of both mixed-precision modes agree to the solver tolerance, and the CG
+    iteration counts stay close (the V-cycle's operator differs by BF16 rounding, ~2^-9)."""
+    wl = inputs.load_workload("darcy256_precision")
+    N = 64
+    out = {}
+    for prec in (smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE):
+        s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, n_components=2, precision=prec))
+        X, _ = s.particles()
+        Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
+        P = torch.empty(N, dtype=torch.float64, device="cuda")
+        W = torch.empty((N, 256, 256), dtype=torch.float64, device="cuda")
+        s.smc_profile_query(reset=True)
+        s.smc_forward(Xd, P, W)
+        prof = s.smc_profile_query(reset=True)
+        out[prec] = (W.cpu().numpy(), P.cpu().numpy(), prof["cg_iterations"] / prof["solves"])
+        s.close()
+    W32, P32, it32 = out[smcgm.SMC_P_FP32_REFINE]
+    W16, P16, it16 = out[smcgm.SMC_P_BF16SMOOTH_REFINE]
+    for p in range(N):
+        assert _rel(W16[p], W32[p]) < 2e-10
+    assert np.max(np.abs(P16 - P32) / np.abs(P32)) < 2e-10
+    assert it16 <= 1.15 * it32 + 1, (it16, it32)

@@ -1,10 +1,11 @@
 """Whole SMC-pCN-GM runs on the 2D Darcy workload (64^2, mirror-pair data) on the GPU.
 
 * Parity: the run of Alg. 1 with Alg. 2 as mutation, from the prior to t = 1, in FP64
-  and in mixed precision, against the oracle's own run (96 particles, K = 4, L = 10,
-  50 EM iterations): every layer's temperature increment and acceptance rate, the log
+  and in both mixed-precision modes (FP32 + refinement, with FP32 or BF16 smoother
+  faces), against the oracle's own run (96 particles, K = 4, L = 10, 50 EM
+  iterations): every layer's temperature increment and acceptance rate, the log
   evidence, and the final particles and potentials.  The oracle's run is computed once
-  for both precisions.
+  for all precisions.
 * The mirror invariant of this workload: the observation points come in pairs
   (x, y) / (1 - x, y) with pair-averaged data, and the prior, the source and the grid
   are symmetric under x -> 1 - x, so Phi(Ru) = Phi(u) for the reflection R, which flips
@@ -47,7 +48,7 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_darcy64_full_run_matches_oracle(oracle_run, precision):
     wl = inputs.load_workload("darcy64_bimodal")
     cfg = smcgm.make_config(wl, n_particles=N_PARITY, em_iters=50, precision=precision)

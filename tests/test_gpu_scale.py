@@ -13,7 +13,8 @@ the remainder fix-up and the chunk scan all run there and are compared here.
   iterations): temperature, indices, gathered particles and the fitted mixture.
 * A 512^2 grid (the largest the library accepts: the cosine-transform block at its
   shared-memory limit, one more multigrid level): initial potentials and one pCN-GM
-  move of 2 particles, in both precisions.
+  move of 2 particles, in every precision of the solver (FP64, FP32 + refinement, and
+  FP32 + refinement with the BF16 smoother).
 
 Resampling indices must be identical.  Weights come from floating-point exponentials,
 so each test first asks the oracle for the systematic points within 64 CDF units of a
@@ -107,7 +108,7 @@ def test_metric_workload_first_layer_matches_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE])
+@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_grid_512_init_and_move(precision):
     wl = dict(inputs.load_workload("darcy256_precision"))
     wl["n"] = 512
