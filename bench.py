@@ -23,7 +23,7 @@ run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
 the GPU and on the CPU oracle, the SM clocks sampled during the timed region and
 the CPU oracle baseline.
 --smoother bf16 times the BF16-smoother mode as the headline; --no-fp64, --no-alt-smoother,
---no-e2e, --no-forward, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
+--no-e2e, --no-forward, --no-em, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
 """
 import argparse
 import json
@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-alt-smoother", action="store_true", help="skip the timing of the other smoother storage")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (host buffers)")
     ap.add_argument("--no-forward", action="store_true", help="skip the solver-only leg")
+    ap.add_argument("--no-em", action="store_true", help="skip the EM-fit timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -369,6 +370,29 @@ def time_small(args, smcgm, torch, barrier):
                 unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
+def time_em(wl, N, smcgm, torch, calls=2):
+    """gm_fit (the EM fit on the r leading modes, em_iters iterations) on the workload's
+    resampled particles, diagonal and full covariances, each timed with CUDA events on the
+    library's stream after one untimed call."""
+    out = {}
+    for form, full in (("diagonal", 0), ("full_covariance", 1)):
+        s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, full_cov=full))
+        s.smc_temper_step()
+        s.smc_resample()
+        s.gm_fit()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record(s.stream)
+        for _ in range(calls):
+            s.gm_fit()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        out[form] = dict(ms_per_fit=e0.elapsed_time(e1) / calls, em_iters=int(s.cfg.em_iters), components=int(s.cfg.n_components),
+                         modes=int(s.r), particles=N)
+        s.close()
+    return out
+
+
 def time_e2e(s, N, d, steps, torch, barrier, world):
     """End to end through the C ABI (smc_move_host): every step copies the particles and potentials
     from pinned host buffers to the device, moves them and copies them back, inside the timed region
@@ -543,6 +567,7 @@ def run_native(args, rank, world, local):
                     dominant_kernel_gbs=prof64["dom_bytes"] / (prof64["dom_ms"] / 1000.0) / 1e9 if prof64["dom_ms"] else None)
         agree = precision_agreement(s64, 1 + st64, wl, N, smcgm)
         s64.close()
+    em = None if args.no_em else time_em(wl, N, smcgm, torch)
     grad = None
     if not args.no_gradient:
         grad = time_gradient(wl, N, smcgm, torch)
@@ -570,7 +595,7 @@ def run_native(args, rank, world, local):
                 fp64_agreement=agree,
                 solver_only=forward, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
                 cpu_baseline=cpu,
-                adjoint_gradient=grad, smc_run=layers, small_workload=small)
+                adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small)
     print(json.dumps(line), flush=True)
 
 

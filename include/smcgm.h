@@ -213,9 +213,11 @@ smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Ph
  * keeps C_j = L_j L_j^T, L_j^{-1} and log det L_j; the pCN-GM proposal draws
  * beta L_j z on the mixture modes and the acceptance ratio uses
  * N(e; (1-gamma) m_j, beta^2 C_j) / N(e; 0, beta^2 diag(lambda)).  gm_fit
- * then fits full covariances (EM, ridge var_floor * diag(lambda)).
+ * then fits full covariances (EM, ridge var_floor * diag(lambda)).  The
+ * factors are formed on the device (FP64 Cholesky, one block per component).
  * SMC_ESTATE without cfg.full_cov; SMC_EINVAL for a C_j that is not positive
- * definite. */
+ * definite, after which the context holds no usable mixture (smc_move returns
+ * SMC_ESTATE until smc_set_mixture, smc_set_mixture_cov or gm_fit succeeds). */
 smc_status smc_set_mixture_cov(smc_ctx* ctx, const double* w, const double* m, const double* cov);
 smc_status smc_get_mixture_cov(smc_ctx* ctx, double* cov);
 

@@ -135,6 +135,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     if (cfg.full_cov) {
         C.gcov = P.take<double>((size_t)K * r * r); C.gL = P.take<double>((size_t)K * r * r);
         C.gLi = P.take<double>((size_t)K * r * r); C.glogdet = P.take<double>(K);
+        C.covpart = P.take<double>(cov_partial_doubles(K, r));
     }
     C.tab = P.take<double>(4 * (size_t)K * r + r + 2 * K);
     C.xsT = P.take<double>((size_t)r * N); C.resp = P.take<double>((size_t)K * N); C.nj = P.take<double>(K);

@@ -189,8 +189,9 @@ __global__ void k_lamS(int r, const double* __restrict__ lam, const int* __restr
 //   E-step: log p_nj = log w_j - r/2 log(2 pi) - log det L_j - |L_j^{-1}(x_n - m_j)|^2 / 2,
 //   M-step: C_j = sum_n g_nj (x_n - m_j)(x_n - m_j)^T / N_j + floor diag(lambda_S),
 //   initial and re-seeded covariances diag(pooled variances).
-// L_j (Cholesky), L_j^{-1} and log det L_j are formed on the host in FP64
-// (factor_mixture) after every M-step: K r x r matrices, a few hundred KB.
+// L_j (Cholesky), L_j^{-1} and log det L_j are formed on the device in FP64
+// (k_factor, one block per component) after every M-step; a pivot that is not
+// positive sets a device flag, read by the host once per fit.
 // ------------------------------------------------------------------------
 
 // E-step, one block per particle: for each j, y = L_j^{-1}(x_n - m_j) (a row per thread).
@@ -233,27 +234,120 @@ __global__ void __launch_bounds__(128) k_estep_full(int N, int K, int r, const d
     }
 }
 
-// M-step covariances, one block per (j, a, b <= a); both triangles written.
-__global__ void k_mstep_cov(int N, int r, const double* __restrict__ xsT, const double* __restrict__ resp,
-                            const double* __restrict__ nj, const double* __restrict__ m, const double* __restrict__ lamS,
-                            double floor_frac, double* __restrict__ cov) {
-    __shared__ double red[32];
-    const int tri = r * (r + 1) / 2;
-    const int j = blockIdx.x / tri;
-    int t = blockIdx.x % tri, a = 0;
-    while (t > a) { t -= a + 1; ++a; }
-    const int b = t;                                   // b <= a
+// M-step covariances as a blocked SYRK: S_j = sum_n g_nj (x_n - m_j)(x_n - m_j)^T.
+// The r x r output is cut into CT x CT tiles; a block computes one lower-triangle
+// tile (ta >= tb) of one component over one of COV_NC chunks of the particles
+// (FP64, 256 threads, 4 outputs each), staging CT particles x CT modes of the
+// weighted deviations g (x_a - m_a) and of the deviations (x_b - m_b) in shared
+// memory per step.  The chunk partials go to `part`; k_cov_reduce adds them in a
+// fixed order (deterministic), divides by N_j, adds the ridge and writes both
+// triangles.
+constexpr int CT = 32;
+constexpr int COV_NC = 8;
+__host__ __device__ inline int cov_tiles(int r) { const int t = (r + CT - 1) / CT; return t * (t + 1) / 2; }
+
+__global__ void __launch_bounds__(256) k_mstep_cov(int N, int r, const double* __restrict__ xsT, const double* __restrict__ resp,
+                                                   const double* __restrict__ m, double* __restrict__ part) {
+    __shared__ double Wa[CT][CT + 1];   // [particle][mode a]
+    __shared__ double Db[CT][CT + 1];   // [particle][mode b]
+    const int tile = blockIdx.x, j = blockIdx.y, chunk = blockIdx.z;
+    int ta = 0, t = tile;
+    while (t > ta) { t -= ta + 1; ++ta; }
+    const int tb = t;                                   // tb <= ta
+    const int a0 = ta * CT, b0 = tb * CT;
+    const int per = (N + COV_NC - 1) / COV_NC;
+    const int n_lo = chunk * per, n_hi = min(N, n_lo + per);
     const double* g = resp + (size_t)j * N;
-    const double* xa = xsT + (size_t)a * N;
-    const double* xb = xsT + (size_t)b * N;
-    const double ma = m[(size_t)j * r + a], mb = m[(size_t)j * r + b];
-    double acc = 0.0;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) acc += g[n] * (xa[n] - ma) * (xb[n] - mb);
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) {
-        const double v = acc / nj[j] + (a == b ? floor_frac * lamS[a] : 0.0);
+    const int row = threadIdx.x / 8, col0 = (threadIdx.x % 8) * 4;   // outputs (a0 + row, b0 + col0 .. col0 + 3)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n0 = n_lo; n0 < n_hi; n0 += CT) {
+        for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+            const int mode = e / CT, pn = e % CT;          // consecutive threads: consecutive particles
+            const int n = n0 + pn;
+            const bool in_n = n < n_hi;
+            const int a = a0 + mode, b = b0 + mode;
+            Wa[pn][mode] = (in_n && a < r) ? g[n] * (xsT[(size_t)a * N + n] - m[(size_t)j * r + a]) : 0.0;
+            Db[pn][mode] = (in_n && b < r) ? xsT[(size_t)b * N + n] - m[(size_t)j * r + b] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int pn = 0; pn < CT; ++pn) {
+            const double w = Wa[pn][row];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += w * Db[pn][col0 + q];
+        }
+        __syncthreads();
+    }
+    double* out = part + (((size_t)j * cov_tiles(r) + tile) * COV_NC + chunk) * CT * CT;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[row * CT + col0 + q] = acc[q];
+}
+
+__global__ void k_cov_reduce(int r, const double* __restrict__ part, const double* __restrict__ nj, const double* __restrict__ lamS,
+                             double floor_frac, double* __restrict__ cov) {
+    const int tile = blockIdx.x, j = blockIdx.y;
+    int ta = 0, t = tile;
+    while (t > ta) { t -= ta + 1; ++ta; }
+    const int tb = t;
+    const double* p = part + ((size_t)j * cov_tiles(r) + tile) * COV_NC * CT * CT;
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
+        const int a = ta * CT + e / CT, b = tb * CT + e % CT;
+        if (a >= r || b >= r || b > a) continue;
+        double s = 0.0;
+        for (int k = 0; k < COV_NC; ++k) s += p[(size_t)k * CT * CT + e];
+        const double v = s / nj[j] + (a == b ? floor_frac * lamS[a] : 0.0);
         cov[((size_t)j * r + a) * r + b] = v;
         cov[((size_t)j * r + b) * r + a] = v;
+    }
+}
+
+size_t cov_partial_doubles(int K, int r) { return (size_t)K * cov_tiles(r) * COV_NC * CT * CT; }
+
+// Cholesky factor L_j (lower), L_j^{-1} and log det L_j of every C_j, one block per
+// component, FP64, in the order of the Cholesky-Banachiewicz recurrence
+//   L_kk = sqrt(C_kk - sum_{q<k} L_kq^2),  L_ik = (C_ik - sum_{q<k} L_iq L_kq) / L_kk,
+// a column at a time (its entries below the diagonal are independent given the earlier
+// columns: a row per thread); then L^{-1} by forward substitution on the unit vectors (a
+// column per thread) and log det L_j = sum_k log L_kk.  A pivot that is not positive (C_j
+// not positive definite) sets *bad and is replaced by 1 so the rest stays finite.
+__global__ void __launch_bounds__(256) k_factor(int r, const double* __restrict__ cov, double* __restrict__ L, double* __restrict__ Li,
+                                                double* __restrict__ logdet, int* __restrict__ bad) {
+    __shared__ double s_piv;
+    const int j = blockIdx.x;
+    const size_t rr = (size_t)r * r;
+    const double* A = cov + j * rr;
+    double* Lj = L + j * rr;
+    double* Ij = Li + j * rr;
+    for (size_t e = threadIdx.x; e < rr; e += blockDim.x)
+        if ((int)(e % r) > (int)(e / r)) { Lj[e] = 0.0; Ij[e] = 0.0; }
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            double sum = A[(size_t)k * r + k];
+            for (int q = 0; q < k; ++q) sum -= Lj[(size_t)k * r + q] * Lj[(size_t)k * r + q];
+            if (!(sum > 0.0)) { atomicExch(bad, 1); sum = 1.0; }
+            s_piv = sqrt(sum);
+            Lj[(size_t)k * r + k] = s_piv;
+        }
+        __syncthreads();
+        const double piv = s_piv;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) {
+            double sum = A[(size_t)i * r + k];
+            for (int q = 0; q < k; ++q) sum -= Lj[(size_t)i * r + q] * Lj[(size_t)k * r + q];
+            Lj[(size_t)i * r + k] = sum / piv;
+        }
+        __syncthreads();
+    }
+    for (int col = threadIdx.x; col < r; col += blockDim.x) {
+        for (int i = col; i < r; ++i) {
+            double sum = i == col ? 1.0 : 0.0;
+            for (int q = col; q < i; ++q) sum -= Lj[(size_t)i * r + q] * Ij[(size_t)q * r + col];
+            Ij[(size_t)i * r + col] = sum / Lj[(size_t)i * r + i];
+        }
+    }
+    if (threadIdx.x == 0) {
+        double sdet = 0.0;
+        for (int k = 0; k < r; ++k) sdet += log(Lj[(size_t)k * r + k]);
+        logdet[j] = sdet;
     }
 }
 
@@ -272,46 +366,32 @@ __global__ void k_diag_of_cov(int K, int r, const double* __restrict__ cov, doub
     if (t < K * r) lam[t] = cov[((size_t)(t / r) * r + t % r) * r + t % r];
 }
 
+// Factors every C_j on the device (k_factor) into L_j, L_j^{-1} and log det L_j; with
+// cov_host the covariances are uploaded first.  check_now: wait and fail (InputError) if a
+// C_j is not positive definite; otherwise the flag is read by the caller later.
+static int* factor_flag(Ctx& c) { return c.icount + 40; }
+
+static void launch_factor(Ctx& c) {
+    k_factor<<<c.K, 256, 0, c.stream>>>(c.r, c.gcov, c.gL, c.gLi, c.glogdet, factor_flag(c)); ++c.pc.launches;
+    check(cudaGetLastError(), "factor launch");
+}
+
+static void check_factor_flag(Ctx& c) {
+    int bad = 0;
+    check(cudaMemcpyAsync(&bad, factor_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c.stream), "factor flag");
+    check(cudaStreamSynchronize(c.stream), "sync");
+    if (bad) {
+        c.fitted = false;   // the stored mixture is no longer usable
+        throw InputError{"a mixture covariance is not positive definite"};
+    }
+}
+
 void factor_mixture(Ctx& c, const double* cov_host) {
-    const int K = c.K, r = c.r;
-    const size_t rr = (size_t)r * r;
-    std::vector<double> cov(K * rr), L(K * rr, 0.0), Li(K * rr, 0.0), logdet(K, 0.0);
-    if (cov_host) {
-        std::copy(cov_host, cov_host + K * rr, cov.begin());
-    } else {
-        check(cudaMemcpyAsync(cov.data(), c.gcov, K * rr * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "cov d2h");
-        check(cudaStreamSynchronize(c.stream), "sync");
-    }
-    for (int j = 0; j < K; ++j) {
-        const double* A = cov.data() + j * rr;
-        double* Lj = L.data() + j * rr;
-        double* Ij = Li.data() + j * rr;
-        for (int i = 0; i < r; ++i) {                  // Cholesky-Banachiewicz, A = L L^T
-            for (int k = 0; k <= i; ++k) {
-                double sum = A[(size_t)i * r + k];
-                for (int q = 0; q < k; ++q) sum -= Lj[(size_t)i * r + q] * Lj[(size_t)k * r + q];
-                if (i == k) {
-                    if (!(sum > 0.0)) throw InputError{"a mixture covariance is not positive definite"};
-                    Lj[(size_t)i * r + i] = std::sqrt(sum);
-                } else {
-                    Lj[(size_t)i * r + k] = sum / Lj[(size_t)k * r + k];
-                }
-            }
-            logdet[j] += std::log(Lj[(size_t)i * r + i]);
-        }
-        for (int col = 0; col < r; ++col) {            // L^{-1} by forward substitution on the unit vectors
-            for (int i = col; i < r; ++i) {
-                double sum = i == col ? 1.0 : 0.0;
-                for (int q = col; q < i; ++q) sum -= Lj[(size_t)i * r + q] * Ij[(size_t)q * r + col];
-                Ij[(size_t)i * r + col] = sum / Lj[(size_t)i * r + i];
-            }
-        }
-    }
-    if (cov_host) check(cudaMemcpyAsync(c.gcov, cov.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "cov");
-    check(cudaMemcpyAsync(c.gL, L.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "L");
-    check(cudaMemcpyAsync(c.gLi, Li.data(), K * rr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "Li");
-    check(cudaMemcpyAsync(c.glogdet, logdet.data(), K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "logdet");
-    check(cudaStreamSynchronize(c.stream), "sync");    // the host vectors go out of scope
+    const size_t n = (size_t)c.K * c.r * c.r;
+    check(cudaMemsetAsync(factor_flag(c), 0, sizeof(int), c.stream), "memset");
+    if (cov_host) check(cudaMemcpyAsync(c.gcov, cov_host, n * sizeof(double), cudaMemcpyHostToDevice, c.stream), "cov");
+    launch_factor(c);
+    check_factor_flag(c);
 }
 
 double gm_fit_device(Ctx& c) {
@@ -342,22 +422,25 @@ double gm_fit_device(Ctx& c) {
     const int eg = (N + 255) / 256;
     if (c.cfg.full_cov) {
         const int kr2 = K * r * r;
+        const dim3 cg(cov_tiles(r), K, COV_NC);
+        check(cudaMemsetAsync(factor_flag(c), 0, sizeof(int), c.stream), "memset");
         k_cov_diag<<<(kr2 + 255) / 256, 256, 0, c.stream>>>(K, r, nullptr, c.glam, c.gcov); ++c.pc.launches;
         for (int it = 0; it < c.cfg.em_iters; ++it) {
-            factor_mixture(c, nullptr);
+            launch_factor(c);
             k_estep_full<<<N, 128, 0, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.gLi, c.glogdet, c.resp, c.lse, c.gmax); ++c.pc.launches;
             k_mstep_mean<<<K * r, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu); ++c.pc.launches;
-            k_mstep_cov<<<K * r * (r + 1) / 2, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.nj, c.gmu, lamS, fl, c.gcov); ++c.pc.launches;
+            k_mstep_cov<<<cg, 256, 0, c.stream>>>(N, r, c.xsT, c.resp, c.gmu, c.covpart); ++c.pc.launches;
+            k_cov_reduce<<<dim3(cov_tiles(r), K), 256, 0, c.stream>>>(r, c.covpart, c.nj, lamS, fl, c.gcov); ++c.pc.launches;
             k_diag_of_cov<<<(K * r + 255) / 256, 256, 0, c.stream>>>(K, r, c.gcov, c.glam); ++c.pc.launches;
             k_mstep_fix<<<1, 1024, 0, c.stream>>>(N, K, r, c.nj, c.gmax, c.xsT, c.pooled, c.gw, c.gmu, c.glam); ++c.pc.launches;
             k_cov_diag<<<(kr2 + 255) / 256, 256, 0, c.stream>>>(K, r, c.nj, c.glam, c.gcov); ++c.pc.launches;   // re-seeded ones
         }
-        factor_mixture(c, nullptr);
+        launch_factor(c);
         k_estep_full<<<N, 128, 0, c.stream>>>(N, K, r, c.xsT, c.gw, c.gmu, c.gLi, c.glogdet, c.resp, c.lse, c.gmax); ++c.pc.launches;
         k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8); ++c.pc.launches;
         double ll = 0.0;
         check(cudaMemcpyAsync(&ll, c.dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "ll");
-        check(cudaStreamSynchronize(c.stream), "sync");
+        check_factor_flag(c);                            // one wait for the whole fit
         return ll;
     }
     for (int it = 0; it < c.cfg.em_iters; ++it) {

@@ -174,7 +174,8 @@ void launch_accept_pcnl(Ctx& c, int* acc_count);
 void launch_temper(Ctx& c, double* out5);
 void launch_resample(Ctx& c);
 double gm_fit_device(Ctx& c);
-void factor_mixture(Ctx& c, const double* cov_host);   // Cholesky, inverse and log det of every C_j (host), uploaded
+void factor_mixture(Ctx& c, const double* cov_host);   // Cholesky, inverse and log det of every C_j (device); waits
+size_t cov_partial_doubles(int K, int r);               // scratch of the full-covariance contraction
 void launch_propose_full(Ctx& c);
 void launch_moments(Ctx& c, double* mean, double* var);
 void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
@@ -201,6 +202,7 @@ struct Ctx {
     // full covariances on the mixture modes (cfg.full_cov): C_j, its Cholesky
     // factor L_j (lower), L_j^{-1} and log det L_j; glam holds diag(C_j)
     double *gcov = nullptr, *gL = nullptr, *gLi = nullptr, *glogdet = nullptr;
+    double* covpart = nullptr;  // chunk partials of the covariance contraction (full_cov)
     double *tab = nullptr;     // per (j, s): c0, a, mu, sq; then per s: b; then per j: log w, cumulative w
     // EM scratch
     double *xsT = nullptr, *resp = nullptr, *nj = nullptr, *pooled = nullptr, *lse = nullptr, *gmax = nullptr;

@@ -103,3 +103,49 @@ def test_full_covariance_checkpoint_roundtrip():
     s.smc_load(buf)
     assert np.array_equal(s.smc_get_mixture_cov(), cov)
     s.close()
+
+
+@pytest.mark.parametrize("N,K,r,iters", [(4096, 8, 64, 20), (1000, 3, 40, 10)])
+def test_full_covariance_em_at_scale(N, K, r, iters):
+    """The EM fit with full covariances at the metric workload's sizes (N = 4096, K = 8,
+    r = 64: whole 32 x 32 tiles of the blocked covariance contraction, particle chunks of
+    512) and at a ragged mode count (r = 40: a partial tile), against the oracle."""
+    wl = inputs.load_workload("darcy64_bimodal")
+    cfg = smcgm.make_config(wl, n_particles=N, n_components=K, gm_rank=r, em_iters=iters, full_cov=1, solve_batch=1024)
+    s = smcgm.Sampler(cfg)
+    s.smc_temper_step()
+    s.smc_resample()
+    X2, _ = s.particles()
+    ll = s.gm_fit()
+    prob = oproblem.from_workload(wl)
+    mix, hist = ogm.fit_full(X2, prob.gm_modes(r), prob.lam, K, iters, wl["seed"], 0, var_floor=cfg.var_floor)
+    w, m, lam, modes = s.smc_get_mixture()
+    cov = s.smc_get_mixture_cov()
+    assert np.allclose(w, mix.w, rtol=1e-7, atol=1e-12)
+    assert _rel(m, mix.m) < 1e-7
+    assert _rel(cov, mix.cov) < 1e-7
+    assert np.array_equal(cov, np.swapaxes(cov, 1, 2))
+    assert abs(ll - hist[-1]) <= 1e-8 * abs(hist[-1])
+    s.close()
+
+
+def test_covariance_that_is_not_positive_definite_is_rejected():
+    """smc_set_mixture_cov with a C_j that is not positive definite: the device factorisation
+    finds a pivot <= 0, the call returns SMC_EINVAL and the context holds no usable mixture
+    (smc_move returns SMC_ESTATE) until a valid one is set."""
+    wl = inputs.load_workload("darcy64_bimodal")
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=8, n_components=2, gm_rank=8, full_cov=1))
+    prob = oproblem.from_workload(wl)
+    mix = _random_full_mixture(s, prob, 2, np.random.default_rng(5))
+    bad = mix.cov.copy()
+    bad[1, 3, 3] = -1.0
+    with pytest.raises(smcgm.SMCError) as ei:
+        s.smc_set_mixture_cov(mix.w, mix.m, bad)
+    assert ei.value.status == smcgm.SMC_EINVAL and "positive definite" in str(ei.value)
+    s.smc_set_schedule(0.1, 0.2, 0, 0)
+    with pytest.raises(smcgm.SMCError) as ei:
+        s.smc_move(1)
+    assert ei.value.status == smcgm.SMC_ESTATE
+    _random_full_mixture(s, prob, 2, np.random.default_rng(6))
+    s.smc_move(1)
+    s.close()
