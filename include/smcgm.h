@@ -268,9 +268,10 @@ typedef struct smc_profile {
     long long dom_particles;   /* particles processed by those launches */
     double dom_ms;             /* summed CUDA-event durations of those launches */
     double dom_bytes;          /* their algorithmic DRAM bytes (inputs read once, outputs written once) */
-    long long launches;        /* kernel launches issued by the library */
+    long long launches;        /* kernel launches issued by the library (outside CUDA graphs) */
     int cells;                 /* grid cells per solve */
     int word_bytes;            /* bytes per word of the inner solver (4: FP32, 8: FP64) */
+    long long graph_launches;  /* launches of batch graphs (smc_batch_move) that moved this context */
 } smc_profile;
 
 /* enable: 1 turns event timing of the dominant kernel on, 0 off, any other
@@ -313,6 +314,36 @@ smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t byt
  * `stream` (a cudaStream_t, NULL = default stream). */
 smc_status smc_resample_indices_static(const double* d_logw, int n_particles, unsigned long long seed, int layer,
                                        int* d_indices, void* stream);
+
+/* Batched moves in one CUDA graph (many independent problems, one launch).
+ *
+ * smc_batch_create captures `steps` moves of every context in ctxs (count >= 1
+ * distinct contexts, on the current device, dim = 2, kernel SMC_K_PCN,
+ * SMC_K_PCN_GM or SMC_K_GM_INDEP; any grid size, particle count and precision)
+ * into one CUDA graph and instantiates it.  The whole move runs on the device:
+ * the steps, the refinement phases and the CG iterations are conditional
+ * 'while' nodes whose conditions kernels set from the device's counts, and the
+ * launches between two compactions of the active particles are 'switch' nodes
+ * over launch sizes (all, 1/2, 1/4, ... of the particles); the contexts' moves are
+ * parallel branches of the graph.  smc_batch_move launches it once: the same
+ * moves, with the same random streams and results, as smc_move(ctx, steps) on
+ * every context in turn (each context's t, beta and Philox step are read at the
+ * launch; afterwards beta follows the acceptance rule, the layer and step
+ * advance, and the counters grow as after smc_move).  accept_rates (host,
+ * count doubles, may be NULL) receives each context's acceptance rate.  The
+ * batch keeps pointers into the contexts' workspaces: destroy it before any of
+ * its contexts, and do not use a context while its batch's move runs.
+ * smc_batch_create: SMC_EINVAL for invalid arguments or an unsupported context,
+ * SMC_ECUDA if the capture or instantiation fails (messages in
+ * smc_last_error(NULL)).  smc_batch_move: SMC_ESTATE if a context has no mixture
+ * fitted, SMC_ECUDA if a kernel's bounded wait timed out, SMC_ENOCONV if more
+ * than 1% of a context's solves missed the tolerance (after all contexts have
+ * moved).  The paper moves one problem at a time; this is its batched form on
+ * one GPU. */
+typedef struct smc_batch smc_batch;
+smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batch** out);
+smc_status smc_batch_move(smc_batch* batch, double* accept_rates);
+void smc_batch_destroy(smc_batch* batch);
 
 /* Library version string (static storage owned by the library; never NULL). */
 const char* smc_version(void);

@@ -130,6 +130,7 @@ static size_t plan(const smc_config& cfg, Ctx* c, char* base) {
     C.lfwd = P.take<double>((size_t)N * K); C.lrev = P.take<double>((size_t)N * K);
     C.acc = P.take<unsigned char>(N); C.idx = P.take<int>(N);
     C.icount = P.take<int>(64); C.dscal = P.take<double>(64); C.dev_err = P.take<int>(4);
+    C.gcnt = P.take<GraphCounters>(1); C.gouter = P.take<int>(2); C.msched = P.take<MoveSched>(1); C.gsteps = P.take<int>(1);
     C.normtab = P.take<float>(2 * NORMAL_TAB);
     C.gw = P.take<double>(K); C.gmu = P.take<double>((size_t)K * r); C.glam = P.take<double>((size_t)K * r);
     if (cfg.full_cov) {
@@ -855,4 +856,196 @@ smc_status smc_load(smc_ctx* ctx, const void* host_buf, size_t bytes) {
     API_END(ctx)
 }
 
+// ---------------------------------------------------------------------------
+// Batched moves in one CUDA graph
+// ---------------------------------------------------------------------------
+struct smc_batch {
+    std::vector<smc_ctx*> ctxs;
+    int steps = 0;
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> streams;   // one capture stream per context
+    cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> done;       // per context: its branch / its stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(smc_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t st : b->streams) if (st) cudaStreamDestroy(st);
+    for (cudaStream_t st : b->aux) if (st) cudaStreamDestroy(st);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->done) if (e) cudaEventDestroy(e);
+    delete b;
+}
+
+smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batch** out) {
+    if (!ctxs || !out || count < 1 || steps < 1) {
+        set_global_error("smc_batch_create: null pointer, count < 1 or steps < 1");
+        return SMC_EINVAL;
+    }
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { set_global_error("smc_batch_create: no CUDA device"); return SMC_ECUDA; }
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) { set_global_error("smc_batch_create: null context"); return SMC_EINVAL; }
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) { set_global_error("smc_batch_create: a context appears twice"); return SMC_EINVAL; }
+        const Ctx& c = ctxs[i]->c;
+        if (c.dim != 2) { set_global_error("smc_batch_create: graph capture is built for the 2D problem"); return SMC_EINVAL; }
+        if (c.cfg.kernel != SMC_K_PCN && c.cfg.kernel != SMC_K_PCN_GM && c.cfg.kernel != SMC_K_GM_INDEP) {
+            set_global_error("smc_batch_create: the pCN, pCN-GM and SMC-GM kernels only");
+            return SMC_EINVAL;
+        }
+        if (!device_visible(c.X)) { set_global_error("smc_batch_create: a context lives on another device"); return SMC_EINVAL; }
+    }
+    smc_batch* b = new smc_batch();
+    b->steps = steps;
+    b->ctxs.assign(ctxs, ctxs + count);
+    std::vector<cudaStream_t> saved(count, nullptr);
+    int captured = -1;
+    try {
+        check(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking), "stream");
+        for (auto& st : b->aux) check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+        b->streams.assign(count, nullptr);
+        b->done.assign(count, nullptr);
+        for (int i = 0; i < count; ++i) {
+            check(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking), "stream");
+            check(cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming), "event");
+            check(cudaStreamSynchronize(ctxs[i]->c.stream), "sync");   // the context's own work is done
+        }
+        check(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+        check(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed), "begin capture");
+        check(cudaEventRecord(b->fork, b->origin), "fork");
+        for (int i = 0; i < count; ++i) {
+            Ctx& c = ctxs[i]->c;
+            captured = i;
+            saved[i] = c.stream;
+            const smc_profile pc = c.pc;
+            const bool prof = c.prof;
+            c.stream = b->streams[i];
+            c.graph = true; c.lenient = true; c.prof = false; c.gdepth = 0;
+            for (int k = 0; k < 4; ++k) c.gaux[k] = b->aux[k];
+            check(cudaStreamWaitEvent(c.stream, b->fork, 0), "fork wait");
+            check(cudaMemsetAsync(c.icount, 0, sizeof(int), c.stream), "memset");
+            check(cudaMemsetAsync(c.gcnt, 0, sizeof(GraphCounters), c.stream), "memset");
+            capture_move_steps(c, steps, c.icount);
+            check(cudaEventRecord(b->done[i], c.stream), "join");
+            check(cudaStreamWaitEvent(b->origin, b->done[i], 0), "join wait");
+            c.stream = saved[i]; c.graph = false; c.lenient = false; c.prof = prof; c.pc = pc;
+            captured = -1;
+        }
+        check(cudaStreamEndCapture(b->origin, &b->graph), "end capture");
+        check(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate");
+    } catch (const CudaError& ce) {
+        if (captured >= 0) {
+            Ctx& c = ctxs[captured]->c;
+            c.stream = saved[captured]; c.graph = false; c.lenient = false;
+        }
+        cudaGraph_t tmp = nullptr;
+        cudaStreamCaptureStatus cs;
+        if (b->origin && cudaStreamIsCapturing(b->origin, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            (void)cudaStreamEndCapture(b->origin, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        (void)cudaGetLastError();
+        set_global_error((std::string("smc_batch_create: ") + ce.what + ": " + cudaGetErrorString(ce.e)).c_str());
+        batch_free(b);
+        return SMC_ECUDA;
+    } catch (const InputError& ie) {
+        if (captured >= 0) {
+            Ctx& c = ctxs[captured]->c;
+            c.stream = saved[captured]; c.graph = false; c.lenient = false;
+        }
+        cudaGraph_t tmp = nullptr;
+        cudaStreamCaptureStatus cs;
+        if (b->origin && cudaStreamIsCapturing(b->origin, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            (void)cudaStreamEndCapture(b->origin, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        (void)cudaGetLastError();
+        set_global_error((std::string("smc_batch_create: ") + ie.what).c_str());
+        batch_free(b);
+        return SMC_EINVAL;
+    }
+    *out = b;
+    return SMC_OK;
+}
+
+smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
+    if (!b) return SMC_EINVAL;
+    const int count = (int)b->ctxs.size();
+    for (int i = 0; i < count; ++i) {
+        const Ctx& c = b->ctxs[i]->c;
+        if (c.stage < 1 || !c.fitted) {
+            set_global_error("smc_batch_move: every context needs an initialised state and a fitted mixture");
+            return SMC_ESTATE;
+        }
+    }
+    std::vector<MoveSched> ms(count);
+    std::vector<int> acc(count, 0);
+    std::vector<GraphCounters> gc(count);
+    std::vector<int> err(2 * count, 0);
+    try {
+        for (int i = 0; i < count; ++i) {
+            Ctx& c = b->ctxs[i]->c;
+            ms[i].t = c.t; ms[i].beta = c.beta; ms[i].gamma = std::sqrt(1.0 - c.beta * c.beta); ms[i].step = c.step; ms[i].pad = 0;
+            check(cudaEventRecord(b->done[i], c.stream), "record");          // earlier work on the context's stream first
+            check(cudaStreamWaitEvent(b->origin, b->done[i], 0), "wait");
+            check(cudaMemcpyAsync(c.msched, &ms[i], sizeof(MoveSched), cudaMemcpyHostToDevice, b->origin), "schedule");
+        }
+        check(cudaGraphLaunch(b->exec, b->origin), "graph launch");
+        for (int i = 0; i < count; ++i) {
+            Ctx& c = b->ctxs[i]->c;
+            check(cudaMemcpyAsync(&acc[i], c.icount, sizeof(int), cudaMemcpyDeviceToHost, b->origin), "d2h");
+            check(cudaMemcpyAsync(&gc[i], c.gcnt, sizeof(GraphCounters), cudaMemcpyDeviceToHost, b->origin), "d2h");
+            check(cudaMemcpyAsync(&err[2 * i], c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->origin), "d2h");
+            check(cudaMemsetAsync(c.dev_err, 0, 2 * sizeof(int), b->origin), "memset");
+        }
+        check(cudaStreamSynchronize(b->origin), "sync");
+    } catch (const CudaError& ce) {
+        set_global_error((std::string("smc_batch_move: ") + ce.what + ": " + cudaGetErrorString(ce.e)).c_str());
+        return SMC_ECUDA;
+    }
+    smc_status st = SMC_OK;
+    for (int i = 0; i < count; ++i) {
+        Ctx& c = b->ctxs[i]->c;
+        if (err[2 * i]) {
+            set_global_error("smc_batch_move: a kernel's bounded mbarrier wait timed out");
+            st = SMC_ECUDA;
+        }
+        const long long solves = (long long)c.N * b->steps;
+        const double rate = (double)acc[i] / (double)solves;
+        if (accept_rates) accept_rates[i] = rate;
+        if (c.cfg.kernel != SMC_K_GM_INDEP) {
+            double be = c.beta;
+            if (rate > 0.3) be = 2.0 * be;
+            else if (rate < 0.15) be = 0.5 * be;
+            c.beta = std::min(be, 1.0);
+        }
+        c.step += (unsigned int)b->steps;
+        ++c.layer;
+        c.stage = 1;
+        c.last_iters = gc[i].itmax;
+        c.nonconv += (long long)gc[i].nonconv;
+        c.pc.solves += solves;
+        c.pc.cg_iterations += (long long)gc[i].cg_iterations;
+        c.pc.inner_solves += (long long)gc[i].inner_solves;
+        c.pc.residuals += (long long)gc[i].residuals;
+        c.pc.graph_launches += 1;
+        c.pc.cells = c.n * c.n;
+        c.pc.word_bytes = mixed_precision(c.cfg) ? 4 : 8;
+        if (st == SMC_OK && (long long)gc[i].nonconv * 100 > solves) {
+            set_global_error("smc_batch_move: more than 1% of a context's forward solves missed the tolerance");
+            st = SMC_ENOCONV;
+        }
+    }
+    return st;
+}
+
+void smc_batch_destroy(smc_batch* b) { batch_free(b); }
+
 }  // extern "C"
+

@@ -77,7 +77,8 @@ void launch_prior_draw(Ctx& c, double* X, int N, uint32_t counter2, uint32_t pur
 //   [.. + r + K, .. + r + 2K) cumulative w (sequential sum in index order)
 __global__ void k_move_tables(int K, int r, const double* __restrict__ w, const double* __restrict__ m,
                               const double* __restrict__ lamj, const double* __restrict__ lam, const int* __restrict__ S,
-                              double beta, double gamma, double* __restrict__ tab) {
+                              double beta, double gamma, double* __restrict__ tab, const MoveSched* __restrict__ ms) {
+    if (ms) { beta = ms->beta; gamma = ms->gamma; }
     const int Kr = K * r;
     for (int t = threadIdx.x; t < Kr; t += blockDim.x) {
         const int s = t % r;
@@ -98,9 +99,9 @@ __global__ void k_move_tables(int K, int r, const double* __restrict__ w, const 
     }
 }
 
-void launch_move_tables(Ctx& c) {
+void launch_move_tables(Ctx& c, const MoveSched* ms) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
-    k_move_tables<<<1, 256, 0, c.stream>>>(c.K, c.r, c.gw, c.gmu, c.glam, c.lam, c.S, c.beta, gamma, c.tab); ++c.pc.launches;
+    k_move_tables<<<1, 256, 0, c.stream>>>(c.K, c.r, c.gw, c.gmu, c.glam, c.lam, c.S, c.beta, gamma, c.tab, ms); ++c.pc.launches;
     check(cudaGetLastError(), "move tables");
 }
 
@@ -112,7 +113,9 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
                                                  const int* __restrict__ S, const double* __restrict__ tab, double beta, double gamma,
                                                  uint32_t step, Key key, double* __restrict__ lfwd, double* __restrict__ lrev,
                                                  const float2* __restrict__ ntab, NormalConsts nc, const double* __restrict__ G,
-                                                 const double* __restrict__ lam, const double* __restrict__ glam, double kt) {
+                                                 const double* __restrict__ lam, const double* __restrict__ glam, double kt,
+                                                 const MoveSched* __restrict__ ms) {
+    if (ms) { beta = ms->beta; gamma = ms->gamma; step += ms->step; }
     __shared__ int s_j;
     __shared__ float2 tab_s[NORMAL_TAB];
     for (int i = threadIdx.x; i < NORMAL_TAB; i += blockDim.x) tab_s[i] = ntab[i];
@@ -178,12 +181,12 @@ __global__ void __launch_bounds__(256) k_propose(int d, int K, int r, const doub
     }
 }
 
-void launch_propose(Ctx& c) {
+void launch_propose(Ctx& c, const MoveSched* ms, uint32_t step_off) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
     const bool drift = c.cfg.kernel == SMC_K_GMPCNL;
-    k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma, c.step, c.key,
-                                         c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab), c.normc,
-                                         drift ? c.G : nullptr, c.lam, c.glam, (1.0 - gamma) * c.t); ++c.pc.launches;
+    k_propose<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.slot, c.S, c.tab, c.beta, gamma,
+                                         ms ? step_off : c.step, c.key, c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab),
+                                         c.normc, drift ? c.G : nullptr, c.lam, c.glam, (1.0 - gamma) * c.t, ms); ++c.pc.launches;
     check(cudaGetLastError(), "propose");
 }
 
@@ -199,7 +202,9 @@ __global__ void __launch_bounds__(256) k_propose_full(int d, int K, int r, const
                                                       const double* __restrict__ tab, const double* __restrict__ L,
                                                       const double* __restrict__ Li, const double* __restrict__ logdet,
                                                       double beta, double gamma, uint32_t step, Key key, double* __restrict__ lfwd,
-                                                      double* __restrict__ lrev, const float2* __restrict__ ntab, NormalConsts nc) {
+                                                      double* __restrict__ lrev, const float2* __restrict__ ntab, NormalConsts nc,
+                                                      const MoveSched* __restrict__ ms) {
+    if (ms) { beta = ms->beta; gamma = ms->gamma; step += ms->step; }
     __shared__ int s_j;
     __shared__ float2 tab_s[NORMAL_TAB];
     __shared__ double zS[MAXR], ef[MAXR], er[MAXR];
@@ -283,11 +288,11 @@ __global__ void __launch_bounds__(256) k_propose_full(int d, int K, int r, const
     }
 }
 
-void launch_propose_full(Ctx& c) {
+void launch_propose_full(Ctx& c, const MoveSched* ms, uint32_t step_off) {
     const double gamma = sqrt(1.0 - c.beta * c.beta);
     k_propose_full<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.X, c.V, c.sqrtlam, c.lam, c.slot, c.S, c.tab, c.gL, c.gLi, c.glogdet,
-                                              c.beta, gamma, c.step, c.key, c.lfwd, c.lrev, reinterpret_cast<const float2*>(c.normtab),
-                                              c.normc); ++c.pc.launches;
+                                              c.beta, gamma, ms ? step_off : c.step, c.key, c.lfwd, c.lrev,
+                                              reinterpret_cast<const float2*>(c.normtab), c.normc, ms); ++c.pc.launches;
     check(cudaGetLastError(), "propose full");
 }
 
@@ -304,7 +309,9 @@ __global__ void __launch_bounds__(256) k_accept(int d, int K, int r, int kernel,
                                                 const double* __restrict__ tab, const double* __restrict__ lfwd,
                                                 const double* __restrict__ lrev, double* __restrict__ X, const double* __restrict__ V,
                                                 double* __restrict__ Phi, const double* __restrict__ PhiV,
-                                                double* __restrict__ logalpha, unsigned char* __restrict__ acc, int* __restrict__ count) {
+                                                double* __restrict__ logalpha, unsigned char* __restrict__ acc, int* __restrict__ count,
+                                                const MoveSched* __restrict__ ms) {
+    if (ms) { t = ms->t; step += ms->step; }
     __shared__ int s_acc;
     const int p = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -340,9 +347,9 @@ __global__ void __launch_bounds__(256) k_accept(int d, int K, int r, int kernel,
     }
 }
 
-void launch_accept(Ctx& c, int* acc_count) {
-    k_accept<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.cfg.kernel, c.t, c.step, c.key, c.tab, c.lfwd, c.lrev, c.X, c.V, c.Phi,
-                                        c.PhiV, c.logalpha, c.acc, acc_count); ++c.pc.launches;
+void launch_accept(Ctx& c, int* acc_count, const MoveSched* ms, uint32_t step_off) {
+    k_accept<<<c.N, 256, 0, c.stream>>>(c.d, c.K, c.r, c.cfg.kernel, c.t, ms ? step_off : c.step, c.key, c.tab, c.lfwd, c.lrev, c.X,
+                                        c.V, c.Phi, c.PhiV, c.logalpha, c.acc, acc_count, ms); ++c.pc.launches;
     check(cudaGetLastError(), "accept");
 }
 

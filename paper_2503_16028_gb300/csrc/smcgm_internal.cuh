@@ -138,6 +138,12 @@ struct InnerSolver {
 
 struct Partials { double *rr, *rz, *pq, *res; int ntiles; };
 
+// Counters of the solves run inside a CUDA graph (device; the host reads them afterwards).
+struct GraphCounters {
+    unsigned long long cg_iterations, inner_solves, residuals, nonconv;
+    int itmax, pad;
+};
+
 struct Ctx;
 
 // kernels / launchers (defined in the .cu files)
@@ -161,12 +167,20 @@ struct Rhs {
 };
 Rhs shared_rhs(const Ctx& c);
 int solve_batch(Ctx& c, int count, const Rhs& R, double* W);   // W: the FP64 solutions (count x n x n)
+void forward_solve_graph(Ctx& c, const double* X, int count, double* Phi_out);   // into the graph being captured
+void capture_move_steps(Ctx& c, int steps, int* acc_count);                      // into the graph being captured
 void launch_mark_out_of_range(Ctx& c, int count, double* Phi);
 void launch_observe(Ctx& c, const double* w, int count, double* Phi);
 void launch_forward1d(Ctx& c, const double* X, int count, double* Phi, double* w_out);
-void launch_move_tables(Ctx& c);
-void launch_propose(Ctx& c);
-void launch_accept(Ctx& c, int* acc_count);
+// Schedule of a move read from device memory by the move kernels of a CUDA graph
+// (t, beta, gamma and the Philox step of its first step); null: the host's values.
+struct MoveSched {
+    double t, beta, gamma;
+    unsigned int step, pad;
+};
+void launch_move_tables(Ctx& c, const MoveSched* ms = nullptr);
+void launch_propose(Ctx& c, const MoveSched* ms = nullptr, uint32_t step_off = 0);
+void launch_accept(Ctx& c, int* acc_count, const MoveSched* ms = nullptr, uint32_t step_off = 0);
 void launch_propose_pcnl(Ctx& c);
 void launch_gmpcnl_terms(Ctx& c);
 void launch_copy_accepted_gradients(Ctx& c);
@@ -176,7 +190,7 @@ void launch_resample(Ctx& c);
 double gm_fit_device(Ctx& c);
 void factor_mixture(Ctx& c, const double* cov_host);   // Cholesky, inverse and log det of every C_j (device); waits
 size_t cov_partial_doubles(int K, int r);               // scratch of the full-covariance contraction
-void launch_propose_full(Ctx& c);
+void launch_propose_full(Ctx& c, const MoveSched* ms = nullptr, uint32_t step_off = 0);
 void launch_moments(Ctx& c, double* mean, double* var);
 void launch_grid_moments(Ctx& c, const double* mean_kl, double* mean_grid, double* var_grid);
 int gradient_batch(Ctx& c, const double* X, int count, double* Phi_out, double* grad_out);   // largest CG iteration count
@@ -247,6 +261,16 @@ struct Ctx {
     bool lenient = false;      // in a move: such proposals are rejected instead of failing the call
     int sm_count = 0;
     std::string err;
+    // CUDA-graph capture of the solver and the move (smc_batch_*): launches are sized
+    // before the active counts are known and read them from device memory; the loops
+    // become conditional nodes whose bodies are captured on the auxiliary streams.
+    bool graph = false;
+    int gdepth = 0;                   // nesting depth of the body being captured
+    cudaStream_t gaux[4] = {nullptr, nullptr, nullptr, nullptr};
+    GraphCounters* gcnt = nullptr;    // device counters of graph-mode solves
+    int* gouter = nullptr;            // device: [0] refinement phase, [1] particles entering it
+    MoveSched* msched = nullptr;      // device schedule of a graph-mode move
+    int* gsteps = nullptr;            // device: steps left in a graph-mode move
 };
 
 // status helper

@@ -459,6 +459,7 @@ struct CoarseLevelPtrs {
     const T* Kw[12]; const T* Ks[12]; const T* E[12]; const T* Nn[12];
     const T* rtop; T* etop;
     int ntop, nlev;   // nlev levels: ntop, ntop/2, ..., 1
+    const int* nact;  // device count of active particles (a launch sized before it was known), or null
 };
 
 template <typename T>
@@ -496,6 +497,7 @@ __device__ inline void chalf(const T* kw, const T* ks, const T* E, const T* Nn, 
 template <typename T, int NU>
 __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, const int* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (P.nact && (int)blockIdx.x >= *P.nact) return;
     const int pb = active[blockIdx.x];   // active-particle list
     T* kw[12]; T* ks[12]; T* E[12]; T* Nn[12]; T* r[12]; T* e[12];
     T* cur = reinterpret_cast<T*>(smraw);
@@ -926,6 +928,7 @@ static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, co
     TmaMaps& M = *s.maps;
     WPreArgs<float> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = s.p[pc];
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
     A.cg = CG ? 1 : 0; A.want_rr = want_rr;
@@ -950,6 +953,7 @@ static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, c
     TmaMaps& M = *s.maps;
     WPostArgs<float> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (float)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = CG ? 1 : 0;
     const CUtensorMap& mkw = FB == 2 ? M.kwb[level] : M.kw[level];
@@ -1022,6 +1026,7 @@ static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T*
     LevelArrays<T>& L = s.lv[level];
     WPreArgs<T> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
     A.cg = cg; A.want_rr = want_rr; A.Kwb = L.Kwb; A.Ksb = L.Ksb;
@@ -1044,6 +1049,7 @@ static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T
     LevelArrays<T>& L = s.lv[level];
     WPostArgs<T> A{};
     A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg; A.Kwb = L.Kwb; A.Ksb = L.Ksb;
     const int grid = (A.a.total + WPB - 1) / WPB;
@@ -1071,6 +1077,7 @@ static void launch_coarse(Ctx& c, InnerSolver<T>& s, int nact) {
     }
     P.rtop = s.lv[top].r;
     P.etop = s.lv[top].e2;
+    P.nact = c.graph ? s.nact : nullptr;
     const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
     if (c.cfg.smooth_sweeps == 1) k_coarse<T, 1><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
     else k_coarse<T, 2><<<nact, 256, cs, c.stream>>>(P, (T)c.cfg.coarse_scale, s.list);
@@ -1175,6 +1182,7 @@ struct Passes {
         if (path != 0) {
             WApplyArgs<T> A{};
             A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+            A.a.nact = c.graph ? s.nact : nullptr;
             A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
             A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;
             k_wapply<T, sizeof(T) == 4 ? 7 : 4><<<(A.a.total + WPB - 1) / WPB, 32 * WPB, 0, c.stream>>>(A); ++c.pc.launches;
@@ -1368,6 +1376,309 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
         if (o == max_outer - 1) c.nonconv += h;
     }
     return itmax;
+}
+
+
+// ---------------------------------------------------------------------------
+// Graph mode: the solve captured into a CUDA graph, its loops on the device.
+//
+// The refinement phases and the CG iterations become conditional 'while' nodes
+// whose condition is set by a kernel: the outer one after each phase's FP64
+// residual (more particles above the tolerance and fewer than max_refine phases),
+// the inner one by the compaction of the active list after each CG step (any
+// particle still iterating).  Every launch between two compactions is sized before
+// the active count is known, so each such stage is a 'switch' node over launch-size
+// buckets (count, count/2, ..., 1 particles, rounded up): the compaction picks the
+// smallest bucket that holds the active particles (none when no particle is left),
+// and the kernels read the exact count from device memory.  The CG loop body holds
+// two iterations, so its ping-pong buffers come back to their entry state.  Both
+// loops are bounded: a particle leaves CG after max_iter iterations, and the
+// refinement stops after max_refine phases.  The counters that the host loop keeps
+// (CG iterations, inner solves, residuals, unconverged solves, largest iteration
+// count) are kept in device memory (GraphCounters).
+// ---------------------------------------------------------------------------
+constexpr int GB_MAX = 16;   // launch-size buckets: count <= 32768 needs 16
+
+__host__ __device__ inline int bucket_size(int count, int b) { return (count + (1 << b) - 1) >> b; }
+
+static int launch_buckets(int count) {
+    int nb = 1;
+    while (bucket_size(count, nb - 1) > 1) ++nb;
+    return nb;
+}
+
+// The smallest launch-size bucket that holds nact particles; nb (no body) for none.
+__device__ inline unsigned int bucket_of(int nact, int count, int nb) {
+    if (nact <= 0) return (unsigned int)nb;
+    int b = 0;
+    while (b + 1 < nb && bucket_size(count, b + 1) >= nact) ++b;
+    return (unsigned int)b;
+}
+
+// The deterministic compaction of k_compact, plus: the previous count added to
+// *add_old, the new one to *add_new, the launch-size bucket of the next stage set
+// on hsw (flags & 1) and 'any active' set on hw (flags & 2).
+__global__ void __launch_bounds__(1024) k_compact_graph(int count, const int* __restrict__ act, int* __restrict__ list,
+                                                        int* __restrict__ nact, unsigned long long* __restrict__ add_old,
+                                                        unsigned long long* __restrict__ add_new, cudaGraphConditionalHandle hsw,
+                                                        int nb, cudaGraphConditionalHandle hw, int flags) {
+    __shared__ int sums[1024];
+    __shared__ int s_run;
+    const int chunk = (count + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * chunk, b1 = min(count, b0 + chunk);
+    int loc = 0;
+    for (int i = b0; i < b1; ++i) loc += act[i] ? 1 : 0;
+    sums[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) { const int v = sums[k]; sums[k] = run; run += v; }
+        const int old = *nact;
+        *nact = run;
+        s_run = run;
+        if (add_old) *add_old += (unsigned long long)old;
+        if (add_new) *add_new += (unsigned long long)run;
+        if (flags & 1) cudaGraphSetConditional(hsw, bucket_of(run, count, nb));
+        if (flags & 2) cudaGraphSetConditional(hw, run > 0 ? 1u : 0u);
+    }
+    __syncthreads();
+    int pos = sums[threadIdx.x];
+    for (int i = b0; i < b1; ++i)
+        if (act[i]) list[pos++] = i;
+}
+
+__global__ void k_fill_int(int* __restrict__ a, int count, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) a[i] = v;
+}
+
+// Before the refinement loop: phase 0, `count` particles entering it, the loop taken.
+__global__ void k_outer_init(cudaGraphConditionalHandle h, int* __restrict__ gouter, int count) {
+    gouter[0] = 0;
+    gouter[1] = count;
+    cudaGraphSetConditional(h, 1u);
+}
+
+// After a refinement phase's residual: its counters, and whether another phase runs.
+__global__ void k_outer_cond(cudaGraphConditionalHandle h, const int* __restrict__ scount, int* __restrict__ gouter, int max_outer,
+                             GraphCounters* __restrict__ g) {
+    const int active = scount[1];                 // particles still above the FP64 tolerance
+    const int o = ++gouter[0];
+    g->residuals += (unsigned long long)gouter[1];
+    gouter[1] = active;
+    g->itmax = max(g->itmax, scount[2]);
+    if (active > 0 && o >= max_outer) g->nonconv += (unsigned long long)active;
+    cudaGraphSetConditional(h, (active > 0 && o < max_outer) ? 1u : 0u);
+}
+
+static cudaGraphConditionalHandle make_handle(cudaStream_t st) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    check(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+    if (cs != cudaStreamCaptureStatusActive || !g) throw CudaError{cudaErrorStreamCaptureInvalidated, "stream not capturing"};
+    cudaGraphConditionalHandle h;
+    check(cudaGraphConditionalHandleCreate(&h, g, 0, 0), "conditional handle");
+    return h;
+}
+
+// Adds a conditional node (while: 1 body; switch: `size` bodies) at the capture
+// position of `st` and makes it the stream's dependency; returns the bodies.
+static void add_conditional_node(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned int size,
+                                 cudaGraph_t* bodies) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    check(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd), "capture info");
+    if (cs != cudaStreamCaptureStatusActive || !g) throw CudaError{cudaErrorStreamCaptureInvalidated, "stream not capturing"};
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node;
+    check(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p), "conditional node");
+    for (unsigned int i = 0; i < size; ++i) bodies[i] = p.conditional.phGraph_out[i];
+    check(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies), "capture dependencies");
+}
+
+// Captures fn()'s launches into `body` on the auxiliary stream of the next depth
+// (the context's launchers use c.stream, which points there meanwhile).
+template <class F>
+static void capture_body(Ctx& c, cudaGraph_t body, F&& fn) {
+    if (c.gdepth >= 4 || !c.gaux[c.gdepth]) throw CudaError{cudaErrorInvalidValue, "graph nesting deeper than the auxiliary streams"};
+    cudaStream_t aux = c.gaux[c.gdepth];
+    check(cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "body capture");
+    cudaStream_t saved = c.stream;
+    c.stream = aux;
+    ++c.gdepth;
+    try {
+        fn();
+    } catch (...) {
+        --c.gdepth;
+        c.stream = saved;
+        cudaGraph_t tmp = nullptr;
+        (void)cudaStreamEndCapture(aux, &tmp);
+        (void)cudaGetLastError();
+        throw;
+    }
+    --c.gdepth;
+    c.stream = saved;
+    cudaGraph_t out = nullptr;
+    check(cudaStreamEndCapture(aux, &out), "end body capture");
+}
+
+template <typename T>
+static void inner_solve_graph(Ctx& c, InnerSolver<T>& s, int count, double tol, double floor2) {
+    SolverScalars& sc = c.sc;
+    Passes<T> P(c, s);
+    if (P.path == 0) throw CudaError{cudaErrorNotSupported, "graph capture needs the warp-tile solver kernels"};
+    const int ntiles = P.ntiles;
+    const int wgrid = (count * 32 + 127) / 128;
+    const double tol2 = tol * tol;
+    const int maxit = c.cfg.max_iter;
+    const int nb = launch_buckets(count);
+    GraphCounters* g = c.gcnt;
+    auto scalar = [&](int mode) {
+        k_scalar<<<wgrid, 128, 0, c.stream>>>(mode, count, ntiles, sc, c.part, tol2, floor2, maxit); ++c.pc.launches;
+    };
+    auto compact = [&](unsigned long long* add_old, unsigned long long* add_new, cudaGraphConditionalHandle hsw,
+                       cudaGraphConditionalHandle hw, int flags) {
+        k_compact_graph<<<1, 1024, 0, c.stream>>>(count, sc.act_in, s.list, s.nact, add_old, add_new, hsw, nb, hw, flags);
+        ++c.pc.launches;
+    };
+    auto switch_stage = [&](cudaGraphConditionalHandle h, auto&& stage) {
+        cudaGraph_t bodies[GB_MAX];
+        add_conditional_node(c.stream, h, cudaGraphCondTypeSwitch, (unsigned int)nb, bodies);
+        for (int b = 0; b < nb; ++b) capture_body(c, bodies[b], [&] { stage(bucket_size(count, b)); });
+    };
+    auto rr_step = [&]() {
+        check(cudaMemsetAsync(sc.count, 0, sizeof(int), c.stream), "memset count");
+        scalar(SM_RR);
+    };
+    scalar(SM_START);
+    check(cudaMemsetAsync(sc.count, 0, 3 * sizeof(int), c.stream), "memset count");
+    const cudaGraphConditionalHandle h0 = make_handle(c.stream);
+    compact(nullptr, nullptr, h0, 0, 1);
+    switch_stage(h0, [&](int L) { P.pre(L, 0, 0, 0); });          // z0 = M r0: the first V-cycle's pre-smoothing
+    scalar(SM_INIT_RR);
+    const cudaGraphConditionalHandle h1 = make_handle(c.stream);
+    compact(nullptr, &g->inner_solves, h1, 0, 1);
+    switch_stage(h1, [&](int L) {                                 // rest of the first V-cycle, then the first CG step
+        P.lower(L); P.post(L, 0); scalar(SM_RZ_FIRST);
+        P.apply(L, 0, 1); scalar(SM_PQ); P.pre(L, 0, 1, 1);
+    });
+    rr_step();
+    const cudaGraphConditionalHandle hA = make_handle(c.stream), hw = make_handle(c.stream);
+    compact(&g->cg_iterations, nullptr, hA, hw, 3);
+    cudaGraph_t wbody;
+    add_conditional_node(c.stream, hw, cudaGraphCondTypeWhile, 1, &wbody);
+    capture_body(c, wbody, [&] {
+        switch_stage(hA, [&](int L) {
+            P.lower(L); P.post(L, 1); scalar(SM_RZ);
+            P.apply(L, 1, 0); scalar(SM_PQ); P.pre(L, 1, 0, 1);
+        });
+        rr_step();
+        const cudaGraphConditionalHandle hB = make_handle(c.stream);
+        compact(&g->cg_iterations, nullptr, hB, 0, 1);
+        switch_stage(hB, [&](int L) {
+            P.lower(L); P.post(L, 0); scalar(SM_RZ);
+            P.apply(L, 0, 0); scalar(SM_PQ); P.pre(L, 0, 1, 1);
+        });
+        rr_step();
+        compact(&g->cg_iterations, nullptr, hA, hw, 3);
+    });
+}
+
+template <typename T>
+static void solve_batch_graph(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, double* W) {
+    const int n = c.n;
+    const int ntiles = (n / TILE) * (n / TILE);
+    dim3 tgrid(ntiles, count);
+    const size_t total = (size_t)n * n * count;
+    set_smem_attrs<T>(c, s);
+    SolverScalars& sc = c.sc;
+    const bool mixed = sizeof(T) == 4;
+    const double tol_out2 = c.cfg.tol_outer * c.cfg.tol_outer;
+    check(cudaMemsetAsync(W, 0, total * sizeof(double), c.stream), "memset w");
+    check(cudaMemsetAsync(s.x, 0, total * sizeof(T), c.stream), "memset x");
+    k_fill_int<<<(count + 255) / 256, 256, 0, c.stream>>>(sc.act_out, count, 1); ++c.pc.launches;
+    k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, R.b64, mixed ? R.bdf : nullptr, R.stride,
+                                                        s.r[0]); ++c.pc.launches;
+    const int sgrid = (count + 127) / 128;
+    const int* badp = (mixed && c.lenient) ? c.badp : nullptr;
+    k_outer<<<sgrid, 128, 0, c.stream>>>(0, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp, badp); ++c.pc.launches;
+    const int max_outer = mixed ? c.cfg.max_refine : std::max(2, c.cfg.max_refine);
+    const double tol_in = mixed ? c.cfg.tol_inner : c.cfg.tol_outer;
+    const double floor2 = 0.25 * tol_out2;
+    const cudaGraphConditionalHandle ho = make_handle(c.stream);
+    k_outer_init<<<1, 1, 0, c.stream>>>(ho, c.gouter, count); ++c.pc.launches;
+    cudaGraph_t obody;
+    add_conditional_node(c.stream, ho, cudaGraphCondTypeWhile, 1, &obody);
+    capture_body(c, obody, [&] {
+        inner_solve_graph<T>(c, s, count, tol_in, floor2);
+        k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, W, s.x, sc.act_out); ++c.pc.launches;
+        if constexpr (sizeof(T) == 4) {
+            LevelArrays<float>& f0 = s.lv[0];
+            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
+                                                       s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
+        } else {
+            k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, W, R.b64, R.stride, s.r[0], c.part.res,
+                                                       sc.act_out); ++c.pc.launches;
+        }
+        check(cudaMemsetAsync(sc.count + 1, 0, sizeof(int), c.stream), "memset");
+        k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp, badp); ++c.pc.launches;
+        k_outer_cond<<<1, 1, 0, c.stream>>>(ho, sc.count, c.gouter, max_outer, c.gcnt); ++c.pc.launches;
+    });
+}
+
+// The forward map of `count` particles (synthesis, set-up, solve, observation) into
+// the graph being captured on c.stream; Phi of an out-of-range field is +inf.
+void forward_solve_graph(Ctx& c, const double* X, int count, double* Phi_out) {
+    if (c.dim != 2) throw CudaError{cudaErrorNotSupported, "graph capture is built for the 2D solver"};
+    for (int off = 0; off < count; off += c.B) {
+        const int cnt = std::min(c.B, count - off);
+        if (mixed_precision(c.cfg) && c.n % FX == 0 && c.n % FY == 0)
+            launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
+        else
+            launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
+        launch_setup_coeffs(c, cnt);
+        if (mixed_precision(c.cfg)) solve_batch_graph<float>(c, c.s32, cnt, shared_rhs(c), c.w64);
+        else solve_batch_graph<double>(c, c.s64, cnt, shared_rhs(c), c.w64);
+        launch_observe(c, c.w64, cnt, Phi_out + off);
+        launch_mark_out_of_range(c, cnt, Phi_out + off);
+    }
+}
+
+// Graph-mode move steps (pCN-GM, pCN and SMC-GM kernels): the proposal tables, then a
+// 'while' node over the steps; each step proposes, solves, accepts and advances the
+// Philox step in the device schedule.
+__global__ void k_steps_init(cudaGraphConditionalHandle h, int* __restrict__ left, int steps) {
+    *left = steps;
+    cudaGraphSetConditional(h, steps > 0 ? 1u : 0u);
+}
+
+__global__ void k_step_next(cudaGraphConditionalHandle h, int* __restrict__ left, MoveSched* __restrict__ ms) {
+    ms->step += 1u;
+    const int l = --(*left);
+    cudaGraphSetConditional(h, l > 0 ? 1u : 0u);
+}
+
+void capture_move_steps(Ctx& c, int steps, int* acc_count) {
+    if (c.cfg.kernel != SMC_K_PCN_GM && c.cfg.kernel != SMC_K_PCN && c.cfg.kernel != SMC_K_GM_INDEP)
+        throw InputError{"graph capture covers the pCN, pCN-GM and SMC-GM kernels"};
+    launch_move_tables(c, c.msched);
+    const cudaGraphConditionalHandle hs = make_handle(c.stream);
+    k_steps_init<<<1, 1, 0, c.stream>>>(hs, c.gsteps, steps); ++c.pc.launches;
+    cudaGraph_t body;
+    add_conditional_node(c.stream, hs, cudaGraphCondTypeWhile, 1, &body);
+    capture_body(c, body, [&] {
+        if (c.cfg.full_cov) launch_propose_full(c, c.msched, 0);
+        else launch_propose(c, c.msched, 0);
+        forward_solve_graph(c, c.V, c.N, c.PhiV);
+        launch_accept(c, acc_count, c.msched, 0);
+        k_step_next<<<1, 1, 0, c.stream>>>(hs, c.gsteps, c.msched); ++c.pc.launches;
+    });
 }
 
 Rhs shared_rhs(const Ctx& c) { return Rhs{c.b64, c.bdf, 0, nullptr, c.b2}; }

@@ -89,10 +89,15 @@ __host__ __device__ inline void quad_pos(int qi, int& qx, int& qy) {
 }
 
 struct WArgs {
-    int n, ntiles, total;   // total = active particles x tiles
+    int n, ntiles, total;   // total = active particles x tiles (when nact is null)
     const int* list;        // active particle indices
     int* err;               // set to 1 by a staged kernel whose bounded wait timed out
+    const int* nact;        // device count of active particles: total = *nact x ntiles
 };
+
+// Work items of a launch: the active particles' tiles, counted on the device when the
+// launch was sized before the count was known (a launch inside a CUDA graph).
+__device__ inline int work_total(const WArgs& a) { return a.nact ? *a.nact * a.ntiles : a.total; }
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
@@ -559,7 +564,7 @@ __global__ void __launch_bounds__(32 * WPB, (BF && !CG) ? 4 : 0) k_wpre(WPreArgs
     __shared__ T sme[WPB][G::EN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WPB + warp;
-    if (item >= A.a.total) return;
+    if (item >= work_total(A.a)) return;
     const int n = A.a.n;
     const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
     const int p = A.a.list[pi];
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     __shared__ T sme[WPB][G::EN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WPB + warp;
-    if (item >= A.a.total) return;
+    if (item >= work_total(A.a)) return;
     const int n = A.a.n, m = n / 2;
     const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
     const int p = A.a.list[pi];
@@ -614,14 +619,13 @@ struct WApplyArgs {
 // MINB: resident blocks per SM asked of the register allocator (7 for FP32:
 // 72 registers without spills, 28 warps per SM to cover the load latency;
 // 4 for FP64: 128 registers).
-template <typename T, int MINB>
-__global__ void __launch_bounds__(32 * WPB, MINB) k_wapply(WApplyArgs<T> A) {
-    constexpr int PW = 48;                    // staged p row stride (tile + ring: 18 columns used)
-    constexpr int PR = WT + 2;                // staged rows
-    __shared__ T smp[WPB][PR * PW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + warp;
-    if (item >= A.a.total) return;
+constexpr int WAPPLY_PW = 48;                 // staged p row stride (tile + ring: 18 columns used)
+constexpr int WAPPLY_PR = WT + 2;             // staged rows
+
+template <typename T>
+__device__ inline void wapply_item(const WApplyArgs<T>& A, T* sp, int lane, int item) {
+    constexpr int PW = WAPPLY_PW;
+    constexpr int PR = WAPPLY_PR;
     const int n = A.a.n;
     const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
     const int p = A.a.list[pi];
@@ -634,7 +638,6 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_wapply(WApplyArgs<T> A) {
     const T* ks = A.Ks + base;
     const bool first = A.first != 0;
     const T b = first ? T(0) : (T)A.betac[p];
-    T* sp = smp[warp];
     const int cx = lane & 15, ry = lane >> 4;
     const int gx = tx * WT + cx;
     // phase 1: loads
@@ -695,6 +698,15 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_wapply(WApplyArgs<T> A) {
     }
     const double tot = warp_sum<T>(pq);
     if (lane == 0) A.part_pq[(size_t)p * A.a.ntiles + tile] = tot;
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(32 * WPB, MINB) k_wapply(WApplyArgs<T> A) {
+    __shared__ T smp[WPB][WAPPLY_PR * WAPPLY_PW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + warp;
+    if (item >= work_total(A.a)) return;
+    wapply_item<T>(A, smp[warp], lane, item);
 }
 
 }  // namespace smcgm

@@ -133,8 +133,9 @@ __device__ inline void item_decode(const WArgs& a, int item, int& p, int& tile, 
 template <class Issue, class Work>
 __device__ inline void warp_pipeline(const WArgs& a, uint64_t* bar, int lane, Issue issue, Work work) {
     const int nw = gridDim.x * TW_WARPS;
+    const int total = work_total(a);
     int item = blockIdx.x * TW_WARPS + (threadIdx.x >> 5);
-    if (item >= a.total) return;
+    if (item >= total) return;
     if (lane == 0) {
         mbar_init(bar, 1);
         mbar_fence_init();
@@ -142,8 +143,8 @@ __device__ inline void warp_pipeline(const WArgs& a, uint64_t* bar, int lane, Is
     }
     __syncwarp();
     uint32_t ph = 0u;
-    for (; item < a.total; item += nw) {
-        const bool more = item + nw < a.total;
+    for (; item < total; item += nw) {
+        const bool more = item + nw < total;
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, ph));
         if (!ok) {
             if (lane == 0) {

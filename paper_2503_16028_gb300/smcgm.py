@@ -41,7 +41,7 @@ class smc_profile(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_longlong), ("cg_iterations", ctypes.c_longlong), ("inner_solves", ctypes.c_longlong),
                 ("residuals", ctypes.c_longlong), ("dom_launches", ctypes.c_longlong), ("dom_particles", ctypes.c_longlong),
                 ("dom_ms", ctypes.c_double), ("dom_bytes", ctypes.c_double), ("launches", ctypes.c_longlong), ("cells", ctypes.c_int),
-                ("word_bytes", ctypes.c_int)]
+                ("word_bytes", ctypes.c_int), ("graph_launches", ctypes.c_longlong)]
 
 
 EXPORTS = {
@@ -74,6 +74,9 @@ EXPORTS = {
     "smc_profile_query": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(smc_profile), ctypes.c_int]),
     "smc_copy_to_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t]),
     "smc_resample_indices_static": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _vp, _vp]),
+    "smc_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "smc_batch_move": (ctypes.c_int, [_vp, _vp]),
+    "smc_batch_destroy": (None, [_vp]),
 }
 
 _LIB = None
@@ -385,3 +388,40 @@ class Sampler:
         out = np.empty(count, dtype=dtype)
         self._check(self.lib.smc_copy_to_host(self.ctx, _ptr(out), ctypes.c_void_p(ptr), out.nbytes), self.ctx)
         return out
+
+
+class Batch:
+    """smc_batch: `steps` moves of several samplers (any grid size, particle count and
+    precision; pCN, pCN-GM or SMC-GM kernels) captured in one CUDA graph and run with one
+    launch per move() -- the same results as smc_move(steps) on each sampler in turn.
+    Keeps the samplers alive; close it before closing them."""
+
+    def __init__(self, samplers, steps):
+        self.lib = load_library()
+        self.samplers = list(samplers)
+        arr = (_vp * len(self.samplers))(*[s.ctx.value for s in self.samplers])
+        out = _vp()
+        st = self.lib.smc_batch_create(arr, len(self.samplers), int(steps), ctypes.byref(out))
+        if st != SMC_OK:
+            raise SMCError(st, self.lib.smc_last_error(None).decode())
+        self.handle = out
+        self.steps = int(steps)
+
+    def move(self, allow_noconv=False):
+        """One launch of the graph; returns the acceptance rate of every sampler."""
+        rates = np.empty(len(self.samplers))
+        st = self.lib.smc_batch_move(self.handle, _ptr(rates))
+        if st != SMC_OK and not (allow_noconv and st == SMC_ENOCONV):
+            raise SMCError(st, self.lib.smc_last_error(None).decode())
+        return rates
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.smc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
