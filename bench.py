@@ -20,10 +20,12 @@ mixed-precision path, the solver-only rate (smc_forward), the end-to-end rate
 through smc_move_host with host buffers, the adjoint-gradient rate, a whole SMC
 run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
 (the posterior error of the mixed-precision run against it), the 64^2 workload on
-the GPU and on the CPU oracle, the SM clocks sampled during the timed region and
-the CPU oracle baseline.
+the GPU (host-driven and as one CUDA graph) and on the CPU oracle, the 32-problem
+batching workload (one after another, a host thread each, one CUDA graph), the SM
+clocks sampled during the timed region and the CPU oracle baseline.
 --smoother bf16 times the BF16-smoother mode as the headline; --no-fp64, --no-alt-smoother,
---no-e2e, --no-forward, --no-em, --no-gradient, --no-layers, --no-small and --no-cpu leave legs out.
+--no-e2e, --no-forward, --no-em, --no-batch, --no-gradient, --no-layers, --no-small and --no-cpu leave
+legs out.
 """
 import argparse
 import json
@@ -63,6 +65,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (host buffers)")
     ap.add_argument("--no-forward", action="store_true", help="skip the solver-only leg")
     ap.add_argument("--no-em", action="store_true", help="skip the EM-fit timing")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-problem batching workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -360,14 +363,53 @@ def precision_agreement(s64, moves, wl, N, smcgm):
 
 
 def time_small(args, smcgm, torch, barrier):
-    """GPU solves/s on the 64^2 workload (32^2 modes, N = 1024, K = 4), timed like the headline."""
+    """GPU solves/s on the 64^2 workload (32^2 modes, N = 1024, K = 4), timed like the headline
+    (host-driven smc_move, CUDA events), and the same moves as one CUDA graph (smc_batch of
+    this one problem, --steps moves per launch, wall clock around the launch)."""
     from paper_2503_16028_gb300 import inputs
     wl = inputs.load_workload(SMALL_WORKLOAD)
-    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, wl["n_particles"], smcgm)
+    N = wl["n_particles"]
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
     ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
+    b = smcgm.Batch([s], args.steps)
+    b.move(allow_noconv=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        b.move(allow_noconv=True)
+    torch.cuda.synchronize()
+    gsec = (time.perf_counter() - t0) / reps
+    b.close()
     s.close()
-    return dict(workload=SMALL_WORKLOAD, particles=wl["n_particles"], value=wl["n_particles"] * args.steps / (ms / 1000.0),
-                unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
+    return dict(workload=SMALL_WORKLOAD, particles=N, value=N * args.steps / (ms / 1000.0),
+                unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]),
+                graph=dict(value=N * args.steps / gsec, unit=UNIT, ms_per_launch=1000.0 * gsec, moves_per_launch=args.steps))
+
+
+def time_batch32(smcgm, torch, steps=2):
+    """The batching workload: 32 independent Darcy problems (grids 64^2..512^2, 256..4096
+    particles, 16..256 observations, sigma 0.002..0.02; inputs.batch_specs), each taken
+    through one tempering layer and a mixture fit, then `steps` moves of all of them timed
+    one after another, with a host thread per problem, and as one CUDA graph."""
+    from paper_2503_16028_gb300 import batch, inputs
+    specs = inputs.load_batch_workload(32)
+    samplers = batch.make_samplers(batch.batch_configs(specs))
+    for sm in samplers:
+        sm.smc_temper_step()
+        sm.smc_resample()
+        sm.gm_fit()
+    modes = batch.time_moves(samplers, steps)
+    cells = sum(sp["n"] ** 2 * sp["n_particles"] for sp in specs)
+    for sm in samplers:
+        sm.close()
+    torch.cuda.empty_cache()
+    out = dict(workload="batch32: 32 independent Darcy problems, grids 64^2..512^2, 256..4096 particles",
+               problems=len(specs), moves=steps, particle_solves_per_move=sum(sp["n_particles"] for sp in specs),
+               cell_solves_per_move=cells, unit=UNIT, **modes)
+    out["graph_vs_sequential"] = modes["graph"]["solves_per_s"] / modes["sequential"]["solves_per_s"]
+    out["graph_vs_threads"] = modes["graph"]["solves_per_s"] / modes["threads"]["solves_per_s"]
+    return out
 
 
 def time_em(wl, N, smcgm, torch, calls=2):
@@ -574,6 +616,7 @@ def run_native(args, rank, world, local):
     layers = posterior = None
     if not args.no_layers:
         layers, posterior = time_layers(wl, N, smcgm, torch, fp64=not args.no_fp64)
+    batch32 = None if args.no_batch else time_batch32(smcgm, torch)
     small = None
     if not args.no_small:
         small = time_small(args, smcgm, torch, barrier)
@@ -595,7 +638,7 @@ def run_native(args, rank, world, local):
                 fp64_agreement=agree,
                 solver_only=forward, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
                 cpu_baseline=cpu,
-                adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small)
+                adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small, batch_workload=batch32)
     print(json.dumps(line), flush=True)
 
 

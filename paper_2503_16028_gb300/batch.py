@@ -8,6 +8,11 @@ a few hundred particles) that cannot fill 152 SMs alone overlap on the GPU.
 A problem's result does not depend on the others (its kernels touch only its
 own workspace, and its random numbers are its own Philox streams).
 
+One graph: `smcgm.Batch` captures the moves of many contexts (any grid size,
+particle count and precision) into one CUDA graph whose loops run on the device
+(`smc_batch_*`): one launch moves every problem, with no host round trip inside
+the move.  `time_moves` compares it with the other two ways on the same problems.
+
 Autotuning: the multigrid smoothing counts, the coarse-correction factor and
 the inner tolerance are run-time settings (`smc_config`); `autotune` times
 `smc_move` for each candidate on the problem itself and keeps the fastest.
@@ -15,6 +20,7 @@ Every candidate meets the same FP64 tolerance, so the choice changes speed,
 not the answer beyond that tolerance.
 """
 import concurrent.futures as cf
+import ctypes
 import json
 import time
 
@@ -146,3 +152,73 @@ def mesh_sweep(preset, grids, n_particles, kl_modes, mcmc_steps, max_layers=200,
     for s in samplers:
         s.close()
     return out, seconds
+
+
+def capped_solve_batch(cfg, budget_bytes):
+    """The largest solve batch (particles solved per launch sequence) whose share of the
+    workspace fits `budget_bytes`, at most all particles; the results do not depend on it."""
+    lib = smcgm.load_library()
+    size = ctypes.c_size_t()
+
+    def ws(b):
+        cfg.solve_batch = int(b)
+        st = lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size))
+        if st != smcgm.SMC_OK:
+            raise smcgm.SMCError(st, lib.smc_last_error(None).decode())
+        return size.value
+    per_particle = ws(2) - ws(1)
+    return int(min(cfg.n_particles, max(1, budget_bytes // max(1, per_particle))))
+
+
+def batch_configs(specs, budget_bytes=3e9):
+    """smc_config of every problem of a batching workload (inputs.load_batch_workload), each
+    solve batch capped so that its solver workspace stays within `budget_bytes`."""
+    cfgs = []
+    for sp in specs:
+        cfg = smcgm.make_config(sp)
+        cfg.solve_batch = capped_solve_batch(cfg, budget_bytes)
+        cfgs.append(cfg)
+    return cfgs
+
+
+def time_moves(samplers, steps, modes=("sequential", "threads", "graph")):
+    """`steps` moves of every sampler (each with a fitted mixture), timed three ways: one
+    sampler after another (smc_move), concurrently with a host thread per sampler, and as
+    one CUDA graph (smcgm.Batch, one launch).  Each way is warmed up once first.  Returns
+    {mode: dict(seconds, solves, solves_per_s, cg_per_solve)} and, for the graph, the
+    seconds its capture and instantiation took."""
+    import torch
+    out = {}
+    for mode in modes:
+        batch = None
+        if mode == "graph":
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            batch = smcgm.Batch(samplers, steps)
+            capture_s = time.perf_counter() - t0
+
+        def run():
+            if mode == "sequential":
+                for sm in samplers:
+                    sm.smc_move(steps, allow_noconv=True)
+            elif mode == "threads":
+                with cf.ThreadPoolExecutor(max_workers=len(samplers)) as ex:
+                    list(ex.map(lambda sm: sm.smc_move(steps, allow_noconv=True), samplers))
+            else:
+                batch.move(allow_noconv=True)
+        run()                                                  # warm-up
+        for sm in samplers:
+            sm.smc_profile_query(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        prof = [sm.smc_profile_query(reset=True) for sm in samplers]
+        solves = sum(p["solves"] for p in prof)
+        out[mode] = dict(seconds=sec, solves=solves, solves_per_s=solves / sec,
+                         cg_per_solve=sum(p["cg_iterations"] for p in prof) / max(1, solves))
+        if batch is not None:
+            out[mode]["capture_seconds"] = capture_s
+            batch.close()
+    return out

@@ -104,3 +104,40 @@ def structured_log_weights(seed, N, scale=3.0):
     lw[N // 4:N // 4 + 16] = lw[N // 4]
     lw[N // 3] = hi + 2.0
     return lw
+
+
+BATCH_SEED = 20250320
+BATCH_GRIDS = (64, 128, 256, 512)
+BATCH_PARTICLES = (256, 1024, 4096)
+
+
+def batch_specs(count=32, seed=BATCH_SEED):
+    """Seeded specifications of `count` independent 2D Darcy inverse problems (the batching
+    workload): grid n uniform in {64, 128, 256, 512}, particles uniform in {256, 1024, 4096},
+    16 to 256 observation points uniform in [0.05, 0.95]^2, sigma uniform in [0.002, 0.02];
+    the prior of the metric workload (alpha = 0.02) on min(64, n/2)^2 cosine modes, f as in
+    the metric workload, K = 4 components on r = 64 modes, 10 moves per layer, and a seed per
+    problem.  Numbers and seeded arrays only; the data come from tests/golden."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(BATCH_GRIDS))
+        N = int(rng.choice(BATCH_PARTICLES))
+        n_obs = int(rng.integers(16, 257))
+        sigma = float(rng.uniform(0.002, 0.02))
+        obs = rng.uniform(0.05, 0.95, size=(n_obs, 2))
+        out.append(dict(index=i, dim=2, n=n, kl_modes=min(64, n // 2), alpha=0.02, sigma=sigma, source_kind=1,
+                        src_amp=10.0, src_width=50.0, n_particles=N, n_components=4, gm_rank=64, mcmc_steps=10,
+                        beta0=0.2, ess_frac=0.5, data_refine=2, seed=seed + 1000 + i, obs=obs))
+    return out
+
+
+def load_batch_workload(count=32):
+    """The batching workload: batch_specs merged with the stored data of each problem."""
+    with open(os.path.join(GOLDEN_DIR, "workload_batch%d.json" % count)) as fh:
+        stored = json.load(fh)
+    specs = batch_specs(count)
+    for sp, st in zip(specs, stored["problems"]):
+        assert st["index"] == sp["index"] and st["n"] == sp["n"] and len(st["data"]) == len(sp["obs"])
+        sp["data"] = np.asarray(st["data"], dtype=np.float64)
+    return specs

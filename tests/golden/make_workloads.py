@@ -45,8 +45,34 @@ def make(name):
     return out
 
 
+def make_batch(count=32):
+    """workload_batch<count>.json: the data of the batching workload's problems
+    (inputs.batch_specs): truth = a prior draw (Philox TRUTH, the problem's seed), data =
+    its observations on a grid refined x2 up to 512^2 (a 512^2 problem's data come from its
+    own grid) plus sigma * N(0, 1) (Philox DATA)."""
+    out = []
+    for sp in inputs.batch_specs(count):
+        lam = prior.eigenvalues(2, sp["kl_modes"], sp["alpha"])
+        truth = np.sqrt(lam) * philox.normals(sp["seed"], lam.shape[0], 0, 0, philox.TRUTH)
+        fine = {k: v for k, v in sp.items() if k not in ("obs", "index")}
+        fine["n"] = min(2 * sp["n"], 512)
+        prob = problem.Problem(obs=sp["obs"], data=np.zeros(len(sp["obs"])), **fine)
+        y = prob.forward(truth)
+        data = y + sp["sigma"] * philox.normals(sp["seed"], len(sp["obs"]), 0, 0, philox.DATA)
+        out.append(dict(index=sp["index"], n=sp["n"], data=[round(float(v), 17) for v in data]))
+        print("batch problem", sp["index"], "n", sp["n"], "N", sp["n_particles"], "obs", len(data), flush=True)
+    doc = dict(count=count, problems=out,
+               recipe="problems from paper_2503_16028_gb300.inputs.batch_specs; truth = sqrt(lambda)*N(0,1) [Philox TRUTH]; "
+                      "data = F(truth) on a grid refined x2 up to 512^2 + sigma*N(0,1) [Philox DATA]")
+    with open(os.path.join(HERE, "workload_batch%d.json" % count), "w") as fh:
+        json.dump(doc, fh)
+
+
 if __name__ == "__main__":
-    names = sys.argv[1:] or list(inputs.PRESETS)
+    names = sys.argv[1:] or list(inputs.PRESETS) + ["batch32"]
     for nm in names:
+        if nm == "batch32":
+            make_batch(32)
+            continue
         o = make(nm)
         print(nm, "obs", len(o["obs"]), "data[:4]", np.round(o["data"][:4], 5))

@@ -75,3 +75,41 @@ def test_run_smc_writes_one_json_line_per_layer(tmp_path):
     s = _Sampler()
     batch.run_smc(s, mcmc_steps=2)
     assert s.counts["solves"] == 3 * 20
+
+
+def test_batch_specs_are_seeded_and_in_range():
+    from paper_2503_16028_gb300 import inputs
+    a, b = inputs.batch_specs(), inputs.batch_specs()
+    assert len(a) == 32
+    for x, y in zip(a, b):
+        assert x["n"] == y["n"] and x["n_particles"] == y["n_particles"] and np.array_equal(x["obs"], y["obs"])
+        assert x["n"] in (64, 128, 256, 512) and x["n_particles"] in (256, 1024, 4096)
+        assert 16 <= len(x["obs"]) <= 256 and 0.002 <= x["sigma"] <= 0.02
+        assert np.all((x["obs"] > 0.0) & (x["obs"] < 1.0)) and x["kl_modes"] <= x["n"] // 2
+    assert len({sp["n"] for sp in a}) == 4                      # every grid size drawn
+    w = inputs.load_batch_workload(32)
+    assert all(len(sp["data"]) == len(sp["obs"]) and np.all(np.isfinite(sp["data"])) for sp in w)
+
+
+def test_capped_solve_batch_fits_the_budget():
+    """The cap uses the library's workspace size (no GPU needed): the solver share of the
+    workspace at the chosen batch fits the budget, one more particle would not (or all fit)."""
+    import ctypes
+    from paper_2503_16028_gb300 import build, inputs, smcgm
+    build.build()
+    lib = smcgm.load_library()
+    sp = next(x for x in inputs.load_batch_workload(32) if x["n"] == 512 and x["n_particles"] == 4096)
+    cfg = smcgm.make_config(sp)
+    budget = 3e9
+    B = batch.capped_solve_batch(cfg, budget)
+    size = ctypes.c_size_t()
+
+    def ws(b):
+        cfg.solve_batch = b
+        assert lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)) == smcgm.SMC_OK
+        return size.value
+    per = ws(2) - ws(1)
+    assert 1 <= B < 4096
+    assert B * per <= budget < (B + 1) * per
+    small = smcgm.make_config(next(x for x in inputs.load_batch_workload(32) if x["n"] == 64))
+    assert batch.capped_solve_batch(small, budget) == small.n_particles

@@ -111,6 +111,19 @@ def test_metric_grid_in_graph_equals_host_loop():
     graph.close()
 
 
+def test_largest_grid_in_graph_equals_host_loop():
+    """512^2 (four tiled levels), 8 particles in ragged solve batches of 3."""
+    host, graph = _twins("darcy256_precision", n=512, n_particles=8, n_components=2, solve_batch=3)
+    b = smcgm.Batch([graph], steps=1)
+    acc_h, _ = host.smc_move(1)
+    acc_g = b.move()
+    assert acc_g[0] == acc_h
+    _same_state(host, graph)
+    b.close()
+    host.close()
+    graph.close()
+
+
 def test_batch_rejects_unsupported_contexts():
     wl = inputs.load_workload("darcy64_bimodal")
     s = smcgm.Sampler(smcgm.make_config(wl, n_particles=8, n_components=1, kernel=smcgm.SMC_K_PCNL, gradient=1))
