@@ -24,8 +24,8 @@ the GPU (host-driven and as one CUDA graph) and on the CPU oracle, the 32-proble
 batching workload (one after another, a host thread each, one CUDA graph), the SM
 clocks sampled during the timed region and the CPU oracle baseline.
 --smoother bf16 times the BF16-smoother mode as the headline; --no-fp64, --no-alt-smoother,
---no-e2e, --no-forward, --no-em, --no-batch, --no-gradient, --no-layers, --no-small and --no-cpu leave
-legs out.
+--no-e2e, --no-forward, --no-em, --no-batch, --no-autotune, --no-gradient, --no-layers, --no-small and
+--no-cpu leave legs out.
 """
 import argparse
 import json
@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-forward", action="store_true", help="skip the solver-only leg")
     ap.add_argument("--no-em", action="store_true", help="skip the EM-fit timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-problem batching workload")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the solver-setting autotuner on the 64^2 workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0, help="oracle time of the whole reference run")
     return ap.parse_args()
@@ -387,6 +388,16 @@ def time_small(args, smcgm, torch, barrier):
                 graph=dict(value=N * args.steps / gsec, unit=UNIT, ms_per_launch=1000.0 * gsec, moves_per_launch=args.steps))
 
 
+def autotune_small(smcgm):
+    """batch.autotune on the 64^2 workload (N = 1024): every candidate setting (stencil-tile
+    kernels, smoothing counts, coarse factor, inner tolerance) timed over two moves."""
+    from paper_2503_16028_gb300 import batch, inputs
+    wl = inputs.load_workload(SMALL_WORKLOAD)
+    best, timings = batch.autotune(wl, n_particles=wl["n_particles"], steps=2, reps=2)
+    return dict(workload=SMALL_WORKLOAD, particles=wl["n_particles"], best=best,
+                ms_per_move=[dict(setting=c, ms=t) for c, t in timings])
+
+
 def time_batch32(smcgm, torch, steps=2):
     """The batching workload: 32 independent Darcy problems (grids 64^2..512^2, 256..4096
     particles, 16..256 observations, sigma 0.002..0.02; inputs.batch_specs), each taken
@@ -617,6 +628,7 @@ def run_native(args, rank, world, local):
     if not args.no_layers:
         layers, posterior = time_layers(wl, N, smcgm, torch, fp64=not args.no_fp64)
     batch32 = None if args.no_batch else time_batch32(smcgm, torch)
+    tuned = None if args.no_autotune else autotune_small(smcgm)
     small = None
     if not args.no_small:
         small = time_small(args, smcgm, torch, barrier)
@@ -638,7 +650,8 @@ def run_native(args, rank, world, local):
                 fp64_agreement=agree,
                 solver_only=forward, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
                 cpu_baseline=cpu,
-                adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small, batch_workload=batch32)
+                adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small, batch_workload=batch32,
+                autotune=tuned)
     print(json.dumps(line), flush=True)
 
 

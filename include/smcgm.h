@@ -124,6 +124,13 @@ typedef struct smc_config {
     int full_cov;       /* 1: mixture components with full r x r covariances on the mixture
                            modes (EM with the ridge var_floor * diag(lambda_S)); 0: diagonal
                            lambda_j as in Sec. 2.3.  pCN-GM and independence kernels only */
+    int tile_kernel;    /* stencil tiles of the multigrid / CG passes on the tiled levels:
+                           0 = the default (2); 1 = 32 x 32 tiles, one thread block each;
+                           2 = 16 x 16 tiles, one warp each, the finest level's inputs staged
+                           by TMA (FP32; the FP64 solver uses 3); 3 = 16 x 16 tiles, one warp
+                           each, loading from global memory.  Same results to the solver
+                           tolerance; a speed choice (batch.autotune times them).  smc_batch_*
+                           needs 0, 2 or 3 */
 } smc_config;
 
 /* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */

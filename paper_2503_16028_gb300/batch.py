@@ -13,9 +13,11 @@ particle count and precision) into one CUDA graph whose loops run on the device
 (`smc_batch_*`): one launch moves every problem, with no host round trip inside
 the move.  `time_moves` compares it with the other two ways on the same problems.
 
-Autotuning: the multigrid smoothing counts, the coarse-correction factor and
-the inner tolerance are run-time settings (`smc_config`); `autotune` times
-`smc_move` for each candidate on the problem itself and keeps the fastest.
+Autotuning: the stencil tiles of the multigrid / CG passes (32 x 32 tiles per
+thread block, or 16 x 16 tiles per warp with or without TMA staging), the
+multigrid smoothing counts, the coarse-correction factor and the inner
+tolerance are run-time settings (`smc_config`); `autotune` times `smc_move`
+for each candidate on the problem itself and keeps the fastest.
 Every candidate meets the same FP64 tolerance, so the choice changes speed,
 not the answer beyond that tolerance.
 """
@@ -94,6 +96,8 @@ def run_batch(samplers, mcmc_steps, max_layers=200, concurrent=True):
 
 DEFAULT_CANDIDATES = (
     dict(),                                            # the library defaults
+    dict(tile_kernel=1),                               # 32 x 32 block tiles
+    dict(tile_kernel=3),                               # 16 x 16 warp tiles, global loads
     dict(smooth_sweeps=1),
     dict(fine_sweeps=2),
     dict(tol_inner=2e-4),

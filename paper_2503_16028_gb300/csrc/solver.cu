@@ -1106,16 +1106,12 @@ static void staged_pre(Ctx&, InnerSolver<double>&, int, int, int, int) {}   // t
 static void staged_post(Ctx&, InnerSolver<double>&, int, int) {}
 static void staged_lower(Ctx&, InnerSolver<double>&, int) {}
 
-// Solver kernel family for the tiled levels: 0 = one block per 32 x 32 tile,
-// 1 = persistent warps with TMA-staged 16 x 16 tiles (FP32), 2 = one warp per
-// 16 x 16 tile loading from global memory.
+// Solver kernel family for the tiled levels (cfg.tile_kernel): 0 = one block per
+// 32 x 32 tile, 1 = persistent warps with TMA-staged 16 x 16 tiles (FP32), 2 = one
+// warp per 16 x 16 tile loading from global memory.
 static int tile_path(const Ctx& c, bool fp32) {
-    static int path = -1;
-    if (path < 0) {
-        const char* e = getenv("SMCGM_TILE_PATH");
-        path = e ? atoi(e) : 1;
-        if (path < 0 || path > 2) path = 1;
-    }
+    const int k = c.cfg.tile_kernel;
+    const int path = k == 1 ? 0 : k == 3 ? 2 : 1;
     if (path == 1 && !fp32) return 2;
     if (path == 1 && c.n % WT) return 2;
     return path;

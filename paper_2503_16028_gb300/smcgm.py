@@ -33,7 +33,7 @@ class smc_config(ctypes.Structure):
         ("kernel", ctypes.c_int), ("precision", ctypes.c_int), ("tol_inner", ctypes.c_double), ("tol_outer", ctypes.c_double),
         ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("smooth_sweeps", ctypes.c_int), ("fine_sweeps", ctypes.c_int),
         ("coarse_scale", ctypes.c_double), ("solve_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-        ("gradient", ctypes.c_int), ("full_cov", ctypes.c_int),
+        ("gradient", ctypes.c_int), ("full_cov", ctypes.c_int), ("tile_kernel", ctypes.c_int),
     ]
 
 
@@ -163,7 +163,7 @@ def make_config(preset, **overrides):
     cfg.n_particles = p["n_particles"]; cfg.n_components = p["n_components"]; cfg.gm_rank = p["gm_rank"]
     cfg.beta0 = p["beta0"]; cfg.ess_frac = p["ess_frac"]; cfg.seed = p["seed"]
     for key in ("em_iters", "var_floor", "kernel", "precision", "tol_inner", "tol_outer", "max_iter", "max_refine",
-                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch", "gradient", "full_cov"):
+                "smooth_sweeps", "fine_sweeps", "coarse_scale", "solve_batch", "gradient", "full_cov", "tile_kernel"):
         if key in p:
             setattr(cfg, key, p[key])
     cfg._keep = (obs, data)

@@ -134,6 +134,11 @@ def test_batch_rejects_unsupported_contexts():
     with pytest.raises(smcgm.SMCError) as ei:
         smcgm.Batch([s2, s2], steps=1)
     assert ei.value.status == smcgm.SMC_EINVAL
+    s3 = smcgm.Sampler(smcgm.make_config(wl, n_particles=8, n_components=1, tile_kernel=1))
+    with pytest.raises(smcgm.SMCError) as ei:
+        smcgm.Batch([s3], steps=1)    # the block-tile kernels are sized on the host
+    assert ei.value.status == smcgm.SMC_EINVAL
+    s3.close()
     b = smcgm.Batch([s2], steps=1)
     with pytest.raises(smcgm.SMCError) as ei:
         b.move()                      # no mixture fitted yet

@@ -53,9 +53,12 @@ def test_init_draws_and_potentials_64(precision):
     s.close()
 
 
+@pytest.mark.parametrize("tile_kernel", [0, 1, 3])
 @pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
-def test_forward_solution_matches_exact_solve(precision):
-    wl, cfg, s = _sampler("darcy64_bimodal", n_particles=8, precision=precision)
+def test_forward_solution_matches_exact_solve(precision, tile_kernel):
+    """Every stencil-tile kernel family (16 x 16 warp tiles with TMA staging, 32 x 32 block
+    tiles, 16 x 16 warp tiles with global loads) in every precision."""
+    wl, cfg, s = _sampler("darcy64_bimodal", n_particles=8, precision=precision, tile_kernel=tile_kernel)
     X, Phi = s.particles()
     n = cfg.n
     Xd = torch.tensor(X, dtype=torch.float64, device="cuda")
@@ -92,10 +95,12 @@ def _random_mixture(s, rng, lam0):
     return opcngm.Mixture(modes, w, m, lam, lam0)
 
 
-@pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
-def test_move_step_matches_oracle(precision):
+@pytest.mark.parametrize("precision,tile_kernel", [(smcgm.SMC_P_FP64, 0), (smcgm.SMC_P_FP32_REFINE, 0),
+                                                    (smcgm.SMC_P_BF16SMOOTH_REFINE, 0), (smcgm.SMC_P_FP32_REFINE, 1),
+                                                    (smcgm.SMC_P_FP32_REFINE, 3)])
+def test_move_step_matches_oracle(precision, tile_kernel):
     N = 24
-    wl, cfg, s = _sampler("darcy64_bimodal", n_particles=N, n_components=4, precision=precision)
+    wl, cfg, s = _sampler("darcy64_bimodal", n_particles=N, n_components=4, precision=precision, tile_kernel=tile_kernel)
     prob = oproblem.from_workload(wl)
     rng = np.random.default_rng(11)
     mix = _random_mixture(s, rng, prob.lam)
