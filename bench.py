@@ -374,6 +374,7 @@ def time_small(args, smcgm, torch, barrier):
     ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
     b = smcgm.Batch([s], args.steps)
     b.move(allow_noconv=True)
+    s.smc_profile_query(reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     reps = 3
@@ -381,11 +382,15 @@ def time_small(args, smcgm, torch, barrier):
         b.move(allow_noconv=True)
     torch.cuda.synchronize()
     gsec = (time.perf_counter() - t0) / reps
+    gprof = s.smc_profile_query(reset=True)
     b.close()
     s.close()
     return dict(workload=SMALL_WORKLOAD, particles=N, value=N * args.steps / (ms / 1000.0),
                 unit=UNIT, cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]),
-                graph=dict(value=N * args.steps / gsec, unit=UNIT, ms_per_launch=1000.0 * gsec, moves_per_launch=args.steps))
+                host_syncs_per_move=prof["host_syncs"] / args.steps,
+                graph=dict(value=N * args.steps / gsec, unit=UNIT, ms_per_launch=1000.0 * gsec, moves_per_launch=args.steps,
+                           host_syncs_per_move=gprof["host_syncs"] / (reps * args.steps),
+                           cg_per_solve=gprof["cg_iterations"] / max(1, gprof["solves"])))
 
 
 def autotune_small(smcgm):
@@ -588,7 +593,8 @@ def run_native(args, rank, world, local):
     step_hbm = bps * N / (ms / args.steps / 1000.0) / 1e9
     iters = dict(cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]),
                  inner_solves_per_solve=prof["inner_solves"] / max(1, prof["solves"]),
-                 residuals_per_solve=prof["residuals"] / max(1, prof["solves"]))
+                 residuals_per_solve=prof["residuals"] / max(1, prof["solves"]),
+                 host_syncs_per_move=prof["host_syncs"] / args.steps)
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None if args.no_e2e else time_e2e(s, N, d, args.steps, torch, barrier, world)
     forward = None if args.no_forward else time_forward(s, torch)

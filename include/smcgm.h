@@ -279,6 +279,8 @@ typedef struct smc_profile {
     int cells;                 /* grid cells per solve */
     int word_bytes;            /* bytes per word of the inner solver (4: FP32, 8: FP64) */
     long long graph_launches;  /* launches of batch graphs (smc_batch_move) that moved this context */
+    long long host_syncs;      /* waits of the host for the context's stream (the host-driven solver
+                                  reads its active counts after every CG step; a graph launch: one) */
 } smc_profile;
 
 /* enable: 1 turns event timing of the dominant kernel on, 0 off, any other

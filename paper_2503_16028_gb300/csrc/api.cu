@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
 #include "smcgm_internal.cuh"
 
 namespace smcgm {
@@ -18,6 +19,14 @@ namespace smcgm {
 void check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw CudaError{e, what};
 }
+
+void sync_stream(Ctx& c) {
+    ++c.pc.host_syncs;
+    check(cudaStreamSynchronize(c.stream), "sync");
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 struct Planner {
     char* base;
@@ -249,14 +258,14 @@ static void set_prior_mixture(Ctx& c) {
     check(cudaMemcpyAsync(lam.data(), c.lam, c.d * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "lam");
     std::vector<int> S(c.r);
     check(cudaMemcpyAsync(S.data(), c.S, c.r * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "S");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     std::vector<double> w(c.K, 1.0 / c.K), m((size_t)c.K * c.r, 0.0), l((size_t)c.K * c.r);
     for (int j = 0; j < c.K; ++j)
         for (int s = 0; s < c.r; ++s) l[(size_t)j * c.r + s] = lam[S[s]];
     check(cudaMemcpyAsync(c.gw, w.data(), c.K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "w");
     check(cudaMemcpyAsync(c.gmu, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream), "m");
     check(cudaMemcpyAsync(c.glam, l.data(), l.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream), "lam");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
 }
 
 }  // namespace smcgm
@@ -319,7 +328,7 @@ smc_status smc_copy_to_host(smc_ctx* ctx, void* dst, const void* src, size_t byt
     Ctx& c = ctx->c;
     API_BEGIN
     if (bytes) check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.stream), "copy to host");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return SMC_OK;
     API_END(ctx)
 }
@@ -449,7 +458,7 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     }
     check(cudaMemcpyAsync(c.slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, c.stream), "h2d");
     check(cudaMemsetAsync(c.dev_err, 0, 4 * sizeof(int), c.stream), "memset err");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     {
         int dev = 0;
         check(cudaGetDevice(&dev), "device");
@@ -467,7 +476,7 @@ smc_status smc_init(const smc_config* cfg, void* d_ws, size_t bytes, void* strea
     c.step = 0;
     launch_prior_draw(c, c.X, c.N, 0u, P_INIT);
     forward_solve(c, c.X, c.N, c.Phi, nullptr);
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     c.stage = 1;
     *out = ctx;
     return SMC_OK;
@@ -495,6 +504,7 @@ void smc_destroy(smc_ctx* ctx) {
 
 smc_status smc_temper_step(smc_ctx* ctx, double* h, double* ess, double* logZ_inc, int* done) {
     if (!ctx) return SMC_EINVAL;
+    NvtxRange nvtx("smc_temper_step");
     Ctx& c = ctx->c;
     if (c.stage != 1) return fail(ctx, SMC_ESTATE, "smc_temper_step: expected after init or move");
     if (c.t >= 1.0) return fail(ctx, SMC_ESTATE, "smc_temper_step: t already 1");
@@ -502,7 +512,7 @@ smc_status smc_temper_step(smc_ctx* ctx, double* h, double* ess, double* logZ_in
     double out[4];
     launch_temper(c, c.dscal);
     check(cudaMemcpyAsync(out, c.dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if (h) *h = out[0];
     if (ess) *ess = out[1];
     if (logZ_inc) *logZ_inc = out[2];
@@ -516,11 +526,12 @@ smc_status smc_temper_step(smc_ctx* ctx, double* h, double* ess, double* logZ_in
 
 smc_status smc_resample(smc_ctx* ctx) {
     if (!ctx) return SMC_EINVAL;
+    NvtxRange nvtx("smc_resample");
     Ctx& c = ctx->c;
     if (c.stage != 2) return fail(ctx, SMC_ESTATE, "smc_resample: expected after smc_temper_step");
     API_BEGIN
     launch_resample(c);
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     c.stage = 3;
     return SMC_OK;
     API_END(ctx)
@@ -528,6 +539,7 @@ smc_status smc_resample(smc_ctx* ctx) {
 
 smc_status gm_fit(smc_ctx* ctx, double* loglik) {
     if (!ctx) return SMC_EINVAL;
+    NvtxRange nvtx("gm_fit");
     Ctx& c = ctx->c;
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "gm_fit: context not initialised");
     if (c.cfg.kernel == SMC_K_PCN || c.cfg.kernel == SMC_K_PCNL) { if (loglik) *loglik = 0.0; return SMC_OK; }
@@ -541,6 +553,7 @@ smc_status gm_fit(smc_ctx* ctx, double* loglik) {
 
 smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max) {
     if (!ctx || steps < 1) return SMC_EINVAL;
+    NvtxRange nvtx("smc_move");
     Ctx& c = ctx->c;
     if (c.stage < 1) return fail(ctx, SMC_ESTATE, "smc_move: context not initialised");
     if (!c.fitted) return fail(ctx, SMC_ESTATE, "smc_move: the pCN-GM kernels need gm_fit or smc_set_mixture first");
@@ -588,7 +601,7 @@ smc_status smc_move(smc_ctx* ctx, int steps, double* accept_rate, int* iters_max
     }
     int hacc = 0;
     check(cudaMemcpyAsync(&hacc, accn, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     const double rate = (double)hacc / ((double)c.N * steps);
     if (accept_rate) *accept_rate = rate;
     if (iters_max) *iters_max = itmax;
@@ -616,7 +629,7 @@ smc_status smc_move_host(smc_ctx* ctx, const double* X_in, const double* Phi_in,
     if (st != SMC_OK && st != SMC_ENOCONV) return st;
     if (X_out) check(cudaMemcpyAsync(X_out, c.X, (size_t)c.N * c.d * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h X");
     if (Phi_out) check(cudaMemcpyAsync(Phi_out, c.Phi, (size_t)c.N * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h Phi");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return st;
     API_END(ctx)
 }
@@ -637,7 +650,7 @@ smc_status smc_posterior_moments(smc_ctx* ctx, double* mean_kl, double* var_kl, 
         if (mean_grid) check(cudaMemcpyAsync(mean_grid, c.gridtmp, cells * 8, cudaMemcpyDeviceToHost, c.stream), "d2h");
         if (var_grid) check(cudaMemcpyAsync(var_grid, c.gridtmp + cells, cells * 8, cudaMemcpyDeviceToHost, c.stream), "d2h");
     }
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return SMC_OK;
     API_END(ctx)
 }
@@ -652,7 +665,7 @@ smc_status smc_gradient(smc_ctx* ctx, const double* d_X, int count, double* d_Ph
     API_BEGIN
     const long long nc0 = c.nonconv;
     gradient_batch(c, d_X, count, d_Phi, d_grad);
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if ((c.nonconv - nc0) * 100 > 2LL * count) return fail(ctx, SMC_ENOCONV, "more than 1% of forward or adjoint solves missed the tolerance");
     return SMC_OK;
     API_END(ctx)
@@ -667,7 +680,7 @@ smc_status smc_forward(smc_ctx* ctx, const double* d_X, int count, double* d_Phi
     API_BEGIN
     const long long nc0 = c.nonconv;
     int it = forward_solve(c, d_X, count, d_Phi, d_w);
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if (iters) *iters = it;
     if ((c.nonconv - nc0) * 100 > count) return fail(ctx, SMC_ENOCONV, "more than 1% of forward solves missed the tolerance");
     return SMC_OK;
@@ -689,7 +702,7 @@ smc_status smc_set_particles(smc_ctx* ctx, const double* X, const double* Phi, i
     check(cudaMemcpyAsync(c.X, X, (size_t)c.N * c.d * sizeof(double), kind, c.stream), "set X");
     if (Phi) check(cudaMemcpyAsync(c.Phi, Phi, (size_t)c.N * sizeof(double), kind, c.stream), "set Phi");
     else forward_solve(c, c.X, c.N, c.Phi, nullptr);
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if (c.stage < 1) c.stage = 1;
     return SMC_OK;
     API_END(ctx)
@@ -728,7 +741,7 @@ smc_status smc_set_mixture(smc_ctx* ctx, const double* w, const double* m, const
             for (int a = 0; a < c.r; ++a) cov[((size_t)j * c.r + a) * c.r + a] = lam[(size_t)j * c.r + a];
         factor_mixture(c, cov.data());
     }
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     c.fitted = true;
     return SMC_OK;
     API_END(ctx)
@@ -747,7 +760,7 @@ smc_status smc_set_mixture_cov(smc_ctx* ctx, const double* w, const double* m, c
     check(cudaMemcpyAsync(c.gw, w, c.K * sizeof(double), cudaMemcpyHostToDevice, c.stream), "w");
     check(cudaMemcpyAsync(c.gmu, m, Kr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "m");
     check(cudaMemcpyAsync(c.glam, lam.data(), Kr * sizeof(double), cudaMemcpyHostToDevice, c.stream), "lam");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     c.fitted = true;
     return SMC_OK;
     API_END(ctx)
@@ -759,7 +772,7 @@ smc_status smc_get_mixture_cov(smc_ctx* ctx, double* cov) {
     if (!c.cfg.full_cov) return fail(ctx, SMC_ESTATE, "smc_get_mixture_cov: the context was set up without cfg.full_cov = 1");
     API_BEGIN
     check(cudaMemcpyAsync(cov, c.gcov, (size_t)c.K * c.r * c.r * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "cov");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return SMC_OK;
     API_END(ctx)
 }
@@ -772,7 +785,7 @@ smc_status smc_get_mixture(smc_ctx* ctx, double* w, double* m, double* lam, int*
     if (m) check(cudaMemcpyAsync(m, c.gmu, (size_t)c.K * c.r * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "m");
     if (lam) check(cudaMemcpyAsync(lam, c.glam, (size_t)c.K * c.r * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "lam");
     if (modes) check(cudaMemcpyAsync(modes, c.S, c.r * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "S");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return SMC_OK;
     API_END(ctx)
 }
@@ -822,7 +835,7 @@ smc_status smc_save(smc_ctx* ctx, void* host_buf, size_t* bytes) {
     check(cudaMemcpyAsync(q, c.glam, (size_t)c.K * c.r * 8, cudaMemcpyDeviceToHost, c.stream), "save");
     q += (size_t)c.K * c.r;
     if (covn) check(cudaMemcpyAsync(q, c.gcov, covn * 8, cudaMemcpyDeviceToHost, c.stream), "save");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     *bytes = need;
     return SMC_OK;
     API_END(ctx)
@@ -851,7 +864,7 @@ smc_status smc_load(smc_ctx* ctx, const void* host_buf, size_t bytes) {
     check(cudaMemcpyAsync(c.glam, q, (size_t)c.K * c.r * 8, cudaMemcpyHostToDevice, c.stream), "load");
     q += (size_t)c.K * c.r;
     if (covn && h.fitted) factor_mixture(c, q);            // uploads C_j and its factors
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     c.layer = h.layer; c.stage = h.stage; c.fitted = h.fitted != 0; c.step = h.step; c.t = h.t; c.beta = h.beta;
     return SMC_OK;
     API_END(ctx)
@@ -981,6 +994,7 @@ smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batc
 
 smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
     if (!b) return SMC_EINVAL;
+    NvtxRange nvtx("smc_batch_move");
     const int count = (int)b->ctxs.size();
     for (int i = 0; i < count; ++i) {
         const Ctx& c = b->ctxs[i]->c;
@@ -1040,6 +1054,7 @@ smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
         c.pc.inner_solves += (long long)gc[i].inner_solves;
         c.pc.residuals += (long long)gc[i].residuals;
         c.pc.graph_launches += 1;
+        c.pc.host_syncs += 1;                        // the one wait after the launch
         c.pc.cells = c.n * c.n;
         c.pc.word_bytes = mixed_precision(c.cfg) ? 4 : 8;
         if (st == SMC_OK && (long long)gc[i].nonconv * 100 > solves) {

@@ -379,7 +379,7 @@ static void launch_factor(Ctx& c) {
 static void check_factor_flag(Ctx& c) {
     int bad = 0;
     check(cudaMemcpyAsync(&bad, factor_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c.stream), "factor flag");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if (bad) {
         c.fitted = false;   // the stored mixture is no longer usable
         throw InputError{"a mixture covariance is not positive definite"};
@@ -453,7 +453,7 @@ double gm_fit_device(Ctx& c) {
     k_sum<<<1, 1024, 0, c.stream>>>(N, c.lse, c.dscal + 8); ++c.pc.launches;
     double ll = 0.0;
     check(cudaMemcpyAsync(&ll, c.dscal + 8, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "ll");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     return ll;
 }
 

@@ -279,6 +279,14 @@ struct InputError { const char* what; };   // input the solver cannot take (repo
 void set_global_error(const char* msg);
 std::string& global_error();
 void check(cudaError_t e, const char* what);   // throws CudaError
+// Waits for the context's stream (counted in smc_profile::host_syncs).
+void sync_stream(Ctx& c);
+// An NVTX range named after a kernel family (set-up, solve, proposal, ...) for the
+// duration of a scope, so that profiler timelines group the library's launches.
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+};
 
 constexpr int TILE = 32;          // inner tile edge of the tiled multigrid kernels
 constexpr int MAXK = 16;          // max mixture components

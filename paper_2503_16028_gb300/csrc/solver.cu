@@ -1006,10 +1006,10 @@ static int compact_active(Ctx& c, InnerSolver<T>& s, int count, int* hcount) {
     check(cudaMemcpyAsync(h, s.nact, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "nact d2h");
     check(cudaMemcpyAsync(hcount, c.sc.count, 3 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "count d2h");
     check(cudaMemcpyAsync(err, c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "err d2h");
-    check(cudaStreamSynchronize(c.stream), "sync");
+    sync_stream(c);
     if (err[0] || err[1]) {   // cleared in stream order, so the context stays usable and no later flag is lost
         check(cudaMemsetAsync(c.dev_err, 0, 2 * sizeof(int), c.stream), "err reset");
-        check(cudaStreamSynchronize(c.stream), "sync");
+        sync_stream(c);
     }
     if (err[0]) throw CudaError{cudaErrorLaunchTimeout, "a kernel's bounded mbarrier wait timed out"};
     if (err[1] && !c.lenient)
@@ -1334,7 +1334,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
     {
         std::vector<int> ones(count, 1);
         check(cudaMemcpyAsync(sc.act_out, ones.data(), count * sizeof(int), cudaMemcpyHostToDevice, c.stream), "act init");
-        check(cudaStreamSynchronize(c.stream), "sync");
+        sync_stream(c);
     }
     k_fill_rhs<T><<<grid_for(total), 256, 0, c.stream>>>((size_t)n * n, count, R.b64, mixed ? R.bdf : nullptr, R.stride,
                                                         s.r[0]); ++c.pc.launches;
@@ -1366,7 +1366,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
         k_outer<<<sgrid, 128, 0, c.stream>>>(1, count, ntiles, sc, c.part, tol_out2, R.b2const, R.b2pp, badp); ++c.pc.launches;
         int h = 0;
         check(cudaMemcpyAsync(&h, sc.count + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
-        check(cudaStreamSynchronize(c.stream), "sync");
+        sync_stream(c);
         if (h == 0) break;
         outer_active = h;
         if (o == max_outer - 1) c.nonconv += h;
@@ -1705,14 +1705,22 @@ int forward_solve(Ctx& c, const double* X, int count, double* Phi_out, double* w
     const size_t nn = (size_t)c.n * c.n;
     for (int off = 0; off < count; off += c.B) {
         const int cnt = std::min(c.B, count - off);
-        // the mixed-precision set-up takes the field as df32 pairs (in the FP64 field's storage)
-        if (mixed_precision(c.cfg) && c.n % FX == 0 && c.n % FY == 0)
-            launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
-        else
-            launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
-        launch_setup_coeffs(c, cnt);
-        int it = solve_batch(c, cnt, shared_rhs(c), c.w64);
+        {
+            NvtxRange nvtx("synthesis and set-up");
+            // the mixed-precision set-up takes the field as df32 pairs (in the FP64 field's storage)
+            if (mixed_precision(c.cfg) && c.n % FX == 0 && c.n % FY == 0)
+                launch_synth2d_df(c, X + (size_t)off * c.d, cnt, reinterpret_cast<float2*>(c.u64));
+            else
+                launch_synth2d(c, X + (size_t)off * c.d, cnt, c.u64);
+            launch_setup_coeffs(c, cnt);
+        }
+        int it = 0;
+        {
+            NvtxRange nvtx("MG-PCG solve");
+            it = solve_batch(c, cnt, shared_rhs(c), c.w64);
+        }
         itmax = std::max(itmax, it);
+        NvtxRange nvtx("observation");
         launch_observe(c, c.w64, cnt, Phi_out + off);
         launch_mark_out_of_range(c, cnt, Phi_out + off);
         if (w_out) check(cudaMemcpyAsync(w_out + off * nn, c.w64, cnt * nn * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "w copy");

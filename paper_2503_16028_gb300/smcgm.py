@@ -41,7 +41,8 @@ class smc_profile(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_longlong), ("cg_iterations", ctypes.c_longlong), ("inner_solves", ctypes.c_longlong),
                 ("residuals", ctypes.c_longlong), ("dom_launches", ctypes.c_longlong), ("dom_particles", ctypes.c_longlong),
                 ("dom_ms", ctypes.c_double), ("dom_bytes", ctypes.c_double), ("launches", ctypes.c_longlong), ("cells", ctypes.c_int),
-                ("word_bytes", ctypes.c_int), ("graph_launches", ctypes.c_longlong)]
+                ("word_bytes", ctypes.c_int), ("graph_launches", ctypes.c_longlong),
+                ("host_syncs", ctypes.c_longlong)]
 
 
 EXPORTS = {
