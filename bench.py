@@ -42,7 +42,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "darcy256_precision"
 SMALL_WORKLOAD = "darcy64_bimodal"
-TRAFFIC_BYTES_PER_CELL = 36.03   # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tpre<2,1,4> per cell
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of the dominant kernel k_tpre<2,CG>, from one
+# capture of the current kernel on the 512-particle case (profiles/k_tpre_darcy256_n512.md), per smoother
+# face storage; None where no capture of the current kernel exists
+TRAFFIC_BYTES_PER_CELL = {"fp32": None, "bf16": None}
 METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
 UNIT = "solves/s"
 
@@ -59,7 +62,7 @@ def parse():
     ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient timing")
     ap.add_argument("--no-layers", action="store_true", help="skip the whole SMC run timed layer by layer")
     ap.add_argument("--no-small", action="store_true", help="skip the 64^2 workload (GPU and CPU oracle)")
-    ap.add_argument("--smoother", default="fp32", choices=["fp32", "bf16"],
+    ap.add_argument("--smoother", default="bf16", choices=["fp32", "bf16"],
                     help="face storage of the multigrid smoother in the headline (mixed-precision) sampler")
     ap.add_argument("--no-alt-smoother", action="store_true", help="skip the timing of the other smoother storage")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (host buffers)")
@@ -219,10 +222,11 @@ def make_sampler(wl, precision, N, smcgm):
     return s
 
 
-def time_gradient(wl, N, smcgm, torch, calls=2):
+def time_gradient(wl, N, smcgm, torch, calls=2, precision=None):
     """Phi and dPhi/dx of all N particles (a forward and an adjoint solve each, mixed precision),
     timed with CUDA events on the library's stream after one untimed call."""
-    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, gradient=1))
+    mixed = smcgm.SMC_P_FP32_REFINE if precision is None else precision
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, gradient=1, precision=mixed))
     X = torch.tensor(s.particles()[0], dtype=torch.float64, device="cuda")
     Phi = torch.empty(N, dtype=torch.float64, device="cuda")
     G = torch.empty_like(X)
@@ -268,7 +272,7 @@ def time_forward(s, torch, calls=2):
                 cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
-def time_layers(wl, N, smcgm, torch, max_layers=60, fp64=True):
+def time_layers(wl, N, smcgm, torch, max_layers=60, fp64=True, precision=None):
     """A whole SMC run of the workload (Alg. 2) to t = 1: every tempering layer reweights (ESS
     bisection), resamples, fits the mixture and makes L pCN-GM moves; each layer's smc_move of the
     mixed-precision sampler is timed with CUDA events.  Returns solves/s of the first layer's
@@ -280,7 +284,8 @@ def time_layers(wl, N, smcgm, torch, max_layers=60, fp64=True):
     step, the resampling indices, the acceptance rate and the potentials; at t = 1 the relative
     L2 error of the posterior mean and variance of the KL coefficients (the target is 1e-6), and
     the first layer at which any decision (an index or an accept) differs, if one does."""
-    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N))
+    mixed = smcgm.SMC_P_FP32_REFINE if precision is None else precision
+    s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, precision=mixed))
     s64 = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, precision=smcgm.SMC_P_FP64)) if fp64 else None
     L = wl["mcmc_steps"]
     rows, logz = [], 0.0
@@ -343,13 +348,13 @@ def time_layers(wl, N, smcgm, torch, max_layers=60, fp64=True):
     return out, (cmp if s64 is not None else None)
 
 
-def precision_agreement(s64, moves, wl, N, smcgm):
+def precision_agreement(s64, moves, wl, N, smcgm, precision=None):
     """The mixed-precision path against the FP64 path from the same state: a fresh mixed-precision
     sampler of the workload taken through the FP64 sampler's history (one tempering layer, then
     `moves` single moves with the same random streams).  Returns the largest absolute difference
     of the posterior mean and variance of the KL coefficients, the largest relative difference of
     Phi and the number of particles whose states differ."""
-    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE if precision is None else precision, N, smcgm)
     for _ in range(moves):
         s.smc_move(1, allow_noconv=True)
     X, P = s.particles()
@@ -363,14 +368,14 @@ def precision_agreement(s64, moves, wl, N, smcgm):
                 particles_differing=int(np.sum(np.any(X != X64, axis=1))), target=1e-6)
 
 
-def time_small(args, smcgm, torch, barrier):
+def time_small(args, smcgm, torch, barrier, precision=None):
     """GPU solves/s on the 64^2 workload (32^2 modes, N = 1024, K = 4), timed like the headline
     (host-driven smc_move, CUDA events), and the same moves as one CUDA graph (smc_batch of
     this one problem, --steps moves per launch, wall clock around the launch)."""
     from paper_2503_16028_gb300 import inputs
     wl = inputs.load_workload(SMALL_WORKLOAD)
     N = wl["n_particles"]
-    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE, N, smcgm)
+    s = make_sampler(wl, smcgm.SMC_P_FP32_REFINE if precision is None else precision, N, smcgm)
     ms, prof = time_moves(s, args.steps, args.warmup, torch, barrier)
     b = smcgm.Batch([s], args.steps)
     b.move(allow_noconv=True)
@@ -403,14 +408,18 @@ def autotune_small(smcgm):
                 ms_per_move=[dict(setting=c, ms=t) for c, t in timings])
 
 
-def time_batch32(smcgm, torch, steps=2):
+def time_batch32(smcgm, torch, steps=2, precision=None):
     """The batching workload: 32 independent Darcy problems (grids 64^2..512^2, 256..4096
     particles, 16..256 observations, sigma 0.002..0.02; inputs.batch_specs), each taken
     through one tempering layer and a mixture fit, then `steps` moves of all of them timed
     one after another, with a host thread per problem, and as one CUDA graph."""
     from paper_2503_16028_gb300 import batch, inputs
     specs = inputs.load_batch_workload(32)
-    samplers = batch.make_samplers(batch.batch_configs(specs))
+    cfgs = batch.batch_configs(specs)
+    if precision is not None:
+        for cfg in cfgs:
+            cfg.precision = precision
+    samplers = batch.make_samplers(cfgs)
     for sm in samplers:
         sm.smc_temper_step()
         sm.smc_resample()
@@ -428,13 +437,14 @@ def time_batch32(smcgm, torch, steps=2):
     return out
 
 
-def time_em(wl, N, smcgm, torch, calls=2):
+def time_em(wl, N, smcgm, torch, calls=2, precision=None):
     """gm_fit (the EM fit on the r leading modes, em_iters iterations) on the workload's
     resampled particles, diagonal and full covariances, each timed with CUDA events on the
     library's stream after one untimed call."""
     out = {}
     for form, full in (("diagonal", 0), ("full_covariance", 1)):
-        s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, full_cov=full))
+        s = smcgm.Sampler(smcgm.make_config(wl, n_particles=N, full_cov=full,
+                                            precision=smcgm.SMC_P_FP32_REFINE if precision is None else precision))
         s.smc_temper_step()
         s.smc_resample()
         s.gm_fit()
@@ -581,9 +591,8 @@ def run_native(args, rank, world, local):
     dom_ach = prof["dom_bytes"] / (prof["dom_ms"] / 1000.0) / 1e9 if prof["dom_ms"] > 0 else 0.0
     # DRAM bytes per cell of the dominant kernel from one ncu capture of the current kernel on
     # the 512-particle case, scaled to the average particles of a launch here
-    # (a capture of the FP32-face kernel: none for the BF16-face kernel, whose traffic is reported as null)
-    traffic = (TRAFFIC_BYTES_PER_CELL * 65536 * prof["dom_particles"] / max(1, prof["dom_launches"])
-               if args.smoother == "fp32" else None)
+    tb = TRAFFIC_BYTES_PER_CELL.get(args.smoother)
+    traffic = tb * 65536 * prof["dom_particles"] / max(1, prof["dom_launches"]) if tb else None
     roof = dict(bound="hbm", achieved=dom_ach, peak=hbm_peak, unit="GB/s", frac=dom_ach / hbm_peak, traffic=traffic,
                 algorithmic_bytes_per_launch=prof["dom_bytes"] / max(1, prof["dom_launches"]),
                 kernel="k_tpre<2,CG> (finest level, CG update + pre-smoothing + restriction, TMA-staged; %s smoother faces)"
@@ -624,20 +633,20 @@ def run_native(args, rank, world, local):
         fp64 = dict(value=whole_job_rate(N * st64, world, ms64), ms_per_step=ms64 / st64,
                     cg_per_solve=prof64["cg_iterations"] / max(1, prof64["solves"]),
                     dominant_kernel_gbs=prof64["dom_bytes"] / (prof64["dom_ms"] / 1000.0) / 1e9 if prof64["dom_ms"] else None)
-        agree = precision_agreement(s64, 1 + st64, wl, N, smcgm)
+        agree = precision_agreement(s64, 1 + st64, wl, N, smcgm, precision=prec_of[args.smoother])
         s64.close()
-    em = None if args.no_em else time_em(wl, N, smcgm, torch)
+    em = None if args.no_em else time_em(wl, N, smcgm, torch, precision=prec_of[args.smoother])
     grad = None
     if not args.no_gradient:
-        grad = time_gradient(wl, N, smcgm, torch)
+        grad = time_gradient(wl, N, smcgm, torch, precision=prec_of[args.smoother])
     layers = posterior = None
     if not args.no_layers:
-        layers, posterior = time_layers(wl, N, smcgm, torch, fp64=not args.no_fp64)
-    batch32 = None if args.no_batch else time_batch32(smcgm, torch)
+        layers, posterior = time_layers(wl, N, smcgm, torch, fp64=not args.no_fp64, precision=prec_of[args.smoother])
+    batch32 = None if args.no_batch else time_batch32(smcgm, torch, precision=prec_of[args.smoother])
     tuned = None if args.no_autotune else autotune_small(smcgm)
     small = None
     if not args.no_small:
-        small = time_small(args, smcgm, torch, barrier)
+        small = time_small(args, smcgm, torch, barrier, precision=prec_of[args.smoother])
         small["cpu_oracle"] = cpu_small
     if rank != 0:
         return

@@ -108,7 +108,7 @@ static void plan_inner(Planner& P, InnerSolver<T>& s, int n, int B, int coarse_t
         }
         L.e = P.take<T>(cells);
         if (l > 0) { L.r = P.take<T>(cells); L.e2 = P.take<T>(cells); }
-        if (bf16_faces && l < s.ntile_levels) { L.Kwb = P.take<__nv_bfloat16>(cells); L.Ksb = P.take<__nv_bfloat16>(cells); }
+        if (bf16_faces && l == 0) { L.Kwb = P.take<__nv_bfloat16>(cells); L.Ksb = P.take<__nv_bfloat16>(cells); }
     }
     s.list = P.take<int>(B); s.nact = P.take<int>(4);
     s.r[0] = P.take<T>(nn); s.r[1] = P.take<T>(nn);

@@ -47,6 +47,14 @@ __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_
     return false;
 }
 
+// Asynchronous 8-byte copy global -> shared (completion: cp_async_wait_all by the same thread).
+__device__ inline void cp_async8(void* dst_smem, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n\tcp.async.commit_group;" ::"r"(smem_u32(dst_smem)),
+                 "l"(reinterpret_cast<uint64_t>(src))
+                 : "memory");
+}
+__device__ inline void cp_async_wait_all_groups() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // 3-D tiled load (x innermost) of one box into shared memory, completing on `bar`.
 __device__ inline void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
     asm volatile(

@@ -300,13 +300,13 @@ struct NoHook {
 // and |r'|^2.
 template <typename T, int H, bool CG, class Src, class Hook = NoHook>
 __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
-                                 Hook loaded = Hook()) {
+                                 Hook loaded = Hook(), const double* alpha_src = nullptr) {
     using G = WGeo<T, H>;
     constexpr int NU = H / 2;
     const int n = A.a.n;
     const size_t base = (size_t)p * n * n;
     zero_border<T, G>(se, lane);
-    const T al = CG ? (T)A.alpha[p] : T(0);
+    const T al = CG ? (T)(alpha_src ? *alpha_src : A.alpha[p]) : T(0);   // alpha_src: a copy fetched ahead
     T* xg = A.x + base;
     T* routg = A.rout + base;
     WQuad<T> Q[G::SLOTS];

@@ -15,7 +15,7 @@
 // x = 8 tx - 4, y = 8 ty - H/2 on the next coarser grid.  With the BF16
 // smoother the interior-face boxes hold 2-byte values; a box must start on a
 // 16-byte boundary, so they start at x = 16 tx - 8 (a multiple of 8 values)
-// and span 32 values (64 bytes) per row.
+// and span 40 values (80 bytes) per row.
 #pragma once
 #include "tma.cuh"
 #include "wtiles.cuh"
@@ -35,8 +35,13 @@ struct TGeo {
     static constexpr int BX = round_up(WT + H + 4, 4);       // r, q, e: columns 16 tx - 4 .. 16 tx + 15 + H
     static constexpr int FXO = FB == 4 ? 4 : 8;              // face boxes start at column 16 tx - FXO
     static constexpr int FA = 16 / FB;                       // values per 16 bytes
-    static constexpr int KWE = round_up(WT + H + 1 + FXO, FA);   // west faces: columns 16 tx - FXO .. 16 tx + 16 + H
-    static constexpr int KSE = round_up(WT + H + FXO, FA);       // south faces: to column 16 tx + 15 + H
+    // west faces: columns 16 tx - FXO .. 16 tx + 16 + H; south faces: to column 16 tx + 15 + H.
+    // BF16 rows are 40 values (80 bytes): the four quad rows a warp reads at once lie two
+    // box rows apart, 160 bytes = 40 banks = 8 mod 32, so their 8-bank spans start on banks
+    // 0, 8, 16, 24 and never share one (32-value rows would put all four on the same banks);
+    // the extra columns are the next tile's, served by L2.
+    static constexpr int KWE = FB == 4 ? round_up(WT + H + 1 + FXO, FA) : 40;
+    static constexpr int KSE = FB == 4 ? round_up(WT + H + FXO, FA) : 40;
     static constexpr int CX = 16;                            // parent box: columns 8 tx - 4 .. 8 tx + 11
     static constexpr int CY = RW / 2;                        // parent box rows
     static constexpr int KW_OFF = 0;                                          // every box 128-byte aligned
@@ -59,6 +64,10 @@ template <int H, int STAGE>
 struct TLayout {
     static constexpr int SE_OFF = STAGE;
     static constexpr int BAR_OFF = SE_OFF + round_up(WGeo<float, H>::EN, 32);
+    // after the mbarrier (8 bytes): the next item's particle index (int) and its CG step
+    // alpha (8-byte aligned), written by the lane that starts the item's copies
+    static constexpr int NEXT_P_OFF = BAR_OFF + 2;
+    static constexpr int NEXT_ALPHA_OFF = BAR_OFF + 4;
     static constexpr int WARP = BAR_OFF + 32;                          // floats per warp
     static constexpr size_t block_bytes() { return (size_t)TW_WARPS * WARP * 4 + 128; }
 };
@@ -190,6 +199,8 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A,
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + L::BAR_OFF);
     const int lane = threadIdx.x & 31;
     const int n = A.a.n;
+    int* next_p = reinterpret_cast<int*>(wb + L::NEXT_P_OFF);
+    double* next_alpha = reinterpret_cast<double*>(wb + L::NEXT_ALPHA_OFF);
     auto issue = [&](int item) {
         int p, tile, tx, ty;
         item_decode(A.a, item, p, tile, tx, ty);
@@ -202,16 +213,24 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A,
             tma_load_3d(wb + G::V_OFF, &m_q, x0, y0, p, bar);
             tma_load_3d(wb + G::X_OFF, &m_x, tx * WT, ty * WT, p, bar);
             tma_load_3d(wb + G::P_OFF, &m_p, tx * WT, ty * WT, p, bar);
+            cp_async8(next_alpha, A.alpha + p);       // the item's alpha, in flight with its tiles
         }
+        *next_p = p;
     };
     auto work = [&](int item, int ln, auto refill) {
-        int p, tile, tx, ty;
-        item_decode(A.a, item, p, tile, tx, ty);
+        // the particle index and alpha were fetched when the item's copies started (its issue)
+        if (CG && ln == 0) cp_async_wait_all_groups();
+        __syncwarp();
+        const int p = *next_p;
+        const double al = CG ? *next_alpha : 0.0;
+        const int tile = item % A.a.ntiles;
+        const int tpr = A.a.n / WT;
+        const int tx = tile % tpr, ty = tile / tpr;
         const float* st = wb;
         StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
                           st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, st + G::P_OFF,
                           A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT, 0, 0};
-        wpre_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill);
+        wpre_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill, CG ? &al : nullptr);
     };
     warp_pipeline(A.a, bar, lane, issue, work);
 }
@@ -231,6 +250,7 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* wb = reinterpret_cast<float*>(align128(smem_raw)) + (threadIdx.x >> 5) * L::WARP;
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + L::BAR_OFF);
+    int* next_p = reinterpret_cast<int*>(wb + L::NEXT_P_OFF);
     const int lane = threadIdx.x & 31;
     const int n = A.a.n;
     auto issue = [&](int item) {
@@ -243,10 +263,14 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
         tma_load_3d(wb + G::R_OFF, &m_r, x0, y0, p, bar);
         tma_load_3d(wb + G::V_OFF, &m_e, x0, y0, p, bar);
         tma_load_3d(wb + G::X_OFF, &m_ec, tx * (WT / 2) - 4, ty * (WT / 2) - H / 2, p, bar);
+        *next_p = p;
     };
     auto work = [&](int item, int ln, auto refill) {
-        int p, tile, tx, ty;
-        item_decode(A.a, item, p, tile, tx, ty);
+        __syncwarp();
+        const int p = *next_p;                       // written when the item's copies started
+        const int tile = item % A.a.ntiles;
+        const int tpr = A.a.n / WT;
+        const int tx = tile % tpr, ty = tile / tpr;
         const float* st = wb;
         StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
                           st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, nullptr,

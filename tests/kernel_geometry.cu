@@ -131,12 +131,19 @@ int main() {
     check_staged<2, false, 4, 4>();
     check_staged<4, true, 2, 4>();
     check_staged<4, false, 2, 4>();
-    // BF16 smoother faces: boxes from 16 tx - 8, 32 values (64 bytes) per row
+    // BF16 smoother faces: boxes from 16 tx - 8, 40 values (80 bytes) per row
     check_staged<2, true, 4, 2>();
     check_staged<2, false, 4, 2>();
     check_staged<4, true, 2, 2>();
     check_staged<4, false, 2, 2>();
-    CHECK((TGeo<2, 2>::FXO == 8 && TGeo<2, 2>::KWE == 32 && TGeo<2, 2>::KSE == 32));
+    CHECK((TGeo<2, 2>::FXO == 8 && TGeo<2, 2>::KWE == 40 && TGeo<2, 2>::KSE == 40));
+    // the four quad rows of a warp's tile slot (qy = 0..3, cell rows two apart) read 8 lanes x
+    // 4 bytes each: their 8-bank spans, starting at 2 qy rows x 80 bytes, are disjoint
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b) {
+            const int ba = (2 * a * TGeo<2, 2>::KWE * 2 / 4) % 32, bb = (2 * b * TGeo<2, 2>::KWE * 2 / 4) % 32;
+            CHECK(ba % 8 == 0 && bb % 8 == 0 && ba != bb);
+        }
     // the cosine-transform block fits up to the largest accepted 2D grid and not beyond it;
     // three blocks share an SM at 256^2
     CHECK(fct_smem_bytes(MAX_N2D) <= BLOCK_MAX);
