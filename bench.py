@@ -23,7 +23,7 @@ run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
 the GPU (host-driven and as one CUDA graph) and on the CPU oracle, the 32-problem
 batching workload (one after another, a host thread each, one CUDA graph), the SM
 clocks sampled during the timed region and the CPU oracle baseline.
---smoother bf16 times the BF16-smoother mode as the headline; --no-fp64, --no-alt-smoother,
+--smoother fp32 times the FP32-smoother mode as the headline; --no-fp64, --no-alt-smoother, --no-graph,
 --no-e2e, --no-forward, --no-em, --no-batch, --no-autotune, --no-gradient, --no-layers, --no-small and
 --no-cpu leave legs out.
 """
@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-alt-smoother", action="store_true", help="skip the timing of the other smoother storage")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (host buffers)")
     ap.add_argument("--no-forward", action="store_true", help="skip the solver-only leg")
+    ap.add_argument("--no-graph", action="store_true", help="skip the headline moves as one CUDA graph")
     ap.add_argument("--no-em", action="store_true", help="skip the EM-fit timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-problem batching workload")
     ap.add_argument("--no-autotune", action="store_true", help="skip the solver-setting autotuner on the 64^2 workload")
@@ -461,6 +462,27 @@ def time_em(wl, N, smcgm, torch, calls=2, precision=None):
     return out
 
 
+def time_graph(s, N, steps, torch, reps=2):
+    """The same moves as the headline as one CUDA graph (smc_batch of this one problem, `steps`
+    moves per launch: no host wait inside the move), wall clock around the launches after one
+    untimed launch."""
+    from paper_2503_16028_gb300 import smcgm
+    b = smcgm.Batch([s], steps)
+    b.move(allow_noconv=True)
+    s.smc_profile_query(reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.move(allow_noconv=True)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    prof = s.smc_profile_query(reset=True)
+    b.close()
+    return dict(value=N * steps / sec, unit=UNIT, ms_per_move=1000.0 * sec / steps, moves_per_launch=steps,
+                host_syncs_per_move=prof["host_syncs"] / (reps * steps),
+                cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
+
+
 def time_e2e(s, N, d, steps, torch, barrier, world):
     """End to end through the C ABI (smc_move_host): every step copies the particles and potentials
     from pinned host buffers to the device, moves them and copies them back, inside the timed region
@@ -607,6 +629,7 @@ def run_native(args, rank, world, local):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None if args.no_e2e else time_e2e(s, N, d, args.steps, torch, barrier, world)
     forward = None if args.no_forward else time_forward(s, torch)
+    graph = None if args.no_graph else time_graph(s, N, args.steps, torch)
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -663,7 +686,7 @@ def run_native(args, rank, world, local):
                 iterations=iters, fp64=fp64,
                 speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, posterior_error_vs_fp64=posterior,
                 fp64_agreement=agree,
-                solver_only=forward, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
+                solver_only=forward, graph=graph, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
                 cpu_baseline=cpu,
                 adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small, batch_workload=batch32,
                 autotune=tuned)
