@@ -961,10 +961,12 @@ static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, c
     k_tpost<H, CG, MINB, FB><<<persistent_grid(A.a.total, per_sm, c.sm_count), 32 * TW_WARPS, tpost_smem<H, FB>(), c.stream>>>(
         A, mkw, mks, mr, M.e[level], M.ec[level]); ++c.pc.launches;
 }
+// One sweep (H = 2): 5 blocks of 4 warps per SM (<= 96 registers, no spills; the staging buffers fit);
+// two sweeps: 2 blocks.
 template <int H, bool CG>
 static void launch_tpost(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* r, float* eout) {
-    if (s.lv[level].Kwb) launch_tpost_b<H, CG, H == 2 ? 4 : 2, 2>(c, s, level, nact, mr, r, eout);
-    else launch_tpost_b<H, CG, H == 2 ? 4 : 2, 4>(c, s, level, nact, mr, r, eout);
+    if (s.lv[level].Kwb) launch_tpost_b<H, CG, H == 2 ? 5 : 2, 2>(c, s, level, nact, mr, r, eout);
+    else launch_tpost_b<H, CG, H == 2 ? 5 : 2, 4>(c, s, level, nact, mr, r, eout);
 }
 
 template <typename T, int NU>

@@ -63,7 +63,7 @@ void check_quads() {
     CHECK(G::QR <= G::QS);
 }
 
-template <int H, bool CG, int MINB, int FB>
+template <int H, bool CG, int MINB, int FB, int POST_MINB = MINB>
 void check_staged() {
     using G = TGeo<H, FB>;
     CHECK(H <= 4);                                  // r, q, e boxes start 4 columns left of the tile
@@ -121,19 +121,19 @@ void check_staged() {
     constexpr size_t post = tpost_smem<H, FB>();
     CHECK(pre <= BLOCK_MAX && post <= BLOCK_MAX);
     CHECK(MINB * (pre + BLOCK_RESERVED) <= SM_SHARED);
-    CHECK(MINB * (post + BLOCK_RESERVED) <= SM_SHARED);
+    CHECK(POST_MINB * (post + BLOCK_RESERVED) <= SM_SHARED);
 }
 
 int main() {
     check_quads<2>();
     check_quads<4>();
-    check_staged<2, true, 4, 4>();
-    check_staged<2, false, 4, 4>();
+    check_staged<2, true, 4, 4, 5>();       // post-smoothing: 5 blocks of 4 warps per SM
+    check_staged<2, false, 4, 4, 5>();
     check_staged<4, true, 2, 4>();
     check_staged<4, false, 2, 4>();
     // BF16 smoother faces: boxes from 16 tx - 8, 40 values (80 bytes) per row
-    check_staged<2, true, 4, 2>();
-    check_staged<2, false, 4, 2>();
+    check_staged<2, true, 4, 2, 5>();
+    check_staged<2, false, 4, 2, 5>();
     check_staged<4, true, 2, 2>();
     check_staged<4, false, 2, 2>();
     CHECK((TGeo<2, 2>::FXO == 8 && TGeo<2, 2>::KWE == 40 && TGeo<2, 2>::KSE == 40));
