@@ -128,9 +128,10 @@ typedef struct smc_config {
                            0 = the default (2); 1 = 32 x 32 tiles, one thread block each;
                            2 = 16 x 16 tiles, one warp each, the finest level's inputs staged
                            by TMA (FP32; the FP64 solver uses 3); 3 = 16 x 16 tiles, one warp
-                           each, loading from global memory.  Same results to the solver
-                           tolerance; a speed choice (batch.autotune times them).  smc_batch_*
-                           needs 0, 2 or 3 */
+                           each, loading from global memory; 4 = the finest level as 2, the
+                           coarser tiled levels as 1.  Same results to the solver tolerance; a
+                           speed choice (batch.autotune times them).  smc_batch_* needs 0, 2,
+                           3 or 4 */
 } smc_config;
 
 /* Fills cfg with the defaults (2D, n = 64, 32 x 32 modes, alpha = 0.02, ...). */

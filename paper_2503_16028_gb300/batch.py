@@ -98,6 +98,7 @@ DEFAULT_CANDIDATES = (
     dict(),                                            # the library defaults
     dict(tile_kernel=1),                               # 32 x 32 block tiles
     dict(tile_kernel=3),                               # 16 x 16 warp tiles, global loads
+    dict(tile_kernel=4),                               # warp tiles on the finest level, block tiles below
     dict(smooth_sweeps=1),
     dict(fine_sweeps=2),
     dict(tol_inner=2e-4),

@@ -75,7 +75,7 @@ static const char* validate(const smc_config& c) {
     if (c.solve_batch < 0) return "solve_batch must be >= 0";
     if (c.gradient != 0 && c.gradient != 1) return "gradient must be 0 or 1";
     if (c.full_cov != 0 && c.full_cov != 1) return "full_cov must be 0 or 1";
-    if (c.tile_kernel < 0 || c.tile_kernel > 3) return "tile_kernel must be 0, 1, 2 or 3";
+    if (c.tile_kernel < 0 || c.tile_kernel > 4) return "tile_kernel must be 0, 1, 2, 3 or 4";
     if (c.full_cov && c.kernel != SMC_K_PCN_GM && c.kernel != SMC_K_GM_INDEP)
         return "full_cov needs the pCN-GM or the mixture independence kernel";
     if (c.full_cov && !(c.var_floor > 0)) return "full_cov needs var_floor > 0 (the covariance ridge)";
@@ -917,7 +917,7 @@ smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batc
         }
         if (!device_visible(c.X)) { set_global_error("smc_batch_create: a context lives on another device"); return SMC_EINVAL; }
         if (c.cfg.tile_kernel == 1) {
-            set_global_error("smc_batch_create: graph capture needs the warp-tile kernels (tile_kernel 0, 2 or 3)");
+            set_global_error("smc_batch_create: graph capture needs the warp-tile kernels on the finest level (tile_kernel 0, 2, 3 or 4)");
             return SMC_EINVAL;
         }
     }

@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(Own<TILE + 4 * NU>::THREADS) k_pre(
         int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn,
         const T* __restrict__ rin, T* __restrict__ rout, T* __restrict__ e_out, T* __restrict__ rc, const T* __restrict__ q,
         T* __restrict__ x, const T* __restrict__ p, const double* __restrict__ alpha, double* __restrict__ part_rr,
-        const int* __restrict__ active, int cg, int want_rr) {
+        const int* __restrict__ active, int cg, int want_rr, const int* __restrict__ nact_dev = nullptr) {
+    if (nact_dev && (int)blockIdx.y >= *nact_dev) return;   // a launch sized before the active count was known
     constexpr int H = 2 * NU;
     constexpr int R = TILE + 2 * H;
     using O = Own<R>;
@@ -316,7 +317,8 @@ template <typename T, int NU>
 __global__ void __launch_bounds__(Own<TILE + 4 * NU>::THREADS) k_post(
         int n, const T* __restrict__ Kw, const T* __restrict__ Ks, const T* __restrict__ E, const T* __restrict__ Nn,
         const T* __restrict__ r, const T* __restrict__ e_in, const T* __restrict__ ec, T cc, T* __restrict__ e_out,
-        double* __restrict__ part_rz, const int* __restrict__ active, int cg) {
+        double* __restrict__ part_rz, const int* __restrict__ active, int cg, const int* __restrict__ nact_dev = nullptr) {
+    if (nact_dev && (int)blockIdx.y >= *nact_dev) return;
     constexpr int H = 2 * NU;
     constexpr int R = TILE + 2 * H;
     using O = Own<R>;
@@ -969,33 +971,28 @@ static void launch_tpost(Ctx& c, InnerSolver<float>& s, int level, int nact, con
     else launch_tpost_b<H, CG, H == 2 ? 5 : 2, 4>(c, s, level, nact, mr, r, eout);
 }
 
+template <typename T>
+static void launch_coarse(Ctx& c, InnerSolver<T>& s, int nact);
+
+// The tiled levels below the finest with one block per 32 x 32 tile (NU sweeps), then the
+// coarse V-cycle, then back up.
 template <typename T, int NU>
 static void run_vcycle_lower(Ctx& c, InnerSolver<T>& s, int nact) {
     const T cc = (T)c.cfg.coarse_scale;
     constexpr int TPB = Own<TILE + 4 * NU>::THREADS;
+    const int* nd = c.graph ? s.nact : nullptr;
     for (int l = 1; l < s.ntile_levels; ++l) {
         LevelArrays<T>& L = s.lv[l];
         dim3 grid((L.n / TILE) * (L.n / TILE), nact);
         k_pre<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, nullptr, L.e, s.lv[l + 1].r, nullptr, nullptr,
-                                                 nullptr, nullptr, nullptr, s.list, 0, 0); ++c.pc.launches;
+                                                 nullptr, nullptr, nullptr, s.list, 0, 0, nd); ++c.pc.launches;
     }
-    {
-        CoarseLevelPtrs<T> P{};
-        const int top = s.ntile_levels;
-        P.ntop = s.lv[top].n;
-        P.nlev = s.nlev - top;
-        for (int l = 0; l < P.nlev; ++l) {
-            P.Kw[l] = s.lv[top + l].Kw; P.Ks[l] = s.lv[top + l].Ks; P.E[l] = s.lv[top + l].E; P.Nn[l] = s.lv[top + l].Nn;
-        }
-        P.rtop = s.lv[top].r;
-        P.etop = s.lv[top].e2;
-        const size_t cs = coarse_smem_bytes<T>(P.ntop, P.nlev);
-        k_coarse<T, NU><<<nact, 256, cs, c.stream>>>(P, cc, s.list); ++c.pc.launches;
-    }
+    launch_coarse<T>(c, s, nact);
     for (int l = s.ntile_levels - 1; l >= 1; --l) {
         LevelArrays<T>& L = s.lv[l];
         dim3 grid((L.n / TILE) * (L.n / TILE), nact);
-        k_post<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr, s.list, 0); ++c.pc.launches;
+        k_post<T, NU><<<grid, TPB, 0, c.stream>>>(L.n, L.Kw, L.Ks, L.E, L.Nn, L.r, L.e, s.lv[l + 1].e2, cc, L.e2, nullptr, s.list, 0,
+                                                  nd); ++c.pc.launches;
     }
 }
 
@@ -1113,7 +1110,7 @@ static void staged_lower(Ctx&, InnerSolver<double>&, int) {}
 // warp per 16 x 16 tile loading from global memory.
 static int tile_path(const Ctx& c, bool fp32) {
     const int k = c.cfg.tile_kernel;
-    const int path = k == 1 ? 0 : k == 3 ? 2 : 1;
+    const int path = k == 1 ? 0 : k == 3 ? 2 : 1;   // 4: the default's finest level (the coarser levels: Passes)
     if (path == 1 && !fp32) return 2;
     if (path == 1 && c.n % WT) return 2;
     return path;
@@ -1125,10 +1122,12 @@ struct Passes {
     Ctx& c;
     InnerSolver<T>& s;
     int path, n, ntiles;
+    bool lower_blocks;        // the coarser tiled levels with one block per 32 x 32 tile
     Passes(Ctx& cc, InnerSolver<T>& ss) : c(cc), s(ss) {
         path = tile_path(cc, sizeof(T) == 4);
         n = ss.lv[0].n;
         ntiles = path == 0 ? (n / TILE) * (n / TILE) : wtiles(n);
+        lower_blocks = path == 0 || cc.cfg.tile_kernel == 4;
     }
     // finest-level pre-smoothing (cg: with the CG update from r[cur] into r[1-cur])
     void pre(int nact, int cur, int pc, int cg) {
@@ -1146,7 +1145,10 @@ struct Passes {
         }
     }
     void lower(int nact) {
-        if (path == 2) {
+        if (lower_blocks) {
+            if (c.cfg.smooth_sweeps == 2) run_vcycle_lower<T, 2>(c, s, nact);
+            else run_vcycle_lower<T, 1>(c, s, nact);
+        } else if (path == 2) {
             for (int l = 1; l < s.ntile_levels; ++l) {
                 if (level_halo(c, l) == 4) launch_wpre<T, 4>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
                 else launch_wpre<T, 2>(c, s, l, nact, s.lv[l].r, nullptr, 0, 0, nullptr);
@@ -1156,10 +1158,8 @@ struct Passes {
                 if (level_halo(c, l) == 4) launch_wpost<T, 4>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
                 else launch_wpost<T, 2>(c, s, l, nact, s.lv[l].r, s.lv[l].e2, 0);
             }
-        } else if (path == 1) {
-            staged_lower(c, s, nact);
         } else {
-            run_vcycle_lower<T, 1>(c, s, nact);
+            staged_lower(c, s, nact);
         }
     }
     void post(int nact, int cur) {

@@ -97,10 +97,11 @@ def test_mixed_batch_of_uneven_problems_equals_host_loops():
         g.close()
 
 
-def test_metric_grid_in_graph_equals_host_loop():
+@pytest.mark.parametrize("tile_kernel", [0, 4])
+def test_metric_grid_in_graph_equals_host_loop(tile_kernel):
     """256^2 (the TMA-staged finest level and three tiled levels), 64 particles: 7 launch-size
-    buckets per stage."""
-    host, graph = _twins("darcy256_precision", n_particles=64, n_components=2)
+    buckets per stage; the coarser tiled levels as warp tiles (0) or as 32 x 32 block tiles (4)."""
+    host, graph = _twins("darcy256_precision", n_particles=64, n_components=2, tile_kernel=tile_kernel)
     b = smcgm.Batch([graph], steps=2)
     acc_h, _ = host.smc_move(2)
     acc_g = b.move()

@@ -53,7 +53,7 @@ def test_init_draws_and_potentials_64(precision):
     s.close()
 
 
-@pytest.mark.parametrize("tile_kernel", [0, 1, 3])
+@pytest.mark.parametrize("tile_kernel", [0, 1, 3, 4])
 @pytest.mark.parametrize("precision", [smcgm.SMC_P_FP64, smcgm.SMC_P_FP32_REFINE, smcgm.SMC_P_BF16SMOOTH_REFINE])
 def test_forward_solution_matches_exact_solve(precision, tile_kernel):
     """Every stencil-tile kernel family (16 x 16 warp tiles with TMA staging, 32 x 32 block
@@ -97,7 +97,7 @@ def _random_mixture(s, rng, lam0):
 
 @pytest.mark.parametrize("precision,tile_kernel", [(smcgm.SMC_P_FP64, 0), (smcgm.SMC_P_FP32_REFINE, 0),
                                                     (smcgm.SMC_P_BF16SMOOTH_REFINE, 0), (smcgm.SMC_P_FP32_REFINE, 1),
-                                                    (smcgm.SMC_P_FP32_REFINE, 3)])
+                                                    (smcgm.SMC_P_FP32_REFINE, 3), (smcgm.SMC_P_BF16SMOOTH_REFINE, 4)])
 def test_move_step_matches_oracle(precision, tile_kernel):
     N = 24
     wl, cfg, s = _sampler("darcy64_bimodal", n_particles=N, n_components=4, precision=precision, tile_kernel=tile_kernel)
