@@ -498,12 +498,16 @@ def time_e2e(s, N, d, steps, torch, barrier, world):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    step_ms = []
     for _ in range(steps):
-        s.smc_move_host(Xh, Ph, Xo, Po)
+        ts = time.perf_counter()
+        s.smc_move_host(Xh, Ph, Xo, Po)          # returns after its device-to-host copies
+        step_ms.append((time.perf_counter() - ts) * 1000.0)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
     return dict(value=whole_job_rate(N * steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
-                d2h_bytes_per_step=N * d * 8 + N * 8, steps=steps)
+                d2h_bytes_per_step=N * d * 8 + N * 8, steps=steps,
+                step_ms=dict(min=min(step_ms), median=statistics.median(step_ms), max=max(step_ms)))
 
 
 def time_moves(s, steps, warmup, torch, barrier):

@@ -848,6 +848,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 static inline int wtiles(int n) { return (n / WT) * (n / WT); }
 
+// log2 of the warp tiles per row of an n x n level (n / 16, a power of two).
+static int lg_tiles_per_row(int n) {
+    int l = 0;
+    while ((WT << l) < n) ++l;
+    if ((WT << l) != n) throw CudaError{cudaErrorInvalidValue, "warp-tile level size is not 16 times a power of two"};
+    return l;
+}
+
 // 3-D map over a particle-major [B][n][n] array of FP32 (es = 4) or BF16 (es = 2)
 // values, box bx x by x 1 (x innermost).
 static CUtensorMap make_map_es(const void* base, int es_bytes, int n, int B, int bx, int by) {
@@ -929,7 +937,7 @@ static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, co
     LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
     WPreArgs<float> A{};
-    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.lg_tpr = lg_tiles_per_row(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
     A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = s.p[pc];
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
@@ -954,7 +962,7 @@ static void launch_tpost_b(Ctx& c, InnerSolver<float>& s, int level, int nact, c
     LevelArrays<float>& L = s.lv[level];
     TmaMaps& M = *s.maps;
     WPostArgs<float> A{};
-    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.lg_tpr = lg_tiles_per_row(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list; A.a.err = c.dev_err;
     A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (float)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = CG ? 1 : 0;
@@ -1024,7 +1032,7 @@ template <typename T, int H>
 static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T* rin, T* rout, int cg, int want_rr, const T* p) {
     LevelArrays<T>& L = s.lv[level];
     WPreArgs<T> A{};
-    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.lg_tpr = lg_tiles_per_row(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.rin = rin; A.q = s.q; A.p = p;
     A.rout = rout; A.e_out = L.e; A.rc = s.lv[level + 1].r; A.x = s.x; A.alpha = c.sc.alpha; A.part_rr = c.part.rr;
@@ -1047,7 +1055,7 @@ template <typename T, int H>
 static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T* r, T* eout, int cg) {
     LevelArrays<T>& L = s.lv[level];
     WPostArgs<T> A{};
-    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
+    A.a.n = L.n; A.a.ntiles = wtiles(L.n); A.a.lg_tpr = lg_tiles_per_row(L.n); A.a.total = nact * A.a.ntiles; A.a.list = s.list;
     A.a.nact = c.graph ? s.nact : nullptr;
     A.Kw = L.Kw; A.Ks = L.Ks; A.E = L.E; A.Nn = L.Nn; A.r = r; A.e_in = L.e; A.ec = s.lv[level + 1].e2;
     A.cc = (T)c.cfg.coarse_scale; A.e_out = eout; A.part_rz = c.part.rz; A.cg = cg; A.Kwb = L.Kwb; A.Ksb = L.Ksb;
@@ -1179,7 +1187,7 @@ struct Passes {
         LevelArrays<T>& L0 = s.lv[0];
         if (path != 0) {
             WApplyArgs<T> A{};
-            A.a.n = n; A.a.ntiles = ntiles; A.a.total = nact * ntiles; A.a.list = s.list; A.a.err = c.dev_err;
+            A.a.n = n; A.a.ntiles = ntiles; A.a.lg_tpr = lg_tiles_per_row(n); A.a.total = nact * ntiles; A.a.list = s.list; A.a.err = c.dev_err;
             A.a.nact = c.graph ? s.nact : nullptr;
             A.Kw = L0.Kw; A.Ks = L0.Ks; A.E = L0.E; A.Nn = L0.Nn; A.z = s.z; A.pin = s.p[pc];
             A.pout = s.p[1 - pc]; A.q = s.q; A.betac = c.sc.betac; A.part_pq = c.part.pq; A.first = first;

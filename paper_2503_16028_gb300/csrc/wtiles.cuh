@@ -90,6 +90,7 @@ __host__ __device__ inline void quad_pos(int qi, int& qx, int& qy) {
 
 struct WArgs {
     int n, ntiles, total;   // total = active particles x tiles (when nact is null)
+    int lg_tpr;             // log2 of the tiles per row, n / 16 (n is a power of two)
     const int* list;        // active particle indices
     int* err;               // set to 1 by a staged kernel whose bounded wait timed out
     const int* nact;        // device count of active particles: total = *nact x ntiles
@@ -98,6 +99,17 @@ struct WArgs {
 // Work items of a launch: the active particles' tiles, counted on the device when the
 // launch was sized before the count was known (a launch inside a CUDA graph).
 __device__ inline int work_total(const WArgs& a) { return a.nact ? *a.nact * a.ntiles : a.total; }
+
+// Work item -> index in the active list, tile of the particle and its coordinates.
+// The tiles per row and per particle are powers of two, so these are shifts and
+// masks rather than divisions by run-time values.
+__device__ inline void item_tile(const WArgs& a, int item, int& pi, int& tile, int& tx, int& ty) {
+    const int lt = a.lg_tpr;
+    pi = item >> (2 * lt);
+    tile = item & ((1 << (2 * lt)) - 1);
+    tx = tile & ((1 << lt) - 1);
+    ty = tile >> lt;
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
@@ -203,7 +215,8 @@ __device__ __forceinline__ constexpr int qoff(int k, int dir) {
 // Zeroes the border quads of the correction planes that the region's edge
 // cells read (west border: planes 1, 3; east: 0, 2; south: 2, 3; north: 0, 1).
 // Interior quads are always written before they are read, or belong to quads
-// outside the grid, which their owners zero.
+// outside the grid, which their owners zero; no item writes the border, so a
+// warp that keeps its array across items zeroes it once.
 template <typename T, class G>
 __device__ inline void zero_border(T* se, int lane) {
     constexpr int QW = G::QW, QS = G::QS;
@@ -297,7 +310,7 @@ struct NoHook {
 // Pre-smoothing of one work item (particle p, tile (tx, ty)) by one warp:
 // nu = H/2 sweeps (red, black) from zero, residual, restriction; with CG
 // (finest level, a compile-time switch) first r' = r - alpha q, x += alpha p,
-// and |r'|^2.
+// and |r'|^2.  The border of se is zero on entry (zero_border).
 template <typename T, int H, bool CG, class Src, class Hook = NoHook>
 __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
                                  Hook loaded = Hook(), const double* alpha_src = nullptr) {
@@ -305,7 +318,6 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     constexpr int NU = H / 2;
     const int n = A.a.n;
     const size_t base = (size_t)p * n * n;
-    zero_border<T, G>(se, lane);
     const T al = CG ? (T)(alpha_src ? *alpha_src : A.alpha[p]) : T(0);   // alpha_src: a copy fetched ahead
     T* xg = A.x + base;
     T* routg = A.rout + base;
@@ -443,7 +455,8 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
 }
 
 // Prolongation e + cc P ec, nu = H/2 sweeps (black, red), and with CG (the
-// finest level) r.z, for one work item by one warp.
+// finest level) r.z, for one work item by one warp.  The border of se is zero
+// on entry (zero_border).
 template <typename T, int H, bool CG, class Src, class Hook = NoHook>
 __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
                                   Hook loaded = Hook()) {
@@ -451,7 +464,6 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
     constexpr int NU = H / 2;
     const int n = A.a.n, m = n / 2;
     const size_t base = (size_t)p * n * n;
-    zero_border<T, G>(se, lane);
     WQuad<T> Q[G::SLOTS];
     int c0[G::SLOTS], gq[G::SLOTS];
     bool live[G::SLOTS];
@@ -566,14 +578,15 @@ __global__ void __launch_bounds__(32 * WPB, (BF && !CG) ? 4 : 0) k_wpre(WPreArgs
     const int item = blockIdx.x * WPB + warp;
     if (item >= work_total(A.a)) return;
     const int n = A.a.n;
-    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    int pi, tile, tx, ty;
+    item_tile(A.a, item, pi, tile, tx, ty);
     const int p = A.a.list[pi];
-    const int tpr = n / WT;
     const size_t base = (size_t)p * n * n;
     const auto fc = smoother_faces<T, BF>(A, base);
     GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.rin + base, A.q + base,
                       A.x + base, A.p + base, n};
-    wpre_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
+    zero_border<T, G>(sme[warp], lane);
+    wpre_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tx, ty);
 }
 
 template <typename T, int H, bool CG, bool BF = false>
@@ -585,14 +598,15 @@ __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     const int item = blockIdx.x * WPB + warp;
     if (item >= work_total(A.a)) return;
     const int n = A.a.n, m = n / 2;
-    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    int pi, tile, tx, ty;
+    item_tile(A.a, item, pi, tile, tx, ty);
     const int p = A.a.list[pi];
-    const int tpr = n / WT;
     const size_t base = (size_t)p * n * n;
     const auto fc = smoother_faces<T, BF>(A, base);
     GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.r + base, A.e_in + base,
                       A.ec + (size_t)p * m * m, nullptr, n};
-    wpost_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tile % tpr, tile / tpr);
+    zero_border<T, G>(sme[warp], lane);
+    wpost_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tx, ty);
 }
 
 template <typename T>
@@ -627,10 +641,9 @@ __device__ inline void wapply_item(const WApplyArgs<T>& A, T* sp, int lane, int 
     constexpr int PW = WAPPLY_PW;
     constexpr int PR = WAPPLY_PR;
     const int n = A.a.n;
-    const int pi = item / A.a.ntiles, tile = item - pi * A.a.ntiles;
+    int pi, tile, tx, ty;
+    item_tile(A.a, item, pi, tile, tx, ty);
     const int p = A.a.list[pi];
-    const int tpr = n / WT;
-    const int tx = tile % tpr, ty = tile / tpr;
     const size_t base = (size_t)p * n * n;
     const T* zg = A.z + base;
     const T* pg = A.pin + base;

@@ -126,12 +126,9 @@ struct StagedSrc {
 };
 
 __device__ inline void item_decode(const WArgs& a, int item, int& p, int& tile, int& tx, int& ty) {
-    const int pi = item / a.ntiles;
-    tile = item - pi * a.ntiles;
+    int pi;
+    item_tile(a, item, pi, tile, tx, ty);
     p = a.list[pi];
-    const int tpr = a.n / WT;
-    tx = tile % tpr;
-    ty = tile / tpr;
 }
 
 // The persistent pipeline of one warp: `issue(item)` (lane 0) starts the
@@ -223,13 +220,14 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpre(WPreArgs<float> A,
         __syncwarp();
         const int p = *next_p;
         const double al = CG ? *next_alpha : 0.0;
-        const int tile = item % A.a.ntiles;
-        const int tpr = A.a.n / WT;
-        const int tx = tile % tpr, ty = tile / tpr;
+        int pi, tile, tx, ty;
+        item_tile(A.a, item, pi, tile, tx, ty);
         const float* st = wb;
         StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
                           st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, st + G::P_OFF,
                           A.E + (size_t)p * n, A.Nn + (size_t)p * n, n, tx * WT - 4, ty * WT - H, tx * WT, ty * WT, 0, 0};
+        // the border is zeroed per item here (once per warp in k_tpost): measured faster for this pass
+        zero_border<float, WGeo<float, H>>(wb + L::SE_OFF, ln);
         wpre_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill, CG ? &al : nullptr);
     };
     warp_pipeline(A.a, bar, lane, issue, work);
@@ -268,9 +266,8 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
     auto work = [&](int item, int ln, auto refill) {
         __syncwarp();
         const int p = *next_p;                       // written when the item's copies started
-        const int tile = item % A.a.ntiles;
-        const int tpr = A.a.n / WT;
-        const int tx = tile % tpr, ty = tile / tpr;
+        int pi, tile, tx, ty;
+        item_tile(A.a, item, pi, tile, tx, ty);
         const float* st = wb;
         StagedSrc<H, F> S{reinterpret_cast<const F*>(st + G::KW_OFF), reinterpret_cast<const F*>(st + G::KS_OFF),
                           st + G::R_OFF, st + G::V_OFF, st + G::X_OFF, nullptr,
@@ -278,6 +275,7 @@ __global__ void __launch_bounds__(32 * TW_WARPS, MINB) k_tpost(WPostArgs<float> 
                           tx * (WT / 2) - 4, ty * (WT / 2) - H / 2};
         wpost_item<float, H, CG>(A, S, wb + L::SE_OFF, ln, p, tile, tx, ty, refill);
     };
+    zero_border<float, WGeo<float, H>>(wb + L::SE_OFF, lane);   // once: no item writes it
     warp_pipeline(A.a, bar, lane, issue, work);
 }
 
