@@ -45,7 +45,7 @@ SMALL_WORKLOAD = "darcy64_bimodal"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of the dominant kernel k_tpre<2,CG>, from one
 # capture of the current kernel on the 512-particle case (profiles/k_tpre_darcy256_n512.md), per smoother
 # face storage; None where no capture of the current kernel exists
-TRAFFIC_BYTES_PER_CELL = {"fp32": 36.07, "bf16": 31.83}
+TRAFFIC_BYTES_PER_CELL = {"fp32": 36.03, "bf16": 31.83}
 METRIC = "particle-move PDE solves/sec at 256^2, fp32+refine vs fp64; HBM roofline %"
 UNIT = "solves/s"
 
