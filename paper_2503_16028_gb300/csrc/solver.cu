@@ -85,13 +85,8 @@ __global__ void k_faces(int n, int count, const double* __restrict__ s, FaceOut 
 // to ~1e-14 relative for the FP64-accurate residual.  |u| >= 64 (beyond the
 // FP32 range of e^u) sets err[1] and is reported by the host.  With Kwb, Ksb
 // (the BF16 smoother faces) the interior faces are also stored rounded to BF16.
-// The block has two warps beyond the tile's 256 threads, so the 297 exponentials
-// of the tile and its halo take one round (with 256 threads, 41 threads computed
-// a second one while the rest of the block waited at the barrier).
 constexpr int FX = 32, FY = 8;
-constexpr int FACE_THREADS = FX * FY + 64;
-static_assert((FX + 1) * (FY + 1) <= FACE_THREADS, "one exponential per thread");
-__global__ void __launch_bounds__(FACE_THREADS) k_faces_df(int n, const float2* __restrict__ u, const float2* __restrict__ exptab,
+__global__ void __launch_bounds__(FX * FY) k_faces_df(int n, const float2* __restrict__ u, const float2* __restrict__ exptab,
                                                       ExpConsts ec, float* __restrict__ Kwh, float* __restrict__ Kwl,
                                                       float* __restrict__ Ksh, float* __restrict__ Ksl, float* __restrict__ Eh,
                                                       float* __restrict__ El, float* __restrict__ Nh, float* __restrict__ Nl,
@@ -127,7 +122,6 @@ __global__ void __launch_bounds__(FACE_THREADS) k_faces_df(int n, const float2* 
         badp[p] = 1;                          // the particle (batch index) whose field is out of range
     }
     __syncthreads();
-    if (threadIdx.x >= FX * FY) return;       // the extra warps only computed exponentials
     const int lx = threadIdx.x % FX, ly = threadIdx.x / FX;
     const int i = tx * FX + lx, j = ty * FY + ly;
     const size_t t = base + (size_t)j * n + i;
@@ -1313,7 +1307,7 @@ void launch_setup_coeffs(Ctx& c, int count) {
     if (mixed && n % FX == 0 && n % FY == 0) {
         LevelArrays<float>& f0 = c.s32.lv[0];
         check(cudaMemsetAsync(c.badp, 0, count * sizeof(int), c.stream), "memset badp");
-        k_faces_df<<<dim3((n / FX) * (n / FY), count), FACE_THREADS, 0, c.stream>>>(
+        k_faces_df<<<dim3((n / FX) * (n / FY), count), FX * FY, 0, c.stream>>>(
             n, reinterpret_cast<const float2*>(c.u64), reinterpret_cast<const float2*>(c.exptab), c.expc, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo,
             f0.Kwb, f0.Ksb, c.dev_err, c.badp); ++c.pc.launches;
         launch_coarsen_all<float>(c, c.s32, count);
