@@ -510,6 +510,38 @@ def time_e2e(s, N, d, steps, torch, barrier, world):
                 step_ms=dict(min=min(step_ms), median=statistics.median(step_ms), max=max(step_ms)))
 
 
+def time_e2e_graph(s, N, d, steps, torch, barrier, world, smcgm):
+    """End to end through the batched-move API with host buffers (smc_batch_move_host on a
+    one-sampler batch, one move per launch): every step copies the particles and potentials in
+    from pinned host buffers, runs the move as one CUDA graph (its loops on the device, one host
+    wait) and copies them back, inside the timed region (wall clock over all steps)."""
+    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
+    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    X0, P0 = s.particles()
+    Xh.numpy()[:] = X0
+    Ph.numpy()[:] = P0
+    Xo = torch.empty_like(Xh).pin_memory()
+    Po = torch.empty_like(Ph).pin_memory()
+    b = smcgm.Batch([s], steps=1)
+    try:
+        b.move_host([Xh], [Ph], [Xo], [Po], allow_noconv=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_ms = []
+        for _ in range(steps):
+            ts = time.perf_counter()
+            b.move_host([Xh], [Ph], [Xo], [Po], allow_noconv=True)
+            step_ms.append((time.perf_counter() - ts) * 1000.0)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
+    finally:
+        b.close()
+    return dict(value=whole_job_rate(N * steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * d * 8 + N * 8,
+                d2h_bytes_per_step=N * d * 8 + N * 8, steps=steps, api="smc_batch_move_host",
+                step_ms=dict(min=min(step_ms), median=statistics.median(step_ms), max=max(step_ms)))
+
+
 def time_moves(s, steps, warmup, torch, barrier):
     for _ in range(warmup):
         s.smc_move(1, allow_noconv=True)
@@ -631,7 +663,11 @@ def run_native(args, rank, world, local):
                  residuals_per_solve=prof["residuals"] / max(1, prof["solves"]),
                  host_syncs_per_move=prof["host_syncs"] / args.steps)
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e = None if args.no_e2e else time_e2e(s, N, d, args.steps, torch, barrier, world)
+    e2e = e2e_host = None
+    if not args.no_e2e:
+        e2e_host = time_e2e(s, N, d, args.steps, torch, barrier, world)
+        e2e_host["api"] = "smc_move_host"
+        e2e = time_e2e_graph(s, N, d, args.steps, torch, barrier, world, smcgm)
     forward = None if args.no_forward else time_forward(s, torch)
     graph = None if args.no_graph else time_graph(s, N, args.steps, torch)
     s.close()
@@ -690,7 +726,8 @@ def run_native(args, rank, world, local):
                 iterations=iters, fp64=fp64,
                 speedup_vs_fp64=(value / fp64["value"]) if fp64 else None, posterior_error_vs_fp64=posterior,
                 fp64_agreement=agree,
-                solver_only=forward, graph=graph, smoother_alternative=alt_leg, e2e=e2e, clocks=clk, gpu_launches=prof["launches"],
+                solver_only=forward, graph=graph, smoother_alternative=alt_leg, e2e=e2e, e2e_host_driven=e2e_host,
+                clocks=clk, gpu_launches=prof["launches"],
                 cpu_baseline=cpu,
                 adjoint_gradient=grad, em_fit=em, smc_run=layers, small_workload=small, batch_workload=batch32,
                 autotune=tuned)

@@ -353,6 +353,18 @@ smc_status smc_resample_indices_static(const double* d_logw, int n_particles, un
 typedef struct smc_batch smc_batch;
 smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batch** out);
 smc_status smc_batch_move(smc_batch* batch, double* accept_rates);
+
+/* smc_batch_move with the particles in host memory: context i's state is first
+ * replaced by X_in[i] (N x d doubles, row-major) and Phi_in[i] (N doubles), the
+ * graph moves every context, and the moved state is copied to X_out[i] and
+ * Phi_out[i] (the arrays X_out, Phi_out, or an entry of them, may be NULL to skip
+ * that copy).  All arrays have one entry per context, in the order given to
+ * smc_batch_create; the buffers belong to the caller (page-locked ones make the
+ * copies asynchronous).  The copies run on the graph's stream around the launch,
+ * and the call returns after the last one, with one wait.  Errors as
+ * smc_batch_move, and SMC_EINVAL for a NULL X_in, Phi_in or entry of them. */
+smc_status smc_batch_move_host(smc_batch* batch, const double* const* X_in, const double* const* Phi_in,
+                               double* const* X_out, double* const* Phi_out, double* accept_rates);
 void smc_batch_destroy(smc_batch* batch);
 
 /* Library version string (static storage owned by the library; never NULL). */

@@ -992,9 +992,11 @@ smc_status smc_batch_create(smc_ctx* const* ctxs, int count, int steps, smc_batc
     return SMC_OK;
 }
 
-smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
+// The batched move; with host arrays, each context's particles and potentials are
+// copied in before the launch and out after it, on the graph's stream.
+static smc_status batch_move(smc_batch* b, double* accept_rates, const double* const* X_in, const double* const* Phi_in,
+                             double* const* X_out, double* const* Phi_out) {
     if (!b) return SMC_EINVAL;
-    NvtxRange nvtx("smc_batch_move");
     const int count = (int)b->ctxs.size();
     for (int i = 0; i < count; ++i) {
         const Ctx& c = b->ctxs[i]->c;
@@ -1014,10 +1016,18 @@ smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
             check(cudaEventRecord(b->done[i], c.stream), "record");          // earlier work on the context's stream first
             check(cudaStreamWaitEvent(b->origin, b->done[i], 0), "wait");
             check(cudaMemcpyAsync(c.msched, &ms[i], sizeof(MoveSched), cudaMemcpyHostToDevice, b->origin), "schedule");
+            if (X_in) {
+                check(cudaMemcpyAsync(c.X, X_in[i], (size_t)c.N * c.d * sizeof(double), cudaMemcpyHostToDevice, b->origin), "h2d X");
+                check(cudaMemcpyAsync(c.Phi, Phi_in[i], (size_t)c.N * sizeof(double), cudaMemcpyHostToDevice, b->origin), "h2d Phi");
+            }
         }
         check(cudaGraphLaunch(b->exec, b->origin), "graph launch");
         for (int i = 0; i < count; ++i) {
             Ctx& c = b->ctxs[i]->c;
+            if (X_out && X_out[i])
+                check(cudaMemcpyAsync(X_out[i], c.X, (size_t)c.N * c.d * sizeof(double), cudaMemcpyDeviceToHost, b->origin), "d2h X");
+            if (Phi_out && Phi_out[i])
+                check(cudaMemcpyAsync(Phi_out[i], c.Phi, (size_t)c.N * sizeof(double), cudaMemcpyDeviceToHost, b->origin), "d2h Phi");
             check(cudaMemcpyAsync(&acc[i], c.icount, sizeof(int), cudaMemcpyDeviceToHost, b->origin), "d2h");
             check(cudaMemcpyAsync(&gc[i], c.gcnt, sizeof(GraphCounters), cudaMemcpyDeviceToHost, b->origin), "d2h");
             check(cudaMemcpyAsync(&err[2 * i], c.dev_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->origin), "d2h");
@@ -1063,6 +1073,23 @@ smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
         }
     }
     return st;
+}
+
+smc_status smc_batch_move(smc_batch* b, double* accept_rates) {
+    NvtxRange nvtx("smc_batch_move");
+    return batch_move(b, accept_rates, nullptr, nullptr, nullptr, nullptr);
+}
+
+smc_status smc_batch_move_host(smc_batch* b, const double* const* X_in, const double* const* Phi_in, double* const* X_out,
+                               double* const* Phi_out, double* accept_rates) {
+    if (!b || !X_in || !Phi_in) return SMC_EINVAL;
+    for (size_t i = 0; i < b->ctxs.size(); ++i)
+        if (!X_in[i] || !Phi_in[i]) {
+            set_global_error("smc_batch_move_host: every context needs X_in and Phi_in");
+            return SMC_EINVAL;
+        }
+    NvtxRange nvtx("smc_batch_move_host");
+    return batch_move(b, accept_rates, X_in, Phi_in, X_out, Phi_out);
 }
 
 void smc_batch_destroy(smc_batch* b) { batch_free(b); }

@@ -77,6 +77,7 @@ EXPORTS = {
     "smc_resample_indices_static": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _vp, _vp]),
     "smc_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
     "smc_batch_move": (ctypes.c_int, [_vp, _vp]),
+    "smc_batch_move_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "smc_batch_destroy": (None, [_vp]),
 }
 
@@ -412,6 +413,30 @@ class Batch:
         """One launch of the graph; returns the acceptance rate of every sampler."""
         rates = np.empty(len(self.samplers))
         st = self.lib.smc_batch_move(self.handle, _ptr(rates))
+        if st != SMC_OK and not (allow_noconv and st == SMC_ENOCONV):
+            raise SMCError(st, self.lib.smc_last_error(None).decode())
+        return rates
+
+    def move_host(self, X_in, Phi_in, X_out=None, Phi_out=None, allow_noconv=False):
+        """move() with every sampler's particles taken from and returned to host arrays
+        (lists with one float64 array per sampler: X as N x d, Phi as N); returns the
+        acceptance rates."""
+        k = len(self.samplers)
+        for name, arrs in (("X_in", X_in), ("Phi_in", Phi_in), ("X_out", X_out), ("Phi_out", Phi_out)):
+            if arrs is not None and len(arrs) != k:
+                raise ValueError("%s needs one array per sampler" % name)
+        for i, s in enumerate(self.samplers):
+            _host_f64(X_in[i], s.N * s.d, "X_in[%d]" % i)
+            _host_f64(Phi_in[i], s.N, "Phi_in[%d]" % i)
+            if X_out is not None:
+                _host_f64(X_out[i], s.N * s.d, "X_out[%d]" % i)
+            if Phi_out is not None:
+                _host_f64(Phi_out[i], s.N, "Phi_out[%d]" % i)
+
+        def table(arrs):
+            return None if arrs is None else (_vp * k)(*[_ptr(a).value for a in arrs])
+        rates = np.empty(k)
+        st = self.lib.smc_batch_move_host(self.handle, table(X_in), table(Phi_in), table(X_out), table(Phi_out), _ptr(rates))
         if st != SMC_OK and not (allow_noconv and st == SMC_ENOCONV):
             raise SMCError(st, self.lib.smc_last_error(None).decode())
         return rates

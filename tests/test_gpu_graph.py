@@ -125,6 +125,31 @@ def test_largest_grid_in_graph_equals_host_loop():
     graph.close()
 
 
+def test_batch_move_host_equals_move_host():
+    """The host-buffer form of the batched move against smc_move_host on a twin: the state
+    is replaced from host arrays (here the particles in reverse order), moved once and copied
+    back; outputs, acceptance rates and the schedule must be identical."""
+    host, graph = _twins("darcy64_bimodal", n_particles=64, n_components=2)
+    X0, P0 = host.particles()
+    X_in = np.ascontiguousarray(X0[::-1])
+    P_in = np.ascontiguousarray(P0[::-1])
+    b = smcgm.Batch([graph], steps=1)
+    for _ in range(2):
+        Xh, Ph = np.empty_like(X_in), np.empty_like(P_in)
+        Xg, Pg = np.empty_like(X_in), np.empty_like(P_in)
+        acc_h = host.smc_move_host(X_in, P_in, Xh, Ph)
+        acc_g = b.move_host([X_in], [P_in], [Xg], [Pg])
+        assert acc_g[0] == acc_h
+        assert np.array_equal(Xg, Xh) and np.array_equal(Pg, Ph)
+        assert not np.array_equal(Xg, X_in)          # the move did move particles
+        _same_state(host, graph)
+    with pytest.raises(ValueError):
+        b.move_host([X_in, X_in], [P_in])
+    b.close()
+    host.close()
+    graph.close()
+
+
 def test_batch_rejects_unsupported_contexts():
     wl = inputs.load_workload("darcy64_bimodal")
     s = smcgm.Sampler(smcgm.make_config(wl, n_particles=8, n_components=1, kernel=smcgm.SMC_K_PCNL, gradient=1))
