@@ -676,7 +676,7 @@ def run_native(args, rank, world, local):
     alt_leg = None
     if not args.no_alt_smoother:
         sb = make_sampler(wl, prec_of[alt], N, smcgm)
-        msb, profb = time_moves(sb, args.steps, min(args.warmup, 2), torch, barrier)
+        msb, profb = time_moves(sb, args.steps, args.warmup, torch, barrier)
         sb.close()
         msb = max_over_ranks(msb, world, "cuda")
         dom_b = profb["dom_bytes"] / (profb["dom_ms"] / 1000.0) / 1e9 if profb["dom_ms"] > 0 else 0.0

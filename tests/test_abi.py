@@ -79,3 +79,12 @@ def test_init_rejects_small_workspace_without_touching_the_gpu(lib):
     assert lib.smc_init(ctypes.byref(cfg), ctypes.c_void_p(256), 1024, None, ctypes.byref(ctx)) == smcgm.SMC_ENOMEM
     assert b"workspace" in lib.smc_last_error(None)
     assert lib.smc_temper_step(None, None, None, None, None) == smcgm.SMC_EINVAL
+
+
+def test_batch_calls_reject_null_arguments_without_touching_the_gpu(lib):
+    from paper_2503_16028_gb300 import smcgm
+    out = ctypes.c_void_p()
+    assert lib.smc_batch_create(None, 1, 1, ctypes.byref(out)) == smcgm.SMC_EINVAL
+    assert lib.smc_batch_move(None, None) == smcgm.SMC_EINVAL
+    assert lib.smc_batch_move_host(None, None, None, None, None, None) == smcgm.SMC_EINVAL
+    lib.smc_batch_destroy(None)                     # a no-op
