@@ -483,17 +483,21 @@ def time_graph(s, N, steps, torch, reps=2):
                 cg_per_solve=prof["cg_iterations"] / max(1, prof["solves"]))
 
 
-def time_e2e(s, N, d, steps, torch, barrier, world):
+def pinned_buffers(N, d, torch):
+    """The e2e legs' page-locked host buffers (X in, Phi in, X out, Phi out), allocated once when the
+    bench starts, as an application would allocate its staging buffers."""
+    return (torch.empty((N, d), dtype=torch.float64).pin_memory(), torch.empty(N, dtype=torch.float64).pin_memory(),
+            torch.empty((N, d), dtype=torch.float64).pin_memory(), torch.empty(N, dtype=torch.float64).pin_memory())
+
+
+def time_e2e(s, N, d, steps, torch, barrier, world, bufs=None):
     """End to end through the C ABI (smc_move_host): every step copies the particles and potentials
     from pinned host buffers to the device, moves them and copies them back, inside the timed region
     (wall clock over all steps, after one untimed call)."""
-    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
-    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    Xh, Ph, Xo, Po = bufs or pinned_buffers(N, d, torch)
     X0, P0 = s.particles()
     Xh.numpy()[:] = X0
     Ph.numpy()[:] = P0
-    Xo = torch.empty_like(Xh).pin_memory()
-    Po = torch.empty_like(Ph).pin_memory()
     s.smc_move_host(Xh, Ph, Xo, Po)
     barrier()
     torch.cuda.synchronize()
@@ -510,18 +514,15 @@ def time_e2e(s, N, d, steps, torch, barrier, world):
                 step_ms=dict(min=min(step_ms), median=statistics.median(step_ms), max=max(step_ms)))
 
 
-def time_e2e_graph(s, N, d, steps, torch, barrier, world, smcgm):
+def time_e2e_graph(s, N, d, steps, torch, barrier, world, smcgm, bufs=None):
     """End to end through the batched-move API with host buffers (smc_batch_move_host on a
     one-sampler batch, one move per launch): every step copies the particles and potentials in
     from pinned host buffers, runs the move as one CUDA graph (its loops on the device, one host
     wait) and copies them back, inside the timed region (wall clock over all steps)."""
-    Xh = torch.empty((N, d), dtype=torch.float64).pin_memory()
-    Ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    Xh, Ph, Xo, Po = bufs or pinned_buffers(N, d, torch)
     X0, P0 = s.particles()
     Xh.numpy()[:] = X0
     Ph.numpy()[:] = P0
-    Xo = torch.empty_like(Xh).pin_memory()
-    Po = torch.empty_like(Ph).pin_memory()
     b = smcgm.Batch([s], steps=1)
     try:
         b.move_host([Xh], [Ph], [Xo], [Po], allow_noconv=True)
@@ -619,6 +620,10 @@ def run_native(args, rank, world, local):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    wl = inputs.load_workload(WORKLOAD)
+    N = args.particles or wl["n_particles"]
+    d = wl["kl_modes"] ** 2
+    bufs = None if args.no_e2e else pinned_buffers(N, d, torch)
     # CPU oracle first (before the GPU is busy; a plain subprocess, no fork of a CUDA process)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -631,8 +636,6 @@ def run_native(args, rank, world, local):
         rate, o = cpu_oracle_rate(args.cpu_seconds / 3.0, workload=SMALL_WORKLOAD)
         cpu_small = dict(value=rate, unit=UNIT, cores=o["cores"], kind="oracle",
                          sample="%d solves of the 64^2 workload in %.1f s on %d processes" % (o["solves"], o["seconds"], o["cores"]))
-    wl = inputs.load_workload(WORKLOAD)
-    N = args.particles or wl["n_particles"]
     from paper_2503_16028_gb300 import build
     build.build()
     smcgm.load_library()
@@ -665,9 +668,9 @@ def run_native(args, rank, world, local):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = e2e_host = None
     if not args.no_e2e:
-        e2e_host = time_e2e(s, N, d, args.steps, torch, barrier, world)
+        e2e_host = time_e2e(s, N, d, args.steps, torch, barrier, world, bufs)
         e2e_host["api"] = "smc_move_host"
-        e2e = time_e2e_graph(s, N, d, args.steps, torch, barrier, world, smcgm)
+        e2e = time_e2e_graph(s, N, d, args.steps, torch, barrier, world, smcgm, bufs)
     forward = None if args.no_forward else time_forward(s, torch)
     graph = None if args.no_graph else time_graph(s, N, args.steps, torch)
     s.close()
