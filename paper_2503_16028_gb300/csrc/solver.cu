@@ -1046,6 +1046,17 @@ static void launch_wpre(Ctx& c, InnerSolver<T>& s, int level, int nact, const T*
             return;
         }
     }
+    if constexpr (H == 4 && sizeof(T) == 8) {
+        // the FP64 solver's coarser levels: a pair of warps per item (156 registers, 12 warps per SM,
+        // against 235 and 8 for one warp per item: 2 % faster; in FP32 pairs made the move 8 % slower, their
+        // third slot a quarter full)
+        if (!cg && !want_rr && level > 0) {
+            constexpr int IPB = WPB / 2;
+            k_wpre<T, H, false, false, 2><<<(A.a.total + IPB - 1) / IPB, 32 * WPB, 0, c.stream>>>(A);
+            ++c.pc.launches;
+            return;
+        }
+    }
     if (cg) k_wpre<T, H, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
     else k_wpre<T, H, false><<<grid, 32 * WPB, 0, c.stream>>>(A);
     ++c.pc.launches;
@@ -1064,6 +1075,14 @@ static void launch_wpost(Ctx& c, InnerSolver<T>& s, int level, int nact, const T
         if (L.Kwb) {   // the BF16 smoother faces
             if (cg) k_wpost<T, H, true, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
             else k_wpost<T, H, false, true><<<grid, 32 * WPB, 0, c.stream>>>(A);
+            ++c.pc.launches;
+            return;
+        }
+    }
+    if constexpr (H == 4 && sizeof(T) == 8) {
+        if (!cg && level > 0) {               // as in launch_wpre
+            constexpr int IPB = WPB / 2;
+            k_wpost<T, H, false, false, 2><<<(A.a.total + IPB - 1) / IPB, 32 * WPB, 0, c.stream>>>(A);
             ++c.pc.launches;
             return;
         }

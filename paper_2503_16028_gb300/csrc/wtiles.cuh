@@ -26,8 +26,11 @@ namespace smcgm {
 constexpr int WT = 16;            // tile edge of the warp kernels
 constexpr int WPB = 4;            // warps per block
 
-template <typename T, int H>
+// WI: warps per work item (1, or 2 for the FP64 solver's coarser levels: the item's quads spread
+// over 64 lanes, so each lane holds fewer slots and registers).
+template <typename T, int H, int WI = 1>
 struct WGeo {
+    static constexpr int LANES = 32 * WI;              // lanes that share the item
     static constexpr int RW = WT + 2 * H;              // region edge
     static constexpr int QW = RW / 2;                  // quads per region edge
     static constexpr int NQ = QW * QW;
@@ -37,9 +40,9 @@ struct WGeo {
     // remaining 96 quads fill exactly three slots.
     static constexpr bool CORNERS = (H == 2);
     static constexpr int NQM = CORNERS ? NQ - 4 : NQ;  // quads kept in the slots
-    static constexpr int SLOTS = (NQM + 31) / 32;      // quads per lane
+    static constexpr int SLOTS = (NQM + LANES - 1) / LANES;   // quads per lane
     static constexpr int IQ = WT / 2;                  // tile quads per edge
-    static constexpr int ISL = IQ * IQ / 32;           // slots that hold tile quads (the rest: halo)
+    static constexpr int ISL = IQ * IQ / LANES;        // slots that hold tile quads (the rest: halo)
     // The correction lives in four planes, one per quad cell k, each a grid of
     // quads with a zero border: cell k of the quad at (qx, qy) is at
     // k PL + (qy + 1) QS + qx + 1.  With the quad-row stride QS = 24 (= 24 mod
@@ -58,8 +61,17 @@ struct WGeo {
     static constexpr int EN = PACK ? 2 * PL : 4 * PL;
     static constexpr __host__ __device__ int po(int k) { return k == 0 ? 0 : k == 1 ? PO1 : k == 2 ? PO2 : PO3; }
     static_assert(QW + 2 <= QS, "quad row fits the plane stride");
-    static_assert(IQ * IQ % 32 == 0, "tile quads fill whole slots");
+    static_assert(IQ * IQ % LANES == 0, "tile quads fill whole slots");
 };
+
+// Synchronisation of the lanes that share a work item: the warp, or its pair of
+// warps (named barrier 1 + pair index, 64 threads; both warps of a pair hold the
+// same item and reach every barrier of it, so no barrier waits on an absent warp).
+template <int WI> __device__ __forceinline__ void item_sync();
+template <> __device__ __forceinline__ void item_sync<1>() { __syncwarp(); }
+template <> __device__ __forceinline__ void item_sync<2>() {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + (int)(threadIdx.x >> 6)) : "memory");
+}
 
 // Position (qx, qy) in the region of a warp's quad qi: the tile's quads come
 // first (slots 0 .. ISL-1, always inside the grid), then the halo ring.  Keeping
@@ -220,7 +232,7 @@ __device__ __forceinline__ constexpr int qoff(int k, int dir) {
 template <typename T, class G>
 __device__ inline void zero_border(T* se, int lane) {
     constexpr int QW = G::QW, QS = G::QS;
-    for (int i = lane; i < 8 * QW; i += 32) {
+    for (int i = lane; i < 8 * QW; i += G::LANES) {
         const int side = i / (2 * QW), rem = i % (2 * QW), which = rem / QW, j = rem % QW;
         int plane, pos;
         if (side == 0) { plane = which ? 3 : 1; pos = (j + 1) * QS; }
@@ -311,10 +323,11 @@ struct NoHook {
 // nu = H/2 sweeps (red, black) from zero, residual, restriction; with CG
 // (finest level, a compile-time switch) first r' = r - alpha q, x += alpha p,
 // and |r'|^2.  The border of se is zero on entry (zero_border).
-template <typename T, int H, bool CG, class Src, class Hook = NoHook>
+template <typename T, int H, bool CG, class Src, class Hook = NoHook, int WI = 1>
 __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
                                  Hook loaded = Hook(), const double* alpha_src = nullptr) {
-    using G = WGeo<T, H>;
+    static_assert(WI == 1 || !CG, "the CG update and its sums are one warp's");
+    using G = WGeo<T, H, WI>;
     constexpr int NU = H / 2;
     const int n = A.a.n;
     const size_t base = (size_t)p * n * n;
@@ -336,7 +349,7 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
     T xp[G::ISL][XP];             // x + alpha p, or x and p, on the tile quads (cg)
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
-        const int qi = lane + 32 * sl;
+        const int qi = lane + G::LANES * sl;
         int qx, qy;
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
@@ -416,23 +429,23 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
             }
         }
     }
-    __syncwarp();
+    item_sync<WI>();
 #pragma unroll
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
             if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 0, sw == 0); wgs<T, G>(se, c0[sl], Q[sl], 3, sw == 0); }
-        __syncwarp();
+        item_sync<WI>();
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
             if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 1, false); wgs<T, G>(se, c0[sl], Q[sl], 2, false); }
-        __syncwarp();
+        item_sync<WI>();
     }
     const int m = n / 2;
 #pragma unroll
     for (int sl = 0; sl < G::ISL; ++sl) {
         const int gi = gq[sl];
-        const int qi = lane + 32 * sl;
+        const int qi = lane + G::LANES * sl;
         const int gx = tx * WT + 2 * (qi % G::IQ), gy = ty * WT + 2 * (qi / G::IQ);
         T rsum = T(0), ev[4];
 #pragma unroll
@@ -448,19 +461,22 @@ __device__ inline void wpre_item(const WPreArgs<T>& A, const Src& S, T* se, int 
         st2(A.e_out + base + gi + n, ev[2], ev[3]);
         A.rc[(size_t)p * m * m + (gy >> 1) * m + (gx >> 1)] = rsum;
     }
-    if (CG || A.want_rr) {
-        const double tot = warp_sum<T>(rr);
-        if (lane == 0) A.part_rr[(size_t)p * A.a.ntiles + tile] = tot;
+    if constexpr (WI == 1) {
+        if (CG || A.want_rr) {
+            const double tot = warp_sum<T>(rr);
+            if (lane == 0) A.part_rr[(size_t)p * A.a.ntiles + tile] = tot;
+        }
     }
 }
 
 // Prolongation e + cc P ec, nu = H/2 sweeps (black, red), and with CG (the
 // finest level) r.z, for one work item by one warp.  The border of se is zero
 // on entry (zero_border).
-template <typename T, int H, bool CG, class Src, class Hook = NoHook>
+template <typename T, int H, bool CG, class Src, class Hook = NoHook, int WI = 1>
 __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, int lane, int p, int tile, int tx, int ty,
                                   Hook loaded = Hook()) {
-    using G = WGeo<T, H>;
+    static_assert(WI == 1 || !CG, "the r.z sum is one warp's");
+    using G = WGeo<T, H, WI>;
     constexpr int NU = H / 2;
     const int n = A.a.n, m = n / 2;
     const size_t base = (size_t)p * n * n;
@@ -472,7 +488,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
     // phase 1: all loads first
 #pragma unroll
     for (int sl = 0; sl < G::SLOTS; ++sl) {
-        const int qi = lane + 32 * sl;
+        const int qi = lane + G::LANES * sl;
         int qx, qy;
         quad_pos<H>(qi, qx, qy);
         const int gx = tx * WT - H + 2 * qx, gy = ty * WT - H + 2 * qy;
@@ -519,13 +535,13 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
         se[c + G::PO2] = ev[sl][2] + up;
         se[c + G::PO3] = ev[sl][3] + up;
     }
-    __syncwarp();
+    item_sync<WI>();
 #pragma unroll
     for (int sw = 0; sw < NU; ++sw) {
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
             if (live[sl]) { wgs<T, G>(se, c0[sl], Q[sl], 1, false); wgs<T, G>(se, c0[sl], Q[sl], 2, false); }
-        __syncwarp();
+        item_sync<WI>();
         // the last (red) half-sweep matters only on the tile: no later update reads the halo
 #pragma unroll
         for (int sl = 0; sl < G::SLOTS; ++sl)
@@ -533,7 +549,7 @@ __device__ inline void wpost_item(const WPostArgs<T>& A, const Src& S, T* se, in
                 wgs<T, G>(se, c0[sl], Q[sl], 0, false);
                 wgs<T, G>(se, c0[sl], Q[sl], 3, false);
             }
-        __syncwarp();
+        item_sync<WI>();
     }
     T rz = T(0);
 #pragma unroll
@@ -569,14 +585,16 @@ __device__ inline auto smoother_faces(const A& args, size_t base) {
 // smoother's interior faces are the BF16 copies (FP32 solver only); the
 // lower levels' BF16 pre-smoothing is held to 128 registers (16 warps per SM,
 // as the FP32 kernel).
-template <typename T, int H, bool CG, bool BF = false>
-__global__ void __launch_bounds__(32 * WPB, (BF && !CG) ? 4 : 0) k_wpre(WPreArgs<T> A) {
-    using G = WGeo<T, H>;
+// WI = 2: a pair of warps per item (the FP64 solver's coarser levels, 3 blocks per SM; 6 for FP32).
+template <typename T, int H, bool CG, bool BF = false, int WI = 1>
+__global__ void __launch_bounds__(32 * WPB, WI == 2 ? (sizeof(T) == 4 ? 6 : 3) : (BF && !CG) ? 4 : 0) k_wpre(WPreArgs<T> A) {
+    using G = WGeo<T, H, WI>;
     using F = typename std::conditional<BF, __nv_bfloat16, T>::type;
-    __shared__ T sme[WPB][G::EN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + warp;
-    if (item >= work_total(A.a)) return;
+    constexpr int IPB = WPB / WI;                      // items per block
+    __shared__ T sme[IPB][G::EN];
+    const int slot = threadIdx.x / G::LANES, lane = threadIdx.x % G::LANES;
+    const int item = blockIdx.x * IPB + slot;
+    if (item >= work_total(A.a)) return;              // both warps of a pair leave together
     const int n = A.a.n;
     int pi, tile, tx, ty;
     item_tile(A.a, item, pi, tile, tx, ty);
@@ -585,18 +603,19 @@ __global__ void __launch_bounds__(32 * WPB, (BF && !CG) ? 4 : 0) k_wpre(WPreArgs
     const auto fc = smoother_faces<T, BF>(A, base);
     GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.rin + base, A.q + base,
                       A.x + base, A.p + base, n};
-    zero_border<T, G>(sme[warp], lane);
-    wpre_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tx, ty);
+    zero_border<T, G>(sme[slot], lane);
+    wpre_item<T, H, CG, GlobalSrc<T, F>, NoHook, WI>(A, S, sme[slot], lane, p, tile, tx, ty);
 }
 
-template <typename T, int H, bool CG, bool BF = false>
-__global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
-    using G = WGeo<T, H>;
+template <typename T, int H, bool CG, bool BF = false, int WI = 1>
+__global__ void __launch_bounds__(32 * WPB, WI == 2 ? (sizeof(T) == 4 ? 6 : 3) : 0) k_wpost(WPostArgs<T> A) {
+    using G = WGeo<T, H, WI>;
     using F = typename std::conditional<BF, __nv_bfloat16, T>::type;
-    __shared__ T sme[WPB][G::EN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + warp;
-    if (item >= work_total(A.a)) return;
+    constexpr int IPB = WPB / WI;
+    __shared__ T sme[IPB][G::EN];
+    const int slot = threadIdx.x / G::LANES, lane = threadIdx.x % G::LANES;
+    const int item = blockIdx.x * IPB + slot;
+    if (item >= work_total(A.a)) return;              // both warps of a pair leave together
     const int n = A.a.n, m = n / 2;
     int pi, tile, tx, ty;
     item_tile(A.a, item, pi, tile, tx, ty);
@@ -605,8 +624,8 @@ __global__ void __launch_bounds__(32 * WPB) k_wpost(WPostArgs<T> A) {
     const auto fc = smoother_faces<T, BF>(A, base);
     GlobalSrc<T, F> S{fc.kw, fc.ks, A.E + (size_t)p * n, A.Nn + (size_t)p * n, A.r + base, A.e_in + base,
                       A.ec + (size_t)p * m * m, nullptr, n};
-    zero_border<T, G>(sme[warp], lane);
-    wpost_item<T, H, CG>(A, S, sme[warp], lane, p, tile, tx, ty);
+    zero_border<T, G>(sme[slot], lane);
+    wpost_item<T, H, CG, GlobalSrc<T, F>, NoHook, WI>(A, S, sme[slot], lane, p, tile, tx, ty);
 }
 
 template <typename T>
