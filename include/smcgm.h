@@ -117,7 +117,9 @@ typedef struct smc_config {
     int smooth_sweeps;  /* red-black Gauss-Seidel sweeps per pre/post smoothing on coarse levels (1 or 2) */
     int fine_sweeps;    /* the same on the finest level (1 or 2) */
     double coarse_scale;/* multigrid coarse-correction factor */
-    int solve_batch;    /* particles per forward-solve batch (0: all N) */
+    int solve_batch;    /* particles per forward-solve batch (0: the library's choice, all N up
+                           to 2^28 grid cells per batch, e.g. 4096 particles at 256^2; larger
+                           batches measured slower).  Results do not depend on it */
     unsigned long long seed;
     int gradient;       /* 1: also lay out the arrays of smc_gradient (2D only; two more
                            solution-sized FP64 arrays per batch particle); 0: no gradients */

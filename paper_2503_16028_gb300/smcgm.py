@@ -195,9 +195,10 @@ def choose_solve_batch(workspace_size, n_particles, budget):
 class Sampler:
     """One smc_ctx with its caller-owned device workspace (a torch uint8 tensor).
 
-    With cfg.solve_batch = 0 (all particles in one solve batch) and a workspace larger than
-    90 % of the device's free memory, the batch is reduced to the largest that fits
-    (choose_solve_batch); cfg.solve_batch is updated to the value used."""
+    With cfg.solve_batch = 0 (the library's choice: all particles, up to 2^28 grid cells per
+    solve batch) and a workspace larger than 90 % of the device's free memory, the batch is
+    reduced to the largest that fits (choose_solve_batch); cfg.solve_batch is updated to the
+    value used."""
 
     def __init__(self, cfg, device="cuda:0", stream=None):
         import torch
