@@ -46,6 +46,7 @@ struct F64Ops {
         a = t.x;
         b = t.y;
     }
+    static __device__ void store_pair(V* v, V a, V b) { *reinterpret_cast<double2*>(v) = make_double2(a, b); }
     static __device__ V shfl_up(V v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
     static __device__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 };
@@ -63,6 +64,7 @@ struct DfOps {
         a = df32{t.x, t.y};
         b = df32{t.z, t.w};
     }
+    static __device__ void store_pair(V* v, V a, V b) { *reinterpret_cast<float4*>(v) = make_float4(a.hi, a.lo, b.hi, b.lo); }
     static __device__ V shfl_up(V v, int d) {
         return df32{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
     }
@@ -75,6 +77,69 @@ template <> __device__ inline float2 sqrt2_of<DfOps>() {   // df32 split of sqrt
     return make_float2(1.41421353816986083984375f, 2.42032343e-8f);
 }
 
+// Slot of element i in the two buffers around the register pass below (the last
+// splitting pass writes one, the first butterfly pass after it reads the other):
+// each 8-element segment's four 16-byte chunks are rotated by ((i / 16) mod 4), so
+// that the 8 lanes of a quarter warp, each reading or writing the j-th chunk of
+// its own segment, hit 8 different 16-byte bank groups.
+__device__ __forceinline__ int fct_swz(int i) { return (i & ~7) | ((((i >> 1) + (i >> 4)) & 3) << 1) | (i & 1); }
+template <bool SWZ>
+__device__ __forceinline__ int fct_ix(int i) { return SWZ ? fct_swz(i) : i; }
+
+// One butterfly level lm: G = src[o + i], H = src[o + h + i] (i < h = M/2) to
+// X[o + i] = G + t_i H, X[o + M - 1 - i] = G - t_i H.
+template <class O, bool SWZ>
+__device__ inline void fct_level(const typename O::V* src, typename O::V* dst, int N, int lm,
+                                 const typename O::W* __restrict__ tw, int lane) {
+    using V = typename O::V;
+    const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+    const typename O::W* twa = tw + (h - 1);
+    for (int g = lane; g < (N >> 1); g += 32) {
+        const int o = (g >> lh) << lm, i = g & (h - 1);
+        const V G = src[fct_ix<SWZ>(o + i)];
+        const V ht = O::mul(src[fct_ix<SWZ>(o + h + i)], twa[i]);
+        dst[o + i] = O::add(G, ht);
+        dst[o + M - 1 - i] = O::sub(G, ht);
+    }
+}
+
+// Butterfly levels lm and lm + 1 in one pass: the four values src[o2 + i],
+// src[o2 + h + i], src[o2 + M + i], src[o2 + M + h + i] of level lm give, through
+// it, the G and H of two output pairs (i and M - 1 - i) of level lm + 1, so a group
+// of four is closed under both and shared memory is read and written once for the two.
+template <class O, bool SWZ>
+__device__ inline void fct_level_pair(const typename O::V* src, typename O::V* dst, int N, int lm,
+                                      const typename O::W* __restrict__ tw, int lane) {
+    using V = typename O::V;
+    const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+    const typename O::W* twa = tw + (h - 1);             // level lm
+    const typename O::W* twb = tw + (M - 1);             // level lm + 1 (half size M)
+    for (int g = lane; g < (N >> 2); g += 32) {
+        const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
+        const typename O::W ta = twa[i];
+        const V a = src[fct_ix<SWZ>(o2 + i)];
+        const V bt = O::mul(src[fct_ix<SWZ>(o2 + h + i)], ta);
+        const V c = src[fct_ix<SWZ>(o2 + M + i)];
+        const V dt = O::mul(src[fct_ix<SWZ>(o2 + M + h + i)], ta);
+        const V x0 = O::add(a, bt), x1 = O::sub(a, bt);   // level lm: o2 + i, o2 + M - 1 - i
+        const V y0 = O::add(c, dt), y1 = O::sub(c, dt);   // o2 + M + i, o2 + 2M - 1 - i
+        const V p = O::mul(y0, twb[i]);
+        const V q = O::mul(y1, twb[M - 1 - i]);
+        dst[o2 + i] = O::add(x0, p);
+        dst[o2 + 2 * M - 1 - i] = O::sub(x0, p);
+        dst[o2 + M - 1 - i] = O::add(x1, q);
+        dst[o2 + M + i] = O::sub(x1, q);
+    }
+}
+
+// The DCT-III of one row (N = 2^lgN >= 64 values) by one warp, ping-ponging between
+// b0 and b1; returns the buffer holding the result.  Lee's network: splitting levels
+// lgN .. 1, then butterfly levels 1 .. lgN.  Splitting levels down to segment size 16
+// run one per shared-memory pass; the splitting levels of segment sizes 8 and 4 (that
+// of size 2 is the identity) and the butterfly levels 1 .. 3 act within segments of 8
+// consecutive values, so each lane takes whole segments through them in registers
+// (one pass); the remaining butterfly levels run two per pass.  Every value goes
+// through the same operations, in the same order, as one level at a time.
 template <class O>
 __device__ inline typename O::V* fct_warp(typename O::V* b0, typename O::V* b1, int N, int lgN,
                                           const typename O::W* __restrict__ tw, int lane) {
@@ -85,8 +150,9 @@ __device__ inline typename O::V* fct_warp(typename O::V* b0, typename O::V* b1, 
     // top-down splitting: segment size M -> [even | odd sums].  Thread idx reads
     // its pair (2m, 2m+1) in one 16-byte load and takes element 2m-1 from the
     // thread before it (a shuffle, or the last lane of the previous round).
-    for (int lm = lgN; lm >= 1; --lm) {
+    for (int lm = lgN; lm >= 4; --lm) {
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+        const bool last = lm == 4;                          // writes the register pass's input
         V carry = O::zero();
         for (int idx = lane; idx < half; idx += 32) {        // half is a multiple of 32: all lanes take part
             const int o = (idx >> lh) << lm, m = idx & (h - 1);
@@ -95,51 +161,72 @@ __device__ inline typename O::V* fct_warp(typename O::V* b0, typename O::V* b1, 
             V prev = O::shfl_up(a1, 1);
             if (lane == 0) prev = carry;
             carry = O::shfl(a1, 31);
-            dst[o + m] = a0;
-            dst[o + h + m] = m > 0 ? O::add(a1, prev) : a1;
+            const V odd = m > 0 ? O::add(a1, prev) : a1;
+            dst[last ? fct_swz(o + m) : o + m] = a0;
+            dst[last ? fct_swz(o + h + m) : o + h + m] = odd;
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
-    // bottom-up butterflies: level lm maps G = src[o + i], H = src[o + h + i]
-    // (i < h = M/2) to X[o + i] = G + t_i H, X[o + M - 1 - i] = G - t_i H.  Two
-    // levels run per pass: the four values src[o2 + i], src[o2 + h + i],
-    // src[o2 + M + i], src[o2 + M + h + i] of one level give, through it, the
-    // G and H of two outputs pairs (i and M - 1 - i) of the next level, so a
-    // group of four is closed under both and shared memory is read and
-    // written once for the two.
-    int lm = 1;
-    if (lgN & 1) {
-        for (int i0 = lane; i0 < half; i0 += 32) {           // level 1 alone (M = 2, t = tw[0])
-            const V g = src[2 * i0];
-            const V hp = O::mul(src[2 * i0 + 1], tw[0]);
-            dst[2 * i0] = O::add(g, hp);
-            dst[2 * i0 + 1] = O::sub(g, hp);
+    // segments of 8 in registers: splitting (sizes 8, 4), butterflies 1, 2, 3
+    {
+        const typename O::W t1 = tw[0], t2a = tw[1], t2b = tw[2];
+        for (int sg = lane; sg < (N >> 3); sg += 32) {
+            const int o = sg << 3;
+            V x[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) O::load_pair(src + fct_swz(o + 2 * j), x[2 * j], x[2 * j + 1]);
+            // splitting, segment size 8: [x0 x2 x4 x6 | x1, x3+x1, x5+x3, x7+x5]
+            const V a4 = x[1], a5 = O::add(x[3], x[1]), a6 = O::add(x[5], x[3]), a7 = O::add(x[7], x[5]);
+            // splitting, segment size 4, of [x0 x2 x4 x6] and [a4 a5 a6 a7]
+            V b[8] = {x[0], x[4], x[2], O::add(x[6], x[2]), a4, a6, a5, O::add(a7, a5)};
+            // butterfly level 1 (pairs)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const V ht = O::mul(b[2 * j + 1], t1);
+                const V g = b[2 * j];
+                b[2 * j] = O::add(g, ht);
+                b[2 * j + 1] = O::sub(g, ht);
+            }
+            // butterfly level 2 (quads): i = 0, 1 with t = tw[1 + i]
+            V d[8];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const V h0 = O::mul(b[4 * q + 2], t2a), h1 = O::mul(b[4 * q + 3], t2b);
+                d[4 * q + 0] = O::add(b[4 * q + 0], h0);
+                d[4 * q + 3] = O::sub(b[4 * q + 0], h0);
+                d[4 * q + 1] = O::add(b[4 * q + 1], h1);
+                d[4 * q + 2] = O::sub(b[4 * q + 1], h1);
+            }
+            // butterfly level 3 (the segment): i < 4 with t = tw[3 + i]
+            V e[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const V ht = O::mul(d[4 + i], tw[3 + i]);
+                e[i] = O::add(d[i], ht);
+                e[7 - i] = O::sub(d[i], ht);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) O::store_pair(dst + fct_swz(o + 2 * j), e[2 * j], e[2 * j + 1]);
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
-        lm = 2;
+    }
+    // bottom-up butterflies 4 .. lgN: one level alone first when their number is odd,
+    // then two per pass; the first pass reads the register pass's rotated chunks
+    int lm = 4;
+    bool first = true;
+    if ((lgN - 3) & 1) {
+        fct_level<O, true>(src, dst, N, 4, tw, lane);
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+        lm = 5;
+        first = false;
     }
     for (; lm < lgN; lm += 2) {
-        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        const typename O::W* twa = tw + (h - 1);             // level lm
-        const typename O::W* twb = tw + (M - 1);             // level lm + 1 (half size M)
-        for (int g = lane; g < (N >> 2); g += 32) {
-            const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
-            const typename O::W ta = twa[i];
-            const V a = src[o2 + i];
-            const V bt = O::mul(src[o2 + h + i], ta);
-            const V c = src[o2 + M + i];
-            const V dt = O::mul(src[o2 + M + h + i], ta);
-            const V x0 = O::add(a, bt), x1 = O::sub(a, bt);   // level lm: o2 + i, o2 + M - 1 - i
-            const V y0 = O::add(c, dt), y1 = O::sub(c, dt);   // o2 + M + i, o2 + 2M - 1 - i
-            const V p = O::mul(y0, twb[i]);
-            const V q = O::mul(y1, twb[M - 1 - i]);
-            dst[o2 + i] = O::add(x0, p);
-            dst[o2 + 2 * M - 1 - i] = O::sub(x0, p);
-            dst[o2 + M - 1 - i] = O::add(x1, q);
-            dst[o2 + M + i] = O::sub(x1, q);
-        }
+        if (first) fct_level_pair<O, true>(src, dst, N, lm, tw, lane);
+        else fct_level_pair<O, false>(src, dst, N, lm, tw, lane);
+        first = false;
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
@@ -272,7 +359,7 @@ __device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
-    for (int lm = 1; lm <= lgN; ++lm) {
+    for (int lm = 2; lm <= lgN; ++lm) {              // the level of segment size 2 is the identity
         const int M = 1 << lm, h = M >> 1, lh = lm - 1;
         for (int idx = lane; idx < half; idx += 32) {
             const int o = (idx >> lh) << lm, m = idx & (h - 1);
