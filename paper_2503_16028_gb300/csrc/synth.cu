@@ -89,7 +89,7 @@ __device__ __forceinline__ int fct_ix(int i) { return SWZ ? fct_swz(i) : i; }
 // One butterfly level lm: G = src[o + i], H = src[o + h + i] (i < h = M/2) to
 // X[o + i] = G + t_i H, X[o + M - 1 - i] = G - t_i H.
 template <class O, bool SWZ>
-__device__ inline void fct_level(const typename O::V* src, typename O::V* dst, int N, int lm,
+__device__ __forceinline__ void fct_level(const typename O::V* src, typename O::V* dst, int N, int lm,
                                  const typename O::W* __restrict__ tw, int lane) {
     using V = typename O::V;
     const int M = 1 << lm, h = M >> 1, lh = lm - 1;
@@ -108,7 +108,7 @@ __device__ inline void fct_level(const typename O::V* src, typename O::V* dst, i
 // it, the G and H of two output pairs (i and M - 1 - i) of level lm + 1, so a group
 // of four is closed under both and shared memory is read and written once for the two.
 template <class O, bool SWZ>
-__device__ inline void fct_level_pair(const typename O::V* src, typename O::V* dst, int N, int lm,
+__device__ __forceinline__ void fct_level_pair(const typename O::V* src, typename O::V* dst, int N, int lm,
                                       const typename O::W* __restrict__ tw, int lane) {
     using V = typename O::V;
     const int M = 1 << lm, h = M >> 1, lh = lm - 1;
@@ -237,7 +237,7 @@ __device__ inline typename O::V* fct_warp(typename O::V* b0, typename O::V* b1, 
 //        1 = along y (input T^T[i][l], one transform per i, output U[j][i]).
 // The FP64 input of stage 0 is scaled by c_k in FP64 and then converted.
 template <class O>
-__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
+__global__ void __launch_bounds__(32 * FCT_WARPS, 3) k_fct(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
                                                       const typename O::V* __restrict__ in, typename O::V* __restrict__ out,
                                                       const typename O::W* __restrict__ tw) {
     using V = typename O::V;
@@ -251,22 +251,28 @@ __global__ void __launch_bounds__(32 * FCT_WARPS) k_fct(int stage, int n, int lg
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t inb = stage == 0 ? (size_t)p * Km * Km : (size_t)p * n * Km;
     const size_t outb = stage == 0 ? (size_t)p * n * Km : (size_t)p * n * n;
-    // load inputs: stage 0 rows V[k][t0 .. t0+31]; stage 1 rows T^T[t0 + t][0 .. Km)
-    for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
-        if (stage == 0) {
+    // stage 0: the inputs V[k][t0 .. t0 + 15] (a column per transform) go through the
+    // staging rows, read coalesced along t; stage 1 reads each row T^T[t0 + t][0 .. Km)
+    // straight into the transform's buffer
+    if (stage == 0) {
+        for (int idx = threadIdx.x; idx < FCT_T * Km; idx += blockDim.x) {
             const int k = idx / FCT_T, t = idx % FCT_T;
             stg[t * SP + k] = t0 + t < Km ? O::from_input(in64[inb + (size_t)k * Km + t0 + t] * (k == 0 ? 1.0 : M_SQRT2)) : O::zero();
-        } else {
-            const int t = idx / Km, l = idx % Km;
-            const V v = in[inb + (size_t)(t0 + t) * Km + l];
-            stg[t * SP + l] = l == 0 ? v : O::mul(v, sqrt2_of<O>());
         }
+        __syncthreads();
     }
-    __syncthreads();
     V* b0 = work + warp * 2 * n;
     V* b1 = b0 + n;
     for (int t = warp; t < FCT_T; t += FCT_WARPS) {
-        for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : O::zero();
+        if (stage == 0) {
+            for (int k = lane; k < n; k += 32) b0[k] = k < Km ? stg[t * SP + k] : O::zero();
+        } else {
+            const V* row = in + inb + (size_t)(t0 + t) * Km;
+            for (int k = lane; k < n; k += 32) {
+                const V v = k < Km ? row[k] : O::zero();
+                b0[k] = (k == 0 || k >= Km) ? v : O::mul(v, sqrt2_of<O>());
+            }
+        }
         __syncwarp();
         const V* res = fct_warp<O>(b0, b1, n, lgn, tw, lane);
         for (int k = lane; k < n; k += 32) stg[t * SP + k] = res[k];
