@@ -481,8 +481,9 @@ __device__ inline T cnbr(const T* kw, const T* ks, const T* e, int n, int i, int
     return s;
 }
 
+// One half-sweep of colour col on an n x n level; dinv holds 1/D of every cell.
 template <typename T>
-__device__ inline void chalf(const T* kw, const T* ks, const T* E, const T* Nn, const T* r, T* e, int n, int col, bool pointwise) {
+__device__ inline void chalf(const T* kw, const T* ks, const T* dinv, const T* r, T* e, int n, int col, bool pointwise) {
     const int half = (n * n + 1) / 2;
     for (int k = threadIdx.x; k < half; k += blockDim.x) {
         int j = (2 * k) / n;
@@ -492,7 +493,7 @@ __device__ inline void chalf(const T* kw, const T* ks, const T* E, const T* Nn, 
         if (i >= n) continue;
         T num = r[j * n + i];
         if (!pointwise) num += cnbr(kw, ks, e, n, i, j);
-        e[j * n + i] = num / cdiag(kw, ks, E, Nn, n, i, j);
+        e[j * n + i] = num * dinv[j * n + i];
     }
 }
 
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, c
     extern __shared__ __align__(16) unsigned char smraw[];
     if (P.nact && (int)blockIdx.x >= *P.nact) return;
     const int pb = active[blockIdx.x];   // active-particle list
-    T* kw[12]; T* ks[12]; T* E[12]; T* Nn[12]; T* r[12]; T* e[12];
+    T* kw[12]; T* ks[12]; T* E[12]; T* Nn[12]; T* r[12]; T* e[12];   // 1/D of level l at e[l] + n_l^2
     T* cur = reinterpret_cast<T*>(smraw);
     int nl = P.ntop;
     for (int l = 0; l < P.nlev; ++l) {
@@ -510,6 +511,7 @@ __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, c
         ks[l] = cur; cur += nn;
         r[l] = cur; cur += nn;
         e[l] = cur; cur += nn;
+        cur += nn;                          // 1/D
         E[l] = cur; cur += nl;
         Nn[l] = cur; cur += nl;
         const T* gkw = P.Kw[l] + (size_t)pb * nn;
@@ -531,6 +533,14 @@ __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, c
     }
     cp_async_wait_all();   // every copy of this thread is in shared memory
     __syncthreads();
+    // 1/D of every cell of every level, once (the half-sweeps multiply by it)
+    nl = P.ntop;
+    for (int l = 0; l < P.nlev; ++l) {
+        for (int c = threadIdx.x; c < nl * nl; c += blockDim.x)
+            e[l][nl * nl + c] = T(1) / cdiag(kw[l], ks[l], E[l], Nn[l], nl, c % nl, c / nl);
+        nl >>= 1;
+    }
+    __syncthreads();
     // down
     nl = P.ntop;
     for (int l = 0; l < P.nlev - 1; ++l) {
@@ -538,9 +548,9 @@ __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, c
         for (int i = threadIdx.x; i < nn; i += blockDim.x) e[l][i] = T(0);
         __syncthreads();
         for (int sw = 0; sw < NU; ++sw) {
-            chalf(kw[l], ks[l], E[l], Nn[l], r[l], e[l], nl, 0, sw == 0);
+            chalf(kw[l], ks[l], e[l] + nl * nl, r[l], e[l], nl, 0, sw == 0);
             __syncthreads();
-            chalf(kw[l], ks[l], E[l], Nn[l], r[l], e[l], nl, 1, false);
+            chalf(kw[l], ks[l], e[l] + nl * nl, r[l], e[l], nl, 1, false);
             __syncthreads();
         }
         const int m = nl / 2;
@@ -573,9 +583,9 @@ __global__ void __launch_bounds__(256, 4) k_coarse(CoarseLevelPtrs<T> P, T cc, c
         }
         __syncthreads();
         for (int sw = 0; sw < NU; ++sw) {
-            chalf(kw[l], ks[l], E[l], Nn[l], r[l], e[l], nl, 1, false);
+            chalf(kw[l], ks[l], e[l] + nl * nl, r[l], e[l], nl, 1, false);
             __syncthreads();
-            chalf(kw[l], ks[l], E[l], Nn[l], r[l], e[l], nl, 0, false);
+            chalf(kw[l], ks[l], e[l] + nl * nl, r[l], e[l], nl, 0, false);
             __syncthreads();
         }
     }
@@ -590,7 +600,7 @@ template <typename T>
 size_t coarse_smem_bytes(int ntop, int nlev) {
     size_t s = 0;
     int nl = ntop;
-    for (int l = 0; l < nlev; ++l) { s += (size_t)(4 * nl * nl + 2 * nl); nl >>= 1; }
+    for (int l = 0; l < nlev; ++l) { s += (size_t)(5 * nl * nl + 2 * nl); nl >>= 1; }
     return s * sizeof(T);
 }
 
