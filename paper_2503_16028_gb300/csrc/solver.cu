@@ -724,14 +724,17 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* __restric
 // of the face fluxes, whose sum is ~200 |b| at 256^2).  Stored in FP32 with the
 // partial |res|^2 per tile, summed in FP32 (a convergence test needs no more,
 // and the FP64 unit, ~1/64 of the FP32 rate here, is left to the differences).
-__global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __restrict__ Kwh, const float* __restrict__ Kwl,
+// RES_THREADS per 32 x 32 tile: 128 (four rows of threads) measured faster than 256 (+0.6 % for the
+// whole move) and 512.
+constexpr int RES_THREADS = 128;
+__global__ void __launch_bounds__(RES_THREADS) k_residual_mix(int n, const float* __restrict__ Kwh, const float* __restrict__ Kwl,
                                                       const float* __restrict__ Ksh, const float* __restrict__ Ksl,
                                                       const float* __restrict__ Eh, const float* __restrict__ El,
                                                       const float* __restrict__ Nh, const float* __restrict__ Nl,
                                                       const double* __restrict__ w, const float2* __restrict__ bdf,
                                                       size_t bstride, float* __restrict__ rout,
                                                       double* __restrict__ part_res, const int* __restrict__ act) {
-    __shared__ float red[8];
+    __shared__ float red[RES_THREADS / 32];
     __shared__ float2 FW[TILE][TILE + 1];   // FW[j][i]: flux of the west face of cell (x0 + i, y0 + j); column TILE: the east edge
     __shared__ float2 FS[TILE + 1][TILE];   // FS[j][i]: south face; row TILE: the north edge
     const int pb = blockIdx.y;
@@ -742,7 +745,7 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
     const size_t nn = (size_t)n * n, base = (size_t)pb * nn;
     const double* wp = w + base;
     const float *kwh = Kwh + base, *kwl = Kwl + base, *ksh = Ksh + base, *ksl = Ksl + base;
-    const int li = threadIdx.x % TILE, lj0 = threadIdx.x / TILE;   // 8 rows of threads
+    const int li = threadIdx.x % TILE, lj0 = threadIdx.x / TILE;   // RES_THREADS / 32 rows of threads
     auto flux = [](float kh, float kl, double d) {
         const df32 v = df_mul(df32{kh, kl}, df_from_double_bits(d));
         return make_float2(v.hi, v.lo);
@@ -761,7 +764,7 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
                                      : flux(Nh[(size_t)pb * n + i], Nl[(size_t)pb * n + i], -wc);
     }
     __syncthreads();
-    float acc2 = 0.f;                       // |r|^2 of a thread's 4 cells
+    float acc2 = 0.f;                       // |r|^2 of a thread's cells
     for (int lj = lj0; lj < TILE; lj += blockDim.x / TILE) {
         const int c = (y0 + lj) * n + x0 + li;
         const float2 fw = FW[lj][li], fe = FW[lj][li + 1], fs = FS[lj][li], fn = FS[lj + 1][li];
@@ -778,7 +781,7 @@ __global__ void __launch_bounds__(256) k_residual_mix(int n, const float* __rest
     __syncthreads();
     if (threadIdx.x == 0) {
         float t = 0.f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        for (int k = 0; k < RES_THREADS / 32; ++k) t += red[k];
         part_res[(size_t)pb * gridDim.x + blockIdx.x] = (double)t;
     }
 }
@@ -1398,7 +1401,7 @@ static int solve_batch_t(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R, dou
         k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, W, s.x, sc.act_out); ++c.pc.launches;
         if constexpr (sizeof(T) == 4) {
             LevelArrays<float>& f0 = s.lv[0];
-            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
+            k_residual_mix<<<tgrid, RES_THREADS, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
                                                        s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
         } else {
             k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, W, R.b64, R.stride, s.r[0], c.part.res,
@@ -1658,7 +1661,7 @@ static void solve_batch_graph(Ctx& c, InnerSolver<T>& s, int count, const Rhs& R
         k_update_w<T><<<dim3(n * n / 1024, count), 256, 0, c.stream>>>(n * n, W, s.x, sc.act_out); ++c.pc.launches;
         if constexpr (sizeof(T) == 4) {
             LevelArrays<float>& f0 = s.lv[0];
-            k_residual_mix<<<tgrid, 256, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
+            k_residual_mix<<<tgrid, RES_THREADS, 0, c.stream>>>(n, f0.Kw, c.Kwlo, f0.Ks, c.Kslo, f0.E, c.Elo, f0.Nn, c.Nlo, W, R.bdf, R.stride,
                                                        s.r[0], c.part.res, sc.act_out); ++c.pc.launches;
         } else {
             k_residual<T><<<tgrid, 256, 0, c.stream>>>(n, c.Kw64, c.Ks64, c.E64, c.N64, W, R.b64, R.stride, s.r[0], c.part.res,
