@@ -966,10 +966,11 @@ static void launch_tpre_b(Ctx& c, InnerSolver<float>& s, int level, int nact, co
 template <int H, bool CG>
 static void launch_tpre(Ctx& c, InnerSolver<float>& s, int level, int nact, const CUtensorMap& mr, const float* rin, float* rout,
                         int want_rr, int pc) {
-    // blocks per SM asked of the register allocator: 4 (<= 128 registers, 16 warps) on a
-    // 20 x 20 region, 2 on the 24 x 24 region of two sweeps
-    if (s.lv[level].Kwb) launch_tpre_b<H, CG, H == 2 ? 4 : 2, 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
-    else launch_tpre_b<H, CG, H == 2 ? 4 : 2, 4>(c, s, level, nact, mr, rin, rout, want_rr, pc);
+    // blocks per SM asked of the register allocator: on a 20 x 20 region 4 with the CG update
+    // (<= 128 registers, 16 warps) and 5 without it (<= 96 registers, 20 warps; no spills), 2 on
+    // the 24 x 24 region of two sweeps
+    if (s.lv[level].Kwb) launch_tpre_b<H, CG, H == 2 ? (CG ? 4 : 5) : 2, 2>(c, s, level, nact, mr, rin, rout, want_rr, pc);
+    else launch_tpre_b<H, CG, H == 2 ? (CG ? 4 : 5) : 2, 4>(c, s, level, nact, mr, rin, rout, want_rr, pc);
 }
 
 template <int H, bool CG, int MINB, int FB>

@@ -128,12 +128,12 @@ int main() {
     check_quads<2>();
     check_quads<4>();
     check_staged<2, true, 4, 4, 5>();       // post-smoothing: 5 blocks of 4 warps per SM
-    check_staged<2, false, 4, 4, 5>();
+    check_staged<2, false, 5, 4, 5>();      // without the CG update: 5 blocks per SM both ways
     check_staged<4, true, 2, 4>();
     check_staged<4, false, 2, 4>();
     // BF16 smoother faces: boxes from 16 tx - 8, 40 values (80 bytes) per row
     check_staged<2, true, 4, 2, 5>();
-    check_staged<2, false, 4, 2, 5>();
+    check_staged<2, false, 5, 2, 5>();
     check_staged<4, true, 2, 2>();
     check_staged<4, false, 2, 2>();
     CHECK((TGeo<2, 2>::FXO == 8 && TGeo<2, 2>::KWE == 40 && TGeo<2, 2>::KSE == 40));
