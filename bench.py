@@ -17,7 +17,8 @@ collective in the timed region), timed with a barrier and the maximum over ranks
 Beside the headline the line carries: the roofline of the dominant kernel and
 the whole-move HBM byte model, the FP64 solver's rate and its agreement with the
 mixed-precision path, the solver-only rate (smc_forward), the end-to-end rate
-through smc_move_host with host buffers, the adjoint-gradient rate, a whole SMC
+with pinned host buffers through smc_batch_move_host (each move one CUDA graph;
+the smc_move_host form beside it), the adjoint-gradient rate, a whole SMC
 run to t = 1 timed layer by layer with an FP64 run of the same seed in lockstep
 (the posterior error of the mixed-precision run against it), the 64^2 workload on
 the GPU (host-driven and as one CUDA graph) and on the CPU oracle, the 32-problem
