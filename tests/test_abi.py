@@ -88,3 +88,20 @@ def test_batch_calls_reject_null_arguments_without_touching_the_gpu(lib):
     assert lib.smc_batch_move(None, None) == smcgm.SMC_EINVAL
     assert lib.smc_batch_move_host(None, None, None, None, None, None) == smcgm.SMC_EINVAL
     lib.smc_batch_destroy(None)                     # a no-op
+
+
+def test_default_solve_batch_is_capped_at_2_28_cells(lib):
+    """solve_batch = 0 leaves the batch to the library: all particles, up to 2^28 grid cells per
+    batch (4096 particles at 256^2, 1024 at 512^2); the workspace shows which batch was planned."""
+    from paper_2503_16028_gb300 import inputs, smcgm
+    wl = inputs.load_workload("darcy256_precision")
+    size = ctypes.c_size_t()
+
+    def ws(**over):
+        cfg = smcgm.make_config(wl, **over)
+        assert lib.smc_workspace_size(ctypes.byref(cfg), ctypes.byref(size)) == 0
+        return size.value
+    assert ws(n_particles=16384, solve_batch=0) == ws(n_particles=16384, solve_batch=4096)
+    assert ws(n_particles=16384, solve_batch=0) < ws(n_particles=16384, solve_batch=8192)
+    assert ws(n_particles=2048, solve_batch=0) == ws(n_particles=2048, solve_batch=2048)
+    assert ws(n=512, n_particles=4096, solve_batch=0) == ws(n=512, n_particles=4096, solve_batch=1024)
