@@ -326,6 +326,54 @@ void launch_synth2d_df(Ctx& c, const double* X, int count, float2* U) {
 // the splitting levels, in reverse order, x[2m] = e[m], x[2m + 1] =
 // y[m] + y[m + 1] (y[h] = 0).
 // ------------------------------------------------------------------------
+// One transposed butterfly level lm: the pair (X[o + i], X[o + M - 1 - i]), i < h,
+// to G = X[o + i] + X[o + M - 1 - i] at o + i and H = t_i (X[o + i] - X[o + M - 1 - i])
+// at o + h + i; SWZ: the outputs go to the rotated chunks of fct_swz.
+template <class O, bool SWZ>
+__device__ __forceinline__ void fct_level_t(const typename O::V* src, typename O::V* dst, int N, int lm,
+                                            const typename O::W* __restrict__ tw, int lane) {
+    using V = typename O::V;
+    const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+    const typename O::W* twa = tw + (h - 1);
+    for (int g = lane; g < (N >> 1); g += 32) {
+        const int o = (g >> lh) << lm, i = g & (h - 1);
+        const V a = src[o + i], b = src[o + M - 1 - i];
+        dst[fct_ix<SWZ>(o + i)] = O::add(a, b);
+        dst[fct_ix<SWZ>(o + h + i)] = O::mul(O::sub(a, b), twa[i]);
+    }
+}
+
+// Transposed butterfly levels lm + 1 and lm in one pass (the transpose of fct_level_pair):
+// the four values at o2 + i, o2 + 2M - 1 - i, o2 + M - 1 - i, o2 + M + i map to o2 + i,
+// o2 + h + i, o2 + M + i, o2 + M + h + i.
+template <class O, bool SWZ>
+__device__ __forceinline__ void fct_level_pair_t(const typename O::V* src, typename O::V* dst, int N, int lm,
+                                                 const typename O::W* __restrict__ tw, int lane) {
+    using V = typename O::V;
+    const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+    const typename O::W* twa = tw + (h - 1);
+    const typename O::W* twb = tw + (M - 1);
+    for (int g = lane; g < (N >> 2); g += 32) {
+        const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
+        const V A = src[o2 + i], B = src[o2 + 2 * M - 1 - i], C = src[o2 + M - 1 - i], D = src[o2 + M + i];
+        const V x0 = O::add(A, B), x1 = O::add(C, D);
+        const V y0 = O::mul(O::sub(A, B), twb[i]);
+        const V y1 = O::mul(O::sub(C, D), twb[M - 1 - i]);
+        const typename O::W ta = twa[i];
+        dst[fct_ix<SWZ>(o2 + i)] = O::add(x0, x1);
+        dst[fct_ix<SWZ>(o2 + h + i)] = O::mul(O::sub(x0, x1), ta);
+        dst[fct_ix<SWZ>(o2 + M + i)] = O::add(y0, y1);
+        dst[fct_ix<SWZ>(o2 + M + h + i)] = O::mul(O::sub(y0, y1), ta);
+    }
+}
+
+// The transpose of fct_warp (N = 2^lgN >= 64): the butterfly levels lgN .. 4 two per
+// shared-memory pass from the top (a last one alone when their number is odd; the last
+// pass writes the rotated chunks of fct_swz), then each lane takes segments of 8 through
+// the transposed butterfly levels 3, 2, 1 and the splitting levels of sizes 4 and 8 in
+// registers, then the splitting levels 16 .. N (the level of size 2 is the identity);
+// splitting maps x[2m] = e[m], x[2m + 1] = y[m] + y[m + 1] (y[h] = 0).  Every value goes
+// through the same operations, in the same order, as one level at a time.
 template <class O>
 __device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1, int N, int lgN,
                                             const typename O::W* __restrict__ tw, int lane) {
@@ -333,44 +381,67 @@ __device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1
     V* src = b0;
     V* dst = b1;
     const int half = N >> 1;
-    // transposed butterflies, two levels per pass (levels lm + 1 and lm, the
-    // transpose of fct_warp's paired pass): the four values at o2 + i,
-    // o2 + 2M - 1 - i, o2 + M - 1 - i, o2 + M + i map to o2 + i, o2 + h + i,
-    // o2 + M + i, o2 + M + h + i
-    for (int lm = lgN - 1; lm >= 1; lm -= 2) {
-        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
-        const typename O::W* twa = tw + (h - 1);
-        const typename O::W* twb = tw + (M - 1);
-        for (int g = lane; g < (N >> 2); g += 32) {
-            const int o2 = (g >> lh) << (lm + 1), i = g & (h - 1);
-            const V A = src[o2 + i], B = src[o2 + 2 * M - 1 - i], C = src[o2 + M - 1 - i], D = src[o2 + M + i];
-            const V x0 = O::add(A, B), x1 = O::add(C, D);
-            const V y0 = O::mul(O::sub(A, B), twb[i]);
-            const V y1 = O::mul(O::sub(C, D), twb[M - 1 - i]);
-            const typename O::W ta = twa[i];
-            dst[o2 + i] = O::add(x0, x1);
-            dst[o2 + h + i] = O::mul(O::sub(x0, x1), ta);
-            dst[o2 + M + i] = O::add(y0, y1);
-            dst[o2 + M + h + i] = O::mul(O::sub(y0, y1), ta);
+    const int c = lgN - 3;                              // butterfly levels lgN .. 4
+    int lm = lgN - 1;
+    for (int k = 0; k < c / 2; ++k, lm -= 2) {
+        if (k == c / 2 - 1 && !(c & 1)) fct_level_pair_t<O, true>(src, dst, N, lm, tw, lane);
+        else fct_level_pair_t<O, false>(src, dst, N, lm, tw, lane);
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+    }
+    if (c & 1) {
+        fct_level_t<O, true>(src, dst, N, 4, tw, lane);
+        __syncwarp();
+        V* t = src; src = dst; dst = t;
+    }
+    {
+        const typename O::W t1 = tw[0], t2a = tw[1], t2b = tw[2];
+        for (int sg = lane; sg < (N >> 3); sg += 32) {
+            const int o = sg << 3;
+            V x[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) O::load_pair(src + fct_swz(o + 2 * j), x[2 * j], x[2 * j + 1]);
+            V d[8];                                      // transposed butterfly level 3
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                d[i] = O::add(x[i], x[7 - i]);
+                d[4 + i] = O::mul(O::sub(x[i], x[7 - i]), tw[3 + i]);
+            }
+            V b[8];                                      // level 2 on each half
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                b[4 * q + 0] = O::add(d[4 * q + 0], d[4 * q + 3]);
+                b[4 * q + 2] = O::mul(O::sub(d[4 * q + 0], d[4 * q + 3]), t2a);
+                b[4 * q + 1] = O::add(d[4 * q + 1], d[4 * q + 2]);
+                b[4 * q + 3] = O::mul(O::sub(d[4 * q + 1], d[4 * q + 2]), t2b);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {                 // level 1 on pairs
+                const V a = b[2 * j], bb = b[2 * j + 1];
+                b[2 * j] = O::add(a, bb);
+                b[2 * j + 1] = O::mul(O::sub(a, bb), t1);
+            }
+            // splitting, size 4 on each half: [a0, a2 + a3, a1, a3]
+            const V e0 = b[0], e1 = O::add(b[2], b[3]), e2 = b[1], e3 = b[3];
+            const V e4 = b[4], e5 = O::add(b[6], b[7]), e6 = b[5], e7 = b[7];
+            // splitting, size 8: [e0, e4 + e5, e1, e5 + e6, e2, e6 + e7, e3, e7]
+            O::store_pair(dst + fct_swz(o + 0), e0, O::add(e4, e5));
+            O::store_pair(dst + fct_swz(o + 2), e1, O::add(e5, e6));
+            O::store_pair(dst + fct_swz(o + 4), e2, O::add(e6, e7));
+            O::store_pair(dst + fct_swz(o + 6), e3, e7);
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
     }
-    if (lgN & 1) {                                    // level 1 alone, last (the forward runs it first)
-        for (int i0 = lane; i0 < half; i0 += 32) {
-            const V a = src[2 * i0], b = src[2 * i0 + 1];
-            dst[2 * i0] = O::add(a, b);
-            dst[2 * i0 + 1] = O::mul(O::sub(a, b), tw[0]);
-        }
-        __syncwarp();
-        V* t = src; src = dst; dst = t;
-    }
-    for (int lm = 2; lm <= lgN; ++lm) {              // the level of segment size 2 is the identity
-        const int M = 1 << lm, h = M >> 1, lh = lm - 1;
+    for (int ls = 4; ls <= lgN; ++ls) {
+        const int M = 1 << ls, h = M >> 1, lh = ls - 1;
+        const bool first = ls == 4;                      // reads the register pass's rotated chunks
         for (int idx = lane; idx < half; idx += 32) {
-            const int o = (idx >> lh) << lm, m = idx & (h - 1);
-            dst[o + 2 * m] = src[o + m];
-            dst[o + 2 * m + 1] = m + 1 < h ? O::add(src[o + h + m], src[o + h + m + 1]) : src[o + h + m];
+            const int o = (idx >> lh) << ls, m = idx & (h - 1);
+            const V ev = src[first ? fct_swz(o + m) : o + m];
+            const V y0 = src[first ? fct_swz(o + h + m) : o + h + m];
+            dst[o + 2 * m] = ev;
+            dst[o + 2 * m + 1] = m + 1 < h ? O::add(y0, src[first ? fct_swz(o + h + m + 1) : o + h + m + 1]) : y0;
         }
         __syncwarp();
         V* t = src; src = dst; dst = t;
@@ -383,7 +454,7 @@ __device__ inline typename O::V* fct_warp_t(typename O::V* b0, typename O::V* b1
 //        1 = along x (input T^T[i][l], one transform per l, output G[k][l] =
 //            c_k (DCT-II over i)[k] for k < Km, FP64).
 template <class O>
-__global__ void __launch_bounds__(32 * FCT_WARPS) k_fct_t(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
+__global__ void __launch_bounds__(32 * FCT_WARPS, 3) k_fct_t(int stage, int n, int lgn, int Km, const double* __restrict__ in64,
                                                         const typename O::V* __restrict__ in, typename O::V* __restrict__ out,
                                                         double* __restrict__ out64, const typename O::W* __restrict__ tw) {
     using V = typename O::V;
