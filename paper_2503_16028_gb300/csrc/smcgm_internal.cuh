@@ -52,6 +52,12 @@ struct Key { uint32_t k0, k1; };
 constexpr int FCT_T = 16;
 constexpr int FCT_WARPS = 8;
 constexpr size_t fct_smem_bytes(int n) { return 8 * ((size_t)FCT_T * (n + 1) + (size_t)FCT_WARPS * 2 * n); }
+// Slot of element i (8 bytes) in the two work buffers around a transform's register
+// pass, in which each lane takes a segment of 8 consecutive elements: each segment's
+// four 16-byte chunks are rotated by ((i / 16) mod 4), so that the 8 lanes of a quarter
+// warp, each reading or writing the j-th chunk of its own segment, hit 8 different
+// 16-byte bank groups.  Pairs (2m, 2m + 1) stay together and in order.
+__host__ __device__ inline int fct_swz(int i) { return (i & ~7) | ((((i >> 1) + (i >> 4)) & 3) << 1) | (i & 1); }
 // Largest 2D grid: the transform block of a 1024-point grid would need 256 KB of
 // shared memory, above the 227 KB a block can have.
 constexpr int MAX_N2D = 512;

@@ -77,12 +77,8 @@ template <> __device__ inline float2 sqrt2_of<DfOps>() {   // df32 split of sqrt
     return make_float2(1.41421353816986083984375f, 2.42032343e-8f);
 }
 
-// Slot of element i in the two buffers around the register pass below (the last
-// splitting pass writes one, the first butterfly pass after it reads the other):
-// each 8-element segment's four 16-byte chunks are rotated by ((i / 16) mod 4), so
-// that the 8 lanes of a quarter warp, each reading or writing the j-th chunk of
-// its own segment, hit 8 different 16-byte bank groups.
-__device__ __forceinline__ int fct_swz(int i) { return (i & ~7) | ((((i >> 1) + (i >> 4)) & 3) << 1) | (i & 1); }
+// fct_swz (smcgm_internal.cuh) places the elements of the two buffers around the
+// register passes below.
 template <bool SWZ>
 __device__ __forceinline__ int fct_ix(int i) { return SWZ ? fct_swz(i) : i; }
 

@@ -11,7 +11,9 @@
 //   in the staging buffer;
 // * the dynamic shared memory of the staged kernels, of the cosine transform
 //   and the static shared memory of the operator pass fit the blocks per SM
-//   their launches ask for, and the largest accepted 2D grid fits a block.
+//   their launches ask for, and the largest accepted 2D grid fits a block;
+// * the cosine transforms' chunk rotation keeps pairs together and gives the
+//   register pass conflict-free 16-byte accesses.
 #include <cstdio>
 #include <set>
 #include <utility>
@@ -144,6 +146,25 @@ int main() {
             const int ba = (2 * a * TGeo<2, 2>::KWE * 2 / 4) % 32, bb = (2 * b * TGeo<2, 2>::KWE * 2 / 4) % 32;
             CHECK(ba % 8 == 0 && bb % 8 == 0 && ba != bb);
         }
+    // the transforms' chunk rotation: a permutation of each 8-element segment that keeps
+    // the pairs (2m, 2m + 1) together and in order, under which the 8 lanes of every quarter
+    // warp reading the j-th 16-byte chunk of their own segments hit 8 different bank groups
+    for (int i = 0; i < 4096; ++i) {
+        const int sw = fct_swz(i);
+        CHECK((sw & ~7) == (i & ~7) && (sw & 1) == (i & 1));
+        CHECK(fct_swz(i ^ 1) == (sw ^ 1));
+    }
+    for (int seg0 = 0; seg0 < 4096 / 8; seg0 += 8)
+        for (int j = 0; j < 4; ++j) {
+            std::set<int> groups;
+            for (int l = 0; l < 8; ++l) groups.insert((fct_swz(8 * (seg0 + l) + 2 * j) >> 1) & 7);
+            CHECK(groups.size() == 8);
+        }
+    for (int seg = 0; seg < 4096 / 8; ++seg) {                      // a bijection within the segment
+        std::set<int> slots;
+        for (int k = 0; k < 8; ++k) slots.insert(fct_swz(8 * seg + k));
+        CHECK(slots.size() == 8);
+    }
     // the cosine-transform block fits up to the largest accepted 2D grid and not beyond it;
     // three blocks share an SM at 256^2
     CHECK(fct_smem_bytes(MAX_N2D) <= BLOCK_MAX);
